@@ -1,0 +1,285 @@
+"""FP64 CPU oracle for per-channel overlap-save coherent dedispersion.
+
+TEST INFRASTRUCTURE ONLY. This module is the slow, plain statement of what the
+GPU path computes, used to check it. Only the test-suite, the smoke check and the
+CPU-baseline leg of the benchmark may import it; the product path never does.
+
+It follows De & Gupta, "A Real-time Coherent Dedispersion Pipeline for the
+GMRT" (arXiv:1509.00186), in the paper's order:
+
+  Sec. 2.1, Eq. 1-3   the ISM transfer function and its dispersive (chirp) term
+  Sec. 2.2            the taper ("chirp function") and overlap-save deconvolution
+  Sec. 2.3            the FFT-length rule
+  Sec. 3.1 / 4.3      detection (squaring) and integration of the voltages
+  Sec. 1.2 / 1.3      time alignment of the coherently dedispersed sub-bands
+
+Everything is numpy float64 / complex128. The only library primitives used as
+steps are numpy's FFT (forward sign -, inverse scaled by 1/N), pinned against a
+brute-force DFT in the tests.
+
+Readings of points the paper leaves open (each is listed in the design notes):
+  * the ISM multiplies a channel's spectrum by exp(+i*Phi) under a forward
+    exp(-i...) DFT, so dedispersion multiplies by exp(-i*Phi) (Sec. 2.1 says the
+    correction is the inverse of the third term of Eq. 2);
+  * f_o of Eq. 3 is the lower edge of each channel; a channel's complex baseband
+    bin j sits at f_l = fftfreq(j)*chan_bw + chan_bw/2 (the Nyquist bin at f_l=0);
+  * D = 4.148808e3 s MHz^2 cm^3/pc (the paper's 4.148808e9 with Phi in MHz*us);
+  * the overlap n_ov is ceil(n_d) of the lowest channel rounded up to a multiple
+    of the integration length, and is discarded at the segment START (Sec. 2.2);
+  * the inverse DFT carries 1/N; integration is a sum, not a mean;
+  * channels are aligned to the lowest channel by r_k = rint(delay_k / t_int).
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+# Dispersion constant of Eq. 3, in s MHz^2 cm^3 pc^-1 (frequencies in MHz give
+# seconds).  The paper prints it as 4.148808e9 for a phase with f in MHz and time
+# in microseconds; the two differ by the 1e6 that ``chirp_phase`` applies.
+D_DISP_S_MHZ2 = 4.148808e3
+
+TAPERS = ("none", "hann", "welch")
+
+
+# --------------------------------------------------------------------------
+# Geometry (Sec. 2.1, Sec. 2.3)
+# --------------------------------------------------------------------------
+
+def channel_lower_edges(f_center_mhz: float, bandwidth_mhz: float, n_chan: int):
+    """Lower edge f_k of every channel and the channel width (Sec. 2.1: f_o is the
+    lower edge of the band; channel 0 is the lowest, upper sideband)."""
+    chan_bw = bandwidth_mhz / n_chan
+    f_lo = f_center_mhz - bandwidth_mhz / 2.0 + chan_bw * np.arange(n_chan, dtype=np.float64)
+    return f_lo, chan_bw
+
+
+def dispersion_delay_s(f_mhz, f_ref_mhz, dm: float):
+    """Cold-plasma arrival delay of frequency f relative to f_ref, in seconds
+    (positive when f is below f_ref).  Sec. 1.2: the delay grows as 1/f^2."""
+    f = np.asarray(f_mhz, dtype=np.float64)
+    return D_DISP_S_MHZ2 * dm * (f ** -2 - float(f_ref_mhz) ** -2)
+
+
+def dispersion_samples(f_lo_mhz: float, chan_bw_mhz: float, dm: float) -> float:
+    """Dispersion time across one channel [f_lo, f_lo + chan_bw], in complex
+    samples of that channel (sample rate chan_bw MHz).  Sec. 2.2: this is the
+    length of the impulse response that has to be deconvolved."""
+    t = dispersion_delay_s(f_lo_mhz, f_lo_mhz + chan_bw_mhz, dm)
+    return float(t * chan_bw_mhz * 1e6)
+
+
+def _next_pow2_above(x: float) -> int:
+    n = 1
+    while n <= x:
+        n *= 2
+    return n
+
+
+@dataclass(frozen=True)
+class Geometry:
+    n_chan: int
+    chan_bw_mhz: float
+    f_lo_mhz: np.ndarray      # [C] lower channel edges
+    dm: float
+    n_fft: int                # N
+    n_ov: int                 # samples discarded per segment (overlap)
+    hop: int                  # h = N - n_ov, new samples per segment
+    n_avg: int                # integration length
+    n_disp: float             # dispersion samples of the lowest channel
+    shift: np.ndarray         # [C] int64 alignment shift r_k in integrated samples
+
+
+def plan_geometry(f_center_mhz: float, bandwidth_mhz: float, n_chan: int, dm: float,
+                  n_fft: int = 0, n_avg: int = 1) -> Geometry:
+    """Segment geometry of the per-channel overlap-save.
+
+    * n_d: dispersion samples of the lowest channel (longest smear), Sec. 2.2.
+    * n_ov = ceil(n_d) rounded up to a multiple of n_avg (so every integration
+      window stays inside one segment).
+    * N: given, or (n_fft == 0) the Sec. 2.3 rule -- the smallest power of two
+      greater than twice n_d -- raised if needed so that N > n_ov, N >= 2*n_avg
+      and N >= 64 (the smallest transform the GPU path runs).
+    * r_k = rint(delay of f_k relative to f_0, in integrated samples), Sec. 1.2.
+    """
+    if n_chan <= 0 or n_avg <= 0 or bandwidth_mhz <= 0 or dm < 0:
+        raise ValueError("n_chan, n_avg, bandwidth must be positive and DM >= 0")
+    f_lo, chan_bw = channel_lower_edges(f_center_mhz, bandwidth_mhz, n_chan)
+    n_d = dispersion_samples(float(f_lo[0]), chan_bw, dm)
+    n_ov = int(math.ceil(n_d))
+    n_ov = -(-n_ov // n_avg) * n_avg
+    if n_fft == 0:
+        n_fft = max(_next_pow2_above(2.0 * n_d), _next_pow2_above(n_ov), 64)
+        while n_fft < 2 * n_avg:
+            n_fft *= 2
+    if n_fft & (n_fft - 1) or n_fft <= n_ov:
+        raise ValueError(f"N={n_fft} must be a power of two larger than n_ov={n_ov}")
+    hop = n_fft - n_ov
+    if hop % n_avg:
+        raise ValueError(f"hop {hop} is not a multiple of n_avg {n_avg}")
+    delay = dispersion_delay_s(f_lo, f_lo[0], dm)            # <= 0: higher channels lead
+    shift = np.rint(-delay * chan_bw * 1e6 / n_avg).astype(np.int64)
+    return Geometry(n_chan, chan_bw, f_lo, float(dm), int(n_fft), int(n_ov), int(hop),
+                    int(n_avg), float(n_d), shift)
+
+
+# --------------------------------------------------------------------------
+# The chirp (Sec. 2.1, Eq. 3) and taper (Sec. 2.2)
+# --------------------------------------------------------------------------
+
+def bin_offsets(n_fft: int, chan_bw_mhz: float) -> np.ndarray:
+    """f_l (MHz above the channel's lower edge) of each DFT bin j of a complex
+    baseband channel: numpy's fftfreq order plus half a channel, so f_l is in
+    [0, chan_bw) and the Nyquist bin j = N/2 lands on f_l = 0."""
+    return np.fft.fftfreq(n_fft, d=1.0 / chan_bw_mhz) + chan_bw_mhz / 2.0
+
+
+def chirp_phase(f_lo_mhz, f_l_mhz, dm: float):
+    """Phase (radians) of Eq. 3, the dispersive term of the ISM transfer function:
+    Phi = 2*pi * D * DM * f_l^2 / ((f_l + f_o) * f_o^2), frequencies in MHz."""
+    f_lo = np.asarray(f_lo_mhz, dtype=np.float64)
+    f_l = np.asarray(f_l_mhz, dtype=np.float64)
+    return 2.0 * np.pi * D_DISP_S_MHZ2 * 1e6 * dm * f_l ** 2 / ((f_l + f_lo) * f_lo ** 2)
+
+
+def taper(f_l_mhz, chan_bw_mhz: float, kind: str = "none"):
+    """Frequency-domain window of Sec. 2.2 (the paper names Hann and Welch but
+    prints neither): Hann sin^2(pi x), Welch 1 - (2x - 1)^2, x = f_l / chan_bw."""
+    x = np.asarray(f_l_mhz, dtype=np.float64) / chan_bw_mhz
+    if kind == "none":
+        return np.ones_like(x)
+    if kind == "hann":
+        return np.sin(np.pi * x) ** 2
+    if kind == "welch":
+        return 1.0 - (2.0 * x - 1.0) ** 2
+    raise ValueError(f"unknown taper {kind!r}")
+
+
+def dedispersion_filter(f_lo_mhz: float, chan_bw_mhz: float, dm: float, n_fft: int,
+                        taper_kind: str = "none") -> np.ndarray:
+    """The "chirp function" of Sec. 2.2 for one channel on an N-point grid: the
+    taper times the inverse of Eq. 3's term, conj(H) = exp(-i*Phi)."""
+    f_l = bin_offsets(n_fft, chan_bw_mhz)
+    h_ism = np.exp(1j * chirp_phase(f_lo_mhz, f_l, dm))
+    return np.conj(h_ism) * taper(f_l, chan_bw_mhz, taper_kind)
+
+
+# --------------------------------------------------------------------------
+# Overlap-save deconvolution (Sec. 2.2, Sec. 4.3)
+# --------------------------------------------------------------------------
+
+def dft(x: np.ndarray) -> np.ndarray:
+    """Forward DFT X[j] = sum_n x[n] exp(-2 pi i j n / N) along the last axis."""
+    return np.fft.fft(x, axis=-1)
+
+
+def idft(X: np.ndarray) -> np.ndarray:
+    """Inverse DFT x[n] = (1/N) sum_j X[j] exp(+2 pi i j n / N) along the last axis."""
+    return np.fft.ifft(X, axis=-1)
+
+
+def overlap_save(x: np.ndarray, filt: np.ndarray, n_ov: int,
+                 history: np.ndarray | None = None) -> np.ndarray:
+    """Overlap-save convolution of one channel's complex series with the N-point
+    filter spectrum ``filt`` (Sec. 2.2).
+
+    Segment s takes N consecutive inputs starting n_ov samples before s*h
+    (h = N - n_ov), so consecutive segments overlap by n_ov.  After the forward
+    DFT, the product with the filter and the inverse DFT, the first n_ov outputs
+    are discarded and the remaining h are kept.  The samples before the start of
+    the stream are ``history`` (the last n_ov samples of earlier data), or zeros
+    (Sec. 4.3: the lost samples are prefixed to the next block).
+    Only whole segments are processed: len(x) // h of them.
+    """
+    n_fft = filt.shape[-1]
+    hop = n_fft - n_ov
+    n_seg = x.shape[-1] // hop
+    if history is None:
+        history = np.zeros(n_ov, dtype=np.complex128)
+    xp = np.concatenate([np.asarray(history, dtype=np.complex128),
+                         np.asarray(x, dtype=np.complex128)])
+    out = np.empty(n_seg * hop, dtype=np.complex128)
+    if n_seg == 0:
+        return out
+    segs = np.lib.stride_tricks.sliding_window_view(xp, n_fft)[::hop][:n_seg]
+    y = idft(dft(segs) * filt)
+    out[:] = y[:, n_ov:].reshape(-1)
+    return out
+
+
+# --------------------------------------------------------------------------
+# Detection, integration and alignment (Sec. 3.1, Sec. 4.3, Sec. 1.2)
+# --------------------------------------------------------------------------
+
+def detect(v: np.ndarray) -> np.ndarray:
+    """Square the dedispersed voltage: |v|^2 (Sec. 3.1 "squares it")."""
+    return v.real ** 2 + v.imag ** 2
+
+
+def integrate(p: np.ndarray, n_avg: int) -> np.ndarray:
+    """Sum n_avg consecutive detected samples (Sec. 3.1 "integrates it to a given
+    number of samples"); trailing samples that do not fill a window are dropped."""
+    n = (p.shape[-1] // n_avg) * n_avg
+    return p[..., :n].reshape(*p.shape[:-1], -1, n_avg).sum(axis=-1)
+
+
+def align(intensity: np.ndarray, shift: int) -> np.ndarray:
+    """Delay one channel's integrated series by ``shift`` samples (Sec. 1.2: the
+    sub-bands are aligned in time by applying their dispersion delays);
+    Out[m] = I[m - shift], zero before the series starts."""
+    out = np.zeros_like(intensity)
+    if shift < intensity.shape[-1]:
+        out[shift:] = intensity[: intensity.shape[-1] - shift]
+    return out
+
+
+# --------------------------------------------------------------------------
+# Whole path
+# --------------------------------------------------------------------------
+
+def unpack(vin: np.ndarray) -> np.ndarray:
+    """int8 [T][C][2] (re, im; two's complement, Sec. 2.3 "8-bit integers") to
+    complex128 [C][T]."""
+    if vin.dtype != np.int8 or vin.ndim != 3 or vin.shape[2] != 2:
+        raise ValueError("input must be int8 [T][C][2]")
+    return (vin[:, :, 0].astype(np.float64) + 1j * vin[:, :, 1].astype(np.float64)).T
+
+
+def dedisperse(vin: np.ndarray, geo: Geometry, taper_kind: str = "none",
+               return_voltages: bool = False, channels=None):
+    """The whole hot path on one record, from the start of the stream.
+
+    vin: int8 [T][C][2].  Returns Out float64 [C'][n_out] with
+    n_out = (T // h) * h / n_avg, and, if asked, the dedispersed voltages
+    complex128 [C'][(T // h) * h].  ``channels`` restricts the work to a subset
+    (C' of them) for bounded timing runs.
+    """
+    x = unpack(vin)
+    chans = range(geo.n_chan) if channels is None else list(channels)
+    outs, volts = [], []
+    for k in chans:
+        filt = dedispersion_filter(float(geo.f_lo_mhz[k]), geo.chan_bw_mhz, geo.dm,
+                                   geo.n_fft, taper_kind)
+        v = overlap_save(x[k], filt, geo.n_ov)
+        i_k = integrate(detect(v), geo.n_avg)
+        outs.append(align(i_k, int(geo.shift[k])))
+        if return_voltages:
+            volts.append(v)
+    out = np.stack(outs) if outs else np.zeros((0, 0))
+    if return_voltages:
+        return out, np.stack(volts)
+    return out
+
+
+def rel_rms(a: np.ndarray, b: np.ndarray) -> float:
+    """sqrt(sum |a-b|^2 / sum |b|^2): the error measure stated per output array."""
+    a = np.asarray(a)
+    b = np.asarray(b)
+    den = float(np.sum(np.abs(b) ** 2))
+    num = float(np.sum(np.abs(a - b) ** 2))
+    if den == 0.0:
+        return 0.0 if num == 0.0 else float("inf")
+    return math.sqrt(num / den)

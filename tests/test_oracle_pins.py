@@ -1,0 +1,258 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+brute-force sums, closed forms, the textbook cold-plasma delay law, linear
+convolution, and the constants the paper prints.  CPU only."""
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate as sp_integrate
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+# textbook dispersion delay, written independently of the oracle's units:
+# t = 4.148808 ms * DM * nu_GHz^-2
+K_DM_MS_GHZ2 = 4.148808
+
+
+def textbook_delay_s(nu_mhz, dm):
+    return K_DM_MS_GHZ2 * 1e-3 * dm * (np.asarray(nu_mhz) / 1e3) ** -2
+
+
+# ---------------------------------------------------------------- DFT step
+
+@pytest.mark.parametrize("n", [8, 16, 64, 128])
+def test_dft_matches_brute_force_sum(n):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    jj, nn = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    fwd = (np.exp(-2j * np.pi * jj * nn / n) * x[None, :]).sum(axis=1)
+    inv = (np.exp(2j * np.pi * jj * nn / n) * fwd[None, :]).sum(axis=1) / n
+    assert np.max(np.abs(O.dft(x) - fwd)) < 1e-12 * n
+    assert np.max(np.abs(O.idft(fwd) - inv)) < 1e-12 * n
+    assert np.max(np.abs(inv - x)) < 1e-12 * n
+
+
+def test_parseval():
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(4096) + 1j * rng.standard_normal(4096)
+    X = O.dft(x)
+    assert math.isclose(np.sum(np.abs(x) ** 2), np.sum(np.abs(X) ** 2) / x.size, rel_tol=1e-12)
+
+
+# ---------------------------------------------------------------- chirp (Eq. 3)
+
+@pytest.mark.parametrize("f_lo,dm", [(309.0, 50.0), (134.0, 100.0), (550.0, 35.0), (317.0, 10.0)])
+def test_chirp_phase_is_integrated_group_delay(f_lo, dm):
+    """d(Phi)/df / 2pi is the arrival-time difference between the channel's lower
+    edge and f, so Phi(f_l) = 2 pi * integral_0^{f_l} [t(f_o) - t(f_o + u)] du."""
+    for f_l in (0.001, 0.01, 0.03125, 0.0625, 0.09765625):
+        def dt(u_mhz):
+            return textbook_delay_s(f_lo, dm) - textbook_delay_s(f_lo + u_mhz, dm)
+        val, _ = sp_integrate.quad(dt, 0.0, f_l, epsabs=0, epsrel=1e-13)
+        expect = 2 * np.pi * val * 1e6          # seconds * MHz -> cycles
+        got = O.chirp_phase(f_lo, f_l, dm)
+        assert got == pytest.approx(expect, rel=1e-10)
+
+
+def test_chirp_unit_modulus_and_inverse():
+    filt = O.dedispersion_filter(309.0, 0.0625, 50.0, 8192)
+    assert np.max(np.abs(np.abs(filt) - 1.0)) < 1e-14
+    back = O.dedispersion_filter(309.0, 0.0625, -50.0, 8192)
+    assert np.max(np.abs(filt * back - 1.0)) < 1e-12
+    assert np.max(np.abs(O.dedispersion_filter(309.0, 0.0625, 0.0, 256) - 1.0)) == 0.0
+
+
+def test_bin_offsets_cover_channel():
+    f_l = O.bin_offsets(8, 0.0625)
+    step = 0.0625 / 8
+    # bins 0..3 are the upper half, the Nyquist bin 4 is the channel's lower edge
+    assert np.allclose(f_l, [0.03125 + step * j for j in (0, 1, 2, 3, -4, -3, -2, -1)], atol=0)
+    assert f_l[4] == 0.0 and f_l.min() == 0.0 and f_l.max() < 0.0625
+
+
+def test_taper_shapes():
+    x = np.array([0.0, 0.25, 0.5, 0.75]) * 0.0625
+    assert np.allclose(O.taper(x, 0.0625, "hann"), [0.0, 0.5, 1.0, 0.5], atol=1e-15)
+    assert np.allclose(O.taper(x, 0.0625, "welch"), [0.0, 0.75, 1.0, 0.75], atol=1e-15)
+    assert np.all(O.taper(x, 0.0625, "none") == 1.0)
+
+
+def test_dedispersion_response_is_causal_with_textbook_mean_delay():
+    """The dedispersion filter delays the upper part of the channel (it undoes the
+    ISM's advance of high frequencies): its impulse response lives at positive
+    lags, centred on the band-mean of t(f_o) - t(f) (textbook delay law)."""
+    f_lo, bw, dm, n = 309.0, 0.0625, 50.0, 8192
+    resp = O.idft(O.dedispersion_filter(f_lo, bw, dm, n))
+    p = np.abs(resp) ** 2
+    lag = np.arange(n)
+    lag = np.where(lag < n // 2, lag, lag - n)          # signed lag
+    centroid = np.sum(lag * p) / np.sum(p)
+    f = f_lo + bw * (np.arange(4096) + 0.5) / 4096
+    mean_delay_samples = np.mean(textbook_delay_s(f_lo, dm) - textbook_delay_s(f, dm)) * bw * 1e6
+    assert mean_delay_samples > 20
+    assert centroid == pytest.approx(mean_delay_samples, rel=0.02)
+    n_d = O.dispersion_samples(f_lo, bw, dm)
+    inside = p[(lag >= -2) & (lag <= math.ceil(n_d) + 2)].sum() / p.sum()
+    assert inside > 0.95
+
+
+# ---------------------------------------------------------------- overlap-save
+
+@pytest.mark.parametrize("n,n_ov", [(64, 12), (256, 64), (128, 0), (64, 48)])
+def test_overlap_save_equals_linear_convolution(n, n_ov):
+    rng = np.random.default_rng(n + n_ov)
+    hop = n - n_ov
+    x = rng.standard_normal(7 * hop + 5) + 1j * rng.standard_normal(7 * hop + 5)
+    g = rng.standard_normal(n_ov + 1) + 1j * rng.standard_normal(n_ov + 1)
+    filt = O.dft(np.concatenate([g, np.zeros(n - g.size)]))
+    got = O.overlap_save(x, filt, n_ov)
+    want = np.convolve(x, g)[: 7 * hop]
+    assert got.size == 7 * hop
+    assert np.max(np.abs(got - want)) < 1e-11
+
+
+def test_overlap_save_history_continues_the_stream():
+    rng = np.random.default_rng(11)
+    n, n_ov = 128, 40
+    hop = n - n_ov
+    x = rng.standard_normal(10 * hop) + 1j * rng.standard_normal(10 * hop)
+    filt = O.dedispersion_filter(317.0, 0.0625, 400.0, n)
+    whole = O.overlap_save(x, filt, n_ov)
+    a = O.overlap_save(x[: 4 * hop], filt, n_ov)
+    b = O.overlap_save(x[4 * hop:], filt, n_ov, history=x[4 * hop - n_ov: 4 * hop])
+    assert np.max(np.abs(np.concatenate([a, b]) - whole)) < 1e-12
+
+
+def test_periodic_dispersed_impulse_is_recovered_exactly():
+    """An N-periodic input makes each overlap-save segment a cyclic shift of one
+    period, so dispersing with exp(+i Phi) and dedispersing must return the
+    impulse train at its own sample, to rounding."""
+    f_lo, bw, dm, n, n_ov, t0 = 317.0, 0.0625, 10.0, 64, 12, 23
+    period = np.zeros(n, complex)
+    period[t0] = 1.0
+    ism = np.conj(O.dedispersion_filter(f_lo, bw, dm, n))      # exp(+i Phi)
+    disp = O.idft(O.dft(period) * ism)
+    x = np.tile(disp, 20)
+    v = O.overlap_save(x, O.dedispersion_filter(f_lo, bw, dm, n), n_ov)
+    want = np.tile(period, 20)[: v.size]
+    hop = n - n_ov
+    assert np.max(np.abs(v[hop:] - want[hop:])) < 1e-12      # after the zero-history segment
+
+
+# ---------------------------------------------------------------- detect / integrate / align
+
+def test_dm_zero_is_integrated_power_exactly():
+    geo = O.plan_geometry(325.0, 16.0, 8, 0.0, 64, 4)
+    assert geo.n_ov == 0 and geo.hop == 64 and np.all(geo.shift == 0)
+    rng = np.random.default_rng(5)
+    vin = rng.integers(-127, 128, size=(64 * 5, 8, 2)).astype(np.int8)
+    out = O.dedisperse(vin, geo)
+    x = vin.astype(np.float64)
+    want = (x[..., 0] ** 2 + x[..., 1] ** 2).T.reshape(8, -1, 4).sum(-1)
+    assert np.max(np.abs(out - want)) < 1e-9 * np.max(want)
+
+
+def test_integrate_and_align():
+    p = np.arange(12, dtype=float)
+    assert np.array_equal(O.integrate(p, 4), [6.0, 22.0, 38.0])
+    assert np.array_equal(O.align(np.array([1.0, 2.0, 3.0, 4.0]), 1), [0.0, 1.0, 2.0, 3.0])
+    assert np.array_equal(O.align(np.array([1.0, 2.0]), 5), [0.0, 0.0])
+
+
+def test_shift_matches_textbook_delay():
+    geo = O.plan_geometry(325.0, 32.0, 512, 50.0, 8192, 16)
+    nu = geo.f_lo_mhz
+    t_s = 1.0 / (geo.chan_bw_mhz * 1e6)
+    want = np.rint((textbook_delay_s(nu[0], 50.0) - textbook_delay_s(nu, 50.0)) / t_s / 16)
+    assert np.array_equal(geo.shift, want.astype(np.int64))
+    assert geo.shift[0] == 0 and np.all(np.diff(geo.shift) >= 0)
+
+
+def test_geometry_of_the_named_shapes():
+    """n_ov / N / h of the 16 MHz, 32 MHz and 150 MHz shapes, and the Sec. 2.3 rule."""
+    g = O.plan_geometry(325.0, 16.0, 256, 10.0, 64, 4)
+    assert (g.n_ov, g.hop, int(g.shift.max())) == (12, 52, 603)
+    g = O.plan_geometry(325.0, 32.0, 512, 50.0, 8192, 16)
+    assert (g.n_ov, g.hop, int(g.shift.max())) == (64, 8128, 1516)
+    g = O.plan_geometry(150.0, 32.0, 512, 100.0, 65536, 16)
+    assert (g.n_ov, g.hop) == (1360, 64176)
+    # Sec. 2.3: smallest power of two greater than twice the dispersion samples
+    g = O.plan_geometry(325.0, 32.0, 512, 50.0, 0, 16)
+    assert g.n_fft == 128 and g.n_fft > 2 * g.n_disp and g.n_fft // 2 <= 2 * g.n_disp
+    with pytest.raises(ValueError):
+        O.plan_geometry(325.0, 32.0, 512, 50.0, 48, 16)
+
+
+# ---------------------------------------------------------------- physics, end to end
+
+def test_dispersed_impulse_aligns_across_channels():
+    """Disperse one broadband impulse with the full cold-plasma phase
+    2 pi k DM / f (not Eq. 3: this phase also carries the delay term), then run the
+    whole oracle path.  Every channel must peak at its lower edge's arrival time,
+    and after alignment all channels must peak at the same output sample."""
+    f_c, bw, n_chan, dm, n_fft, n_avg = 325.0, 4.0, 64, 10.0, 64, 4
+    geo = O.plan_geometry(f_c, bw, n_chan, dm, n_fft, n_avg)
+    T, t_e = 4096, 3000
+    chan_bw = bw / n_chan
+    f_lo = f_c - bw / 2 + chan_bw * np.arange(n_chan)
+    nu = np.fft.fftfreq(T, d=1.0 / chan_bw)              # baseband offsets, MHz
+    x = np.zeros((n_chan, T), complex)
+    k_s = K_DM_MS_GHZ2 * 1e-3 * 1e6                      # s MHz^2
+    for k in range(n_chan):
+        f = f_lo[k] + chan_bw / 2 + nu                   # sky frequency of each bin, MHz
+        # 2 pi k DM / f, minus its value's linear part at the band bottom so the
+        # record stays short: arrival time relative to channel 0's lower edge
+        phase = 2 * np.pi * k_s * dm * 1e6 * (1.0 / f + f / f_lo[0] ** 2)
+        spec = np.exp(-2j * np.pi * np.fft.fftfreq(T) * t_e * 1.0) * np.exp(1j * phase)
+        x[k] = np.fft.ifft(spec)
+    scale = 100.0 / np.max(np.abs(x))
+    vin = np.zeros((T, n_chan, 2))
+    vin[..., 0] = (x.real * scale).T
+    vin[..., 1] = (x.imag * scale).T
+    vin = np.rint(vin).astype(np.int8)
+    out, v = O.dedisperse(vin, geo, return_voltages=True)
+    for k in range(n_chan):
+        arrival = t_e + (textbook_delay_s(f_lo[k], dm) - textbook_delay_s(f_lo[0], dm)) * chan_bw * 1e6
+        pk = int(np.argmax(np.abs(v[k]) ** 2))
+        assert abs(pk - arrival) <= 1.0, (k, pk, arrival)
+        e = np.abs(v[k]) ** 2
+        assert e[pk - 2: pk + 3].sum() > 0.5 * e.sum()
+    peaks = np.argmax(out, axis=1)
+    assert np.all(np.abs(peaks - t_e // n_avg) <= 1), peaks
+
+
+# ---------------------------------------------------------------- constants the paper prints
+
+def test_paper_constants():
+    with open(os.path.join(GOLDEN, "paper_constants.json")) as fh:
+        g = json.load(fh)
+    assert O.D_DISP_S_MHZ2 * 1e6 == pytest.approx(g["D_eq3"]["value"], rel=1e-12)
+    # Sec. 1.3: recording rates of 120 GB/h (16 MHz) and 240 GB/h (32 MHz);
+    # complex int8 channel samples at C * chan_bw per second, 2 bytes each.
+    for bw, key in ((16.0, "rate_16MHz_GB_per_h"), (32.0, "rate_32MHz_GB_per_h"),
+                    (200.0, "rate_200MHz_GB_per_h")):
+        gb_h = bw * 1e6 * 2 * 3600 / 1e9
+        assert gb_h == pytest.approx(g[key]["value"], rel=0.05)
+
+
+def test_oracle_digest_unchanged():
+    """Regression guard: the oracle on the seeded 16 MHz input still gives the
+    digest that tests/golden/make_golden.py wrote."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(GOLDEN, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    with open(os.path.join(GOLDEN, "tiny_oracle_digest.json")) as fh:
+        want = json.load(fh)
+    got = mg.digest()
+    assert got["n_out"] == want["n_out"] and got["argmax"] == want["argmax"]
+    assert got["input_sum"] == want["input_sum"] and got["input_sq_sum"] == want["input_sq_sum"]
+    assert np.allclose(got["row_sums"], want["row_sums"], rtol=1e-12, atol=0)
+    assert np.allclose(got["row_max"], want["row_max"], rtol=1e-12, atol=0)
+    for k, v in want["samples"].items():
+        assert np.allclose(got["samples"][k], v, rtol=1e-12, atol=1e-9)
