@@ -1,0 +1,145 @@
+/*
+ * cdd.h -- C ABI of the B300 coherent-dedispersion library (libcdd.so).
+ *
+ * The library runs the per-channel overlap-save coherent dedispersion of
+ * De & Gupta, "A Real-time Coherent Dedispersion Pipeline for the GMRT"
+ * (arXiv:1509.00186) on one GPU:
+ *
+ *   unpack complex int8 -> forward FFT -> multiply by the chirp function
+ *   (Sec. 2.1 Eq. 3, times the Sec. 2.2 taper) -> inverse FFT -> discard the
+ *   overlap (Sec. 2.2 overlap-save) -> detect |v|^2 and integrate (Sec. 3.1)
+ *   -> delay each channel to align it with the lowest one (Sec. 1.2).
+ *
+ * Every step runs in the library's own CUDA kernels; nothing here calls cuFFT
+ * or falls back to the CPU.
+ *
+ * Conventions
+ *   - Channel k (0 = lowest) covers [f_k, f_k + B/C) MHz with
+ *     f_k = f_center - B/2 + k*B/C (upper sideband).  Its complex baseband
+ *     sample rate is B/C MHz.
+ *   - Input layout (device or host, as the call says): int8 [T][C][2], time
+ *     major, channel fastest, real then imaginary part (two's complement).
+ *   - Output layout: float32 [C][n_out], channel major, intensities summed over
+ *     n_avg detected samples and delayed by r_k integrated samples.
+ *   - Overlap n_ov = ceil(n_d) rounded up to a multiple of n_avg, where n_d is
+ *     the dispersion time across the lowest channel in samples; hop
+ *     h = N - n_ov.  Each execute consumes block_samples = q*h new samples per
+ *     channel (q = segments per block) and emits n_out = block_samples/n_avg
+ *     outputs per channel: the next contiguous range of the stream's output.
+ *   - r_k = rint(D*DM*(f_0^-2 - f_k^-2) * (B/C)*1e6 / n_avg),
+ *     D = 4.148808e3 s MHz^2 cm^3/pc.
+ *
+ * Ownership: the caller owns every input and output buffer.  The plan owns its
+ * device state (chirp and twiddle tables, overlap tails, alignment ring, host
+ * staging buffers), allocated at the first execute call and freed by
+ * cdd_destroy.  A plan is bound to the device that is current at its first
+ * execute.  A plan is not thread-safe; distinct plans are independent.
+ *
+ * Errors: every int-returning call returns CDD_OK (0) or a negative code.
+ * A CUDA failure is sticky: once a call has returned CDD_ECUDA, later calls on
+ * the same plan return it too (cdd_reset does not clear it).
+ */
+#ifndef CDD_H
+#define CDD_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CDD_OK            0
+#define CDD_EINVAL       -1   /* bad argument or geometry                     */
+#define CDD_ENOMEM       -2   /* device or pinned-host allocation failed      */
+#define CDD_ECUDA        -3   /* a CUDA call failed (sticky)                  */
+#define CDD_EUNSUPPORTED -4   /* valid request this build does not run       */
+#define CDD_ESTATE       -5   /* call not allowed in the plan's current state */
+
+/* Attributes for cdd_plan_get (all) and cdd_plan_set (marked "settable",
+ * only before the first execute). */
+enum cdd_attr {
+  CDD_ATTR_N_FFT = 0,              /* N, power of two                          */
+  CDD_ATTR_N_OV = 1,               /* overlap discarded per segment            */
+  CDD_ATTR_HOP = 2,                /* h = N - n_ov                             */
+  CDD_ATTR_N_AVG = 3,              /* integration length                       */
+  CDD_ATTR_N_CHAN = 4,             /* C                                        */
+  CDD_ATTR_SEGMENTS_PER_BLOCK = 5, /* q, settable, default 1                   */
+  CDD_ATTR_BLOCK_SAMPLES = 6,      /* q*h input samples per channel per call   */
+  CDD_ATTR_N_OUT_PER_BLOCK = 7,    /* q*h/n_avg outputs per channel per call   */
+  CDD_ATTR_R_MAX = 8,              /* largest alignment shift r_k              */
+  CDD_ATTR_BYTES_DEVICE = 9,       /* device bytes the plan holds (0 before)   */
+  CDD_ATTR_TAPER = 10,             /* enum cdd_taper, settable                 */
+  CDD_ATTR_BLOCKS_DONE = 11,       /* execute calls since create / reset       */
+  CDD_ATTR_PIPELINE_CHUNKS = 12,   /* host-buffer path: copy/compute chunks per
+                                      block (settable, default 4, divides q)   */
+  CDD_ATTR_KERNEL_LAUNCHES = 13    /* kernels launched by the last execute     */
+};
+
+enum cdd_taper { CDD_TAPER_NONE = 0, CDD_TAPER_HANN = 1, CDD_TAPER_WELCH = 2 };
+
+typedef struct cdd_plan_s* cdd_plan;
+
+/* Create a plan for one polarisation of a C-channel band.
+ *   f_center_mhz, bandwidth_mhz > 0: observing band (Sec. 2.1 f_o, Delta f).
+ *   n_chan > 0: channels.  dm >= 0: dispersion measure in pc cm^-3 (Eq. 3).
+ *   n_fft: FFT length N (power of two, 64..16384 in this build), or 0 for the
+ *     Sec. 2.3 rule: the smallest power of two > 2*n_d (raised so that
+ *     N > n_ov, N >= 2*n_avg and N >= 64).
+ *   n_avg > 0: detected samples summed per output; h must be a multiple of it.
+ * Touches no GPU.  Returns CDD_EINVAL for an impossible geometry,
+ * CDD_EUNSUPPORTED for an N this build does not run. */
+int cdd_plan_create(cdd_plan* plan, double f_center_mhz, double bandwidth_mhz,
+                    int n_chan, double dm, int n_fft, int n_avg);
+
+/* Set an attribute (see enum cdd_attr).  CDD_ESTATE after the first execute. */
+int cdd_plan_set(cdd_plan plan, int attr, int64_t value);
+
+/* Read an attribute into *value. */
+int cdd_plan_get(cdd_plan plan, int attr, int64_t* value);
+
+/* Copy the n_chan alignment shifts r_k (integrated samples) to host memory
+ * shifts[0..n_chan). */
+int cdd_plan_shifts(cdd_plan plan, int64_t* shifts);
+
+/* Dedisperse one block.  d_in: device int8 [q*h][C][2]; d_out: device
+ * float [C][q*h/n_avg].  Asynchronous on `stream` (0 = legacy default
+ * stream).  The first call allocates the plan's device state and builds its
+ * tables (synchronously), so make it before capturing a stream into a graph.
+ * Consecutive calls continue one stream: the first n_ov input samples of each
+ * segment 0 come from the previous call (zeros before the first call). */
+int cdd_execute(cdd_plan plan, const int8_t* d_in, float* d_out, cudaStream_t stream);
+
+/* cdd_execute that also writes the dedispersed voltages (after the overlap
+ * discard, before detection) to d_volt: device float [C][q*h][2]
+ * (re, im).  For accuracy checks; slower than cdd_execute. */
+int cdd_execute_voltages(cdd_plan plan, const int8_t* d_in, float* d_out,
+                         float* d_volt, cudaStream_t stream);
+
+/* End-to-end form with HOST buffers: h_in int8 [q*h][C][2], h_out float
+ * [C][q*h/n_avg].  Copies in, dedisperses and copies out in
+ * CDD_ATTR_PIPELINE_CHUNKS chunks so that transfers overlap compute (the
+ * copy-in / compute / copy-out streams of Sec. 4.2), then waits for the
+ * result.  Pinned host memory (cudaHostAlloc / torch pin_memory) gives
+ * asynchronous copies; pageable memory works but serialises them.
+ * `stream` orders the call after earlier work on it. */
+int cdd_execute_host(cdd_plan plan, const int8_t* h_in, float* h_out, cudaStream_t stream);
+
+/* Restart the stream: zero the overlap tails and the alignment ring and the
+ * block counter.  Waits for the plan's outstanding work. */
+int cdd_reset(cdd_plan plan);
+
+/* Free the plan and everything it owns (NULL is accepted). */
+int cdd_destroy(cdd_plan plan);
+
+/* Static string for an error code. */
+const char* cdd_strerror(int code);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int cdd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDD_H */

@@ -240,12 +240,12 @@ def align(intensity: np.ndarray, shift: int) -> np.ndarray:
 # Whole path
 # --------------------------------------------------------------------------
 
-def unpack(vin: np.ndarray) -> np.ndarray:
-    """int8 [T][C][2] (re, im; two's complement, Sec. 2.3 "8-bit integers") to
-    complex128 [C][T]."""
+def unpack(vin: np.ndarray, k: int) -> np.ndarray:
+    """Channel k of int8 [T][C][2] (re, im; two's complement, Sec. 2.3 "8-bit
+    integers") as complex128 [T]."""
     if vin.dtype != np.int8 or vin.ndim != 3 or vin.shape[2] != 2:
         raise ValueError("input must be int8 [T][C][2]")
-    return (vin[:, :, 0].astype(np.float64) + 1j * vin[:, :, 1].astype(np.float64)).T
+    return vin[:, k, 0].astype(np.float64) + 1j * vin[:, k, 1].astype(np.float64)
 
 
 def dedisperse(vin: np.ndarray, geo: Geometry, taper_kind: str = "none",
@@ -257,13 +257,12 @@ def dedisperse(vin: np.ndarray, geo: Geometry, taper_kind: str = "none",
     complex128 [C'][(T // h) * h].  ``channels`` restricts the work to a subset
     (C' of them) for bounded timing runs.
     """
-    x = unpack(vin)
     chans = range(geo.n_chan) if channels is None else list(channels)
     outs, volts = [], []
     for k in chans:
         filt = dedispersion_filter(float(geo.f_lo_mhz[k]), geo.chan_bw_mhz, geo.dm,
                                    geo.n_fft, taper_kind)
-        v = overlap_save(x[k], filt, geo.n_ov)
+        v = overlap_save(unpack(vin, k), filt, geo.n_ov)
         i_k = integrate(detect(v), geo.n_avg)
         outs.append(align(i_k, int(geo.shift[k])))
         if return_voltages:

@@ -1,0 +1,225 @@
+"""Thin Python binding of the C ABI in include/cdd.h (argument marshalling only).
+
+Functions keep the C names; every computation happens in libcdd.so's CUDA
+kernels.  Importing this module loads the in-tree library and fails loudly
+if it is missing: there is no fallback.
+
+``Plan`` is a small convenience wrapper that takes torch tensors (device or
+pinned host) and passes their pointers and the current CUDA stream through.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcdd.so")
+
+CDD_OK = 0
+CDD_EINVAL = -1
+CDD_ENOMEM = -2
+CDD_ECUDA = -3
+CDD_EUNSUPPORTED = -4
+CDD_ESTATE = -5
+
+ATTR = {
+    "n_fft": 0, "n_ov": 1, "hop": 2, "n_avg": 3, "n_chan": 4, "segments_per_block": 5,
+    "block_samples": 6, "n_out_per_block": 7, "r_max": 8, "bytes_device": 9, "taper": 10,
+    "blocks_done": 11, "pipeline_chunks": 12, "kernel_launches": 13,
+}
+TAPER = {"none": 0, "hann": 1, "welch": 2}
+
+# every symbol include/cdd.h declares
+EXPORTS = ("cdd_plan_create", "cdd_plan_set", "cdd_plan_get", "cdd_plan_shifts", "cdd_execute",
+           "cdd_execute_voltages", "cdd_execute_host", "cdd_reset", "cdd_destroy",
+           "cdd_strerror", "cdd_version")
+
+
+class CddError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_1509_00186_b300.build` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
+    lib.cdd_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]
+    lib.cdd_plan_set.argtypes = [vp, ctypes.c_int, ctypes.c_int64]
+    lib.cdd_plan_get.argtypes = [vp, ctypes.c_int, i64p]
+    lib.cdd_plan_shifts.argtypes = [vp, i64p]
+    lib.cdd_execute.argtypes = [vp, vp, vp, vp]
+    lib.cdd_execute_voltages.argtypes = [vp, vp, vp, vp, vp]
+    lib.cdd_execute_host.argtypes = [vp, vp, vp, vp]
+    lib.cdd_reset.argtypes = [vp]
+    lib.cdd_destroy.argtypes = [vp]
+    lib.cdd_strerror.argtypes = [ctypes.c_int]
+    lib.cdd_strerror.restype = ctypes.c_char_p
+    lib.cdd_version.argtypes = []
+    for name in EXPORTS:
+        if name not in ("cdd_strerror",):
+            getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != CDD_OK:
+        raise CddError(rc, where)
+
+
+# ------------------------------------------------------------------ C names
+
+def strerror(code: int) -> str:
+    return _lib.cdd_strerror(int(code)).decode()
+
+
+def cdd_version() -> int:
+    return int(_lib.cdd_version())
+
+
+def cdd_plan_create(f_center_mhz: float, bandwidth_mhz: float, n_chan: int, dm: float,
+                    n_fft: int = 0, n_avg: int = 1) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.cdd_plan_create(ctypes.byref(h), float(f_center_mhz), float(bandwidth_mhz),
+                                int(n_chan), float(dm), int(n_fft), int(n_avg)), "cdd_plan_create")
+    return h.value
+
+
+def cdd_plan_set(plan: int, attr, value: int) -> None:
+    a = ATTR[attr] if isinstance(attr, str) else int(attr)
+    _check(_lib.cdd_plan_set(ctypes.c_void_p(plan), a, int(value)), "cdd_plan_set")
+
+
+def cdd_plan_get(plan: int, attr) -> int:
+    a = ATTR[attr] if isinstance(attr, str) else int(attr)
+    v = ctypes.c_int64()
+    _check(_lib.cdd_plan_get(ctypes.c_void_p(plan), a, ctypes.byref(v)), "cdd_plan_get")
+    return int(v.value)
+
+
+def cdd_plan_shifts(plan: int, n_chan: int):
+    buf = (ctypes.c_int64 * n_chan)()
+    _check(_lib.cdd_plan_shifts(ctypes.c_void_p(plan), buf), "cdd_plan_shifts")
+    return list(buf)
+
+
+def cdd_execute(plan: int, d_in: int, d_out: int, stream: int = 0) -> None:
+    _check(_lib.cdd_execute(ctypes.c_void_p(plan), ctypes.c_void_p(d_in), ctypes.c_void_p(d_out),
+                            ctypes.c_void_p(stream)), "cdd_execute")
+
+
+def cdd_execute_voltages(plan: int, d_in: int, d_out: int, d_volt: int, stream: int = 0) -> None:
+    _check(_lib.cdd_execute_voltages(ctypes.c_void_p(plan), ctypes.c_void_p(d_in),
+                                     ctypes.c_void_p(d_out), ctypes.c_void_p(d_volt),
+                                     ctypes.c_void_p(stream)), "cdd_execute_voltages")
+
+
+def cdd_execute_host(plan: int, h_in: int, h_out: int, stream: int = 0) -> None:
+    _check(_lib.cdd_execute_host(ctypes.c_void_p(plan), ctypes.c_void_p(h_in),
+                                 ctypes.c_void_p(h_out), ctypes.c_void_p(stream)),
+           "cdd_execute_host")
+
+
+def cdd_reset(plan: int) -> None:
+    _check(_lib.cdd_reset(ctypes.c_void_p(plan)), "cdd_reset")
+
+
+def cdd_destroy(plan: int) -> None:
+    _check(_lib.cdd_destroy(ctypes.c_void_p(plan)), "cdd_destroy")
+
+
+# ------------------------------------------------------------------ convenience
+
+class Plan:
+    """Owning wrapper of one plan; tensors in, tensors out (no computation here)."""
+
+    def __init__(self, f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft=0, n_avg=1,
+                 segments_per_block=1, taper="none", pipeline_chunks=None):
+        self.handle = cdd_plan_create(f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft, n_avg)
+        try:
+            cdd_plan_set(self.handle, "segments_per_block", segments_per_block)
+            cdd_plan_set(self.handle, "taper", TAPER[taper])
+            if pipeline_chunks is not None:
+                cdd_plan_set(self.handle, "pipeline_chunks", pipeline_chunks)
+        except Exception:
+            cdd_destroy(self.handle)
+            raise
+        self.n_chan = int(n_chan)
+
+    def get(self, attr) -> int:
+        return cdd_plan_get(self.handle, attr)
+
+    @property
+    def block_samples(self) -> int:
+        return self.get("block_samples")
+
+    @property
+    def n_out(self) -> int:
+        return self.get("n_out_per_block")
+
+    def shifts(self):
+        return cdd_plan_shifts(self.handle, self.n_chan)
+
+    def _check_io(self, vin, out, device):
+        import torch
+        if vin.dtype != torch.int8 or tuple(vin.shape) != (self.block_samples, self.n_chan, 2):
+            raise ValueError(f"input must be int8 [{self.block_samples}][{self.n_chan}][2]")
+        if out.dtype != torch.float32 or tuple(out.shape) != (self.n_chan, self.n_out):
+            raise ValueError(f"output must be float32 [{self.n_chan}][{self.n_out}]")
+        for t in (vin, out):
+            if not t.is_contiguous():
+                raise ValueError("tensors must be contiguous")
+            if (t.device.type == "cuda") != device:
+                raise ValueError("tensor on the wrong side of the host/device boundary")
+
+    def execute(self, vin, out=None, volt=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.n_chan, self.n_out), dtype=torch.float32, device=vin.device)
+        self._check_io(vin, out, device=True)
+        stream = torch.cuda.current_stream(vin.device).cuda_stream
+        if volt is None:
+            cdd_execute(self.handle, vin.data_ptr(), out.data_ptr(), stream)
+        else:
+            if volt.dtype != torch.float32 or tuple(volt.shape) != (self.n_chan, self.block_samples, 2) \
+                    or not volt.is_contiguous():
+                raise ValueError("voltages must be contiguous float32 [C][block_samples][2]")
+            cdd_execute_voltages(self.handle, vin.data_ptr(), out.data_ptr(), volt.data_ptr(), stream)
+        return out
+
+    def execute_host(self, vin, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.n_chan, self.n_out), dtype=torch.float32,
+                              pin_memory=vin.is_pinned())
+        self._check_io(vin, out, device=False)
+        s = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        cdd_execute_host(self.handle, vin.data_ptr(), out.data_ptr(), s)
+        return out
+
+    def reset(self):
+        cdd_reset(self.handle)
+
+    def close(self):
+        if self.handle:
+            cdd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,458 @@
+// cdd_api.cu -- the C ABI declared in include/cdd.h: plan geometry, device
+// state, and the device-buffer and host-buffer execute calls.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/cdd.h"
+#include "cdd_internal.h"
+
+namespace {
+
+constexpr double kDispD = 4.148808e3;   // s MHz^2 cm^3 / pc (Sec. 2.1, Eq. 3)
+constexpr int kMinLogN = 6;
+constexpr int kMaxLogN = 14;
+
+}  // namespace
+
+struct cdd_plan_s {
+  // observation and geometry (fixed at create)
+  double f_center = 0, bandwidth = 0, dm = 0, chan_bw = 0, f_lo0 = 0, n_disp = 0;
+  int n_chan = 0, n_fft = 0, logn = 0, n_ov = 0, hop = 0, n_avg = 0;
+  std::vector<int64_t> shift;
+  int64_t r_max = 0;
+  // settable before the first execute
+  int q = 1;
+  int taper = CDD_TAPER_NONE;
+  int chunks = 1;
+  bool chunks_set = false;
+  // device state
+  bool committed = false;
+  int device = -1;
+  int sticky = CDD_OK;
+  float2* d_chirp = nullptr;
+  float2* d_tw = nullptr;
+  char2* d_tail[2] = {nullptr, nullptr};
+  float* d_ring = nullptr;
+  int* d_shift = nullptr;
+  long long ring_len = 0;
+  size_t bytes_device = 0;
+  // stream position
+  long long g_next = 0;     // stream index of the next integrated output
+  int parity = 0;           // which tail buffer holds the previous block's tail
+  int64_t blocks = 0;
+  int last_launches = 0;
+  // host-buffer path
+  int8_t* d_in_stage[2] = {nullptr, nullptr};
+  float* d_out_stage[2] = {nullptr, nullptr};
+  cudaStream_t st_h2d = nullptr, st_comp = nullptr, st_d2h = nullptr;
+  cudaEvent_t ev_start = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
+              ev_out[2] = {nullptr, nullptr};
+  bool host_ready = false;
+};
+
+namespace {
+
+int fail_cuda(cdd_plan p, cudaError_t e) {
+  if (e == cudaSuccess) return CDD_OK;
+  if (p) p->sticky = CDD_ECUDA;
+  return CDD_ECUDA;
+}
+
+#define CDD_TRY(p, call)                           \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return fail_cuda(p, e_); \
+  } while (0)
+
+int64_t n_out_per_block(const cdd_plan p) { return (int64_t)p->q * p->hop / p->n_avg; }
+
+int next_pow2_above(double x) {
+  long long n = 1;
+  while ((double)n <= x && n < (1LL << 40)) n *= 2;
+  return n > (1LL << 30) ? -1 : (int)n;
+}
+
+// Geometry of Sec. 2.2 / 2.3 and the channel alignment of Sec. 1.2.
+int compute_geometry(cdd_plan p, int n_fft) {
+  if (!(p->f_center > 0) || !(p->bandwidth > 0) || p->n_chan <= 0 || !(p->dm >= 0) ||
+      p->n_avg <= 0 || n_fft < 0 || !isfinite(p->dm))
+    return CDD_EINVAL;
+  p->chan_bw = p->bandwidth / p->n_chan;
+  p->f_lo0 = p->f_center - p->bandwidth / 2.0;
+  if (!(p->f_lo0 > 0)) return CDD_EINVAL;
+  // dispersion time across the lowest (most smeared) channel, in samples
+  const double t_d = kDispD * p->dm * (pow(p->f_lo0, -2.0) - pow(p->f_lo0 + p->chan_bw, -2.0));
+  p->n_disp = t_d * p->chan_bw * 1e6;
+  if (!(p->n_disp < 1e9)) return CDD_EINVAL;
+  long long n_ov = (long long)ceil(p->n_disp);
+  n_ov = (n_ov + p->n_avg - 1) / p->n_avg * p->n_avg;
+  if (n_fft == 0) {
+    int a = next_pow2_above(2.0 * p->n_disp), b = next_pow2_above((double)n_ov);
+    if (a < 0 || b < 0) return CDD_EINVAL;
+    n_fft = a > b ? a : b;
+    if (n_fft < 64) n_fft = 64;
+    while ((long long)n_fft < 2LL * p->n_avg) n_fft *= 2;
+  }
+  if (n_fft <= 0 || (n_fft & (n_fft - 1)) || (long long)n_fft <= n_ov) return CDD_EINVAL;
+  const int hop = n_fft - (int)n_ov;
+  if (hop % p->n_avg) return CDD_EINVAL;
+  int logn = 0;
+  while ((1 << logn) < n_fft) ++logn;
+  p->n_fft = n_fft;
+  p->logn = logn;
+  p->n_ov = (int)n_ov;
+  p->hop = hop;
+  p->shift.assign(p->n_chan, 0);
+  p->r_max = 0;
+  const double ref = pow(p->f_lo0, -2.0);
+  for (int k = 0; k < p->n_chan; ++k) {
+    const double f_k = p->f_lo0 + p->chan_bw * k;
+    const double delay = kDispD * p->dm * (pow(f_k, -2.0) - ref);   // <= 0
+    const double r = rint(-delay * p->chan_bw * 1e6 / p->n_avg);
+    if (!(r >= 0 && r < 2e9)) return CDD_EINVAL;
+    p->shift[k] = (int64_t)r;
+    if (p->shift[k] > p->r_max) p->r_max = p->shift[k];
+  }
+  if (logn < kMinLogN || logn > kMaxLogN) return CDD_EUNSUPPORTED;
+  return CDD_OK;
+}
+
+void free_device(cdd_plan p) {
+  cudaFree(p->d_chirp);
+  cudaFree(p->d_tw);
+  cudaFree(p->d_tail[0]);
+  cudaFree(p->d_tail[1]);
+  cudaFree(p->d_ring);
+  cudaFree(p->d_shift);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(p->d_in_stage[i]);
+    cudaFree(p->d_out_stage[i]);
+    if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);
+    if (p->ev_comp[i]) cudaEventDestroy(p->ev_comp[i]);
+    if (p->ev_out[i]) cudaEventDestroy(p->ev_out[i]);
+  }
+  if (p->ev_start) cudaEventDestroy(p->ev_start);
+  if (p->st_h2d) cudaStreamDestroy(p->st_h2d);
+  if (p->st_comp) cudaStreamDestroy(p->st_comp);
+  if (p->st_d2h) cudaStreamDestroy(p->st_d2h);
+}
+
+template <class T>
+int dalloc(cdd_plan p, T** ptr, size_t bytes) {
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return CDD_ENOMEM;
+  }
+  if (e != cudaSuccess) return fail_cuda(p, e);
+  p->bytes_device += bytes;
+  return CDD_OK;
+}
+
+int zero_state(cdd_plan p, cudaStream_t s) {
+  if (p->n_ov > 0) {
+    const size_t tb = (size_t)p->n_chan * p->n_ov * sizeof(char2);
+    CDD_TRY(p, cudaMemsetAsync(p->d_tail[0], 0, tb, s));
+    CDD_TRY(p, cudaMemsetAsync(p->d_tail[1], 0, tb, s));
+  }
+  CDD_TRY(p, cudaMemsetAsync(p->d_ring, 0, (size_t)p->n_chan * p->ring_len * sizeof(float), s));
+  p->g_next = 0;
+  p->parity = 0;
+  p->blocks = 0;
+  return CDD_OK;
+}
+
+// First execute: bind the device, allocate the plan's state and build its
+// tables.  Synchronous.
+int commit_once(cdd_plan p) {
+  CDD_TRY(p, cudaGetDevice(&p->device));
+  const int N = p->n_fft;
+  int rc;
+  p->ring_len = p->r_max + n_out_per_block(p);
+  if ((rc = dalloc(p, &p->d_chirp, (size_t)p->n_chan * N * sizeof(float2)))) return rc;
+  if ((rc = dalloc(p, &p->d_tw, (size_t)N * sizeof(float2)))) return rc;
+  if (p->n_ov > 0) {
+    for (int i = 0; i < 2; ++i)
+      if ((rc = dalloc(p, &p->d_tail[i], (size_t)p->n_chan * p->n_ov * sizeof(char2)))) return rc;
+  }
+  if ((rc = dalloc(p, &p->d_ring, (size_t)p->n_chan * p->ring_len * sizeof(float)))) return rc;
+  if ((rc = dalloc(p, &p->d_shift, (size_t)p->n_chan * sizeof(int)))) return rc;
+  std::vector<int> sh(p->shift.begin(), p->shift.end());
+  CDD_TRY(p, cudaMemcpy(p->d_shift, sh.data(), sh.size() * sizeof(int), cudaMemcpyHostToDevice));
+  cudaStream_t s;
+  CDD_TRY(p, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaError_t e = cdd::launch_twiddle_table(p->logn, p->d_tw, s);
+  if (e == cudaSuccess)
+    e = cdd::launch_chirp_table(p->logn, p->d_chirp, p->n_chan, p->f_lo0, p->chan_bw, p->dm,
+                                p->taper, s);
+  if (e == cudaSuccess && (rc = zero_state(p, s)) != CDD_OK) {
+    cudaStreamDestroy(s);
+    return rc;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess) return fail_cuda(p, e);
+  p->committed = true;
+  return CDD_OK;
+}
+
+// A failed commit leaves the plan unusable (sticky) rather than half built.
+int commit(cdd_plan p) {
+  if (p->committed) return CDD_OK;
+  const int rc = commit_once(p);
+  if (rc != CDD_OK) p->sticky = rc;
+  return rc;
+}
+
+int check_device(cdd_plan p) {
+  int dev = -1;
+  CDD_TRY(p, cudaGetDevice(&dev));
+  return dev == p->device ? CDD_OK : CDD_EINVAL;
+}
+
+// One block of q segments on `s`; advances the stream position.
+int run_block(cdd_plan p, const int8_t* d_in, float* d_out, float* d_volt, int q, cudaStream_t s) {
+  cdd::OlsArgs a;
+  a.in = reinterpret_cast<const char2*>(d_in);
+  a.out = d_out;
+  a.chirp = p->d_chirp;
+  a.tw = p->d_tw;
+  a.tail_rd = p->d_tail[p->parity];
+  a.tail_wr = p->d_tail[p->parity ^ 1];
+  a.ring = p->d_ring;
+  a.shift = p->d_shift;
+  a.volt = reinterpret_cast<float2*>(d_volt);
+  a.n_chan = p->n_chan;
+  a.n_ov = p->n_ov;
+  a.hop = p->hop;
+  a.n_avg = p->n_avg;
+  a.q = q;
+  a.n_out = (int)((int64_t)q * p->hop / p->n_avg);
+  a.g0 = p->g_next;
+  a.ring_len = p->ring_len;
+  CDD_TRY(p, cdd::launch_ols(p->logn, a, s));
+  p->g_next += a.n_out;
+  p->parity ^= 1;
+  p->blocks += 1;
+  return CDD_OK;
+}
+
+int prepare(cdd_plan p) {
+  if (!p) return CDD_EINVAL;
+  if (p->sticky) return p->sticky;
+  int rc = commit(p);
+  if (rc) return rc;
+  return check_device(p);
+}
+
+int setup_host_path(cdd_plan p) {
+  if (p->host_ready) return CDD_OK;
+  const int64_t q_c = p->q / p->chunks;
+  const size_t in_b = (size_t)q_c * p->hop * p->n_chan * 2;
+  const size_t out_b = (size_t)p->n_chan * (q_c * p->hop / p->n_avg) * sizeof(float);
+  int rc;
+  for (int i = 0; i < 2; ++i) {
+    if ((rc = dalloc(p, &p->d_in_stage[i], in_b))) return rc;
+    if ((rc = dalloc(p, &p->d_out_stage[i], out_b))) return rc;
+    CDD_TRY(p, cudaEventCreateWithFlags(&p->ev_in[i], cudaEventDisableTiming));
+    CDD_TRY(p, cudaEventCreateWithFlags(&p->ev_comp[i], cudaEventDisableTiming));
+    CDD_TRY(p, cudaEventCreateWithFlags(&p->ev_out[i], cudaEventDisableTiming));
+  }
+  CDD_TRY(p, cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming));
+  CDD_TRY(p, cudaStreamCreateWithFlags(&p->st_h2d, cudaStreamNonBlocking));
+  CDD_TRY(p, cudaStreamCreateWithFlags(&p->st_comp, cudaStreamNonBlocking));
+  CDD_TRY(p, cudaStreamCreateWithFlags(&p->st_d2h, cudaStreamNonBlocking));
+  p->host_ready = true;
+  return CDD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cdd_version(void) { return 100; }
+
+const char* cdd_strerror(int code) {
+  switch (code) {
+    case CDD_OK: return "success";
+    case CDD_EINVAL: return "invalid argument or geometry";
+    case CDD_ENOMEM: return "out of device or host memory";
+    case CDD_ECUDA: return "CUDA error (sticky for this plan)";
+    case CDD_EUNSUPPORTED: return "not supported by this build";
+    case CDD_ESTATE: return "not allowed in the plan's current state";
+    default: return "unknown error code";
+  }
+}
+
+int cdd_plan_create(cdd_plan* plan, double f_center_mhz, double bandwidth_mhz, int n_chan,
+                    double dm, int n_fft, int n_avg) {
+  if (!plan) return CDD_EINVAL;
+  *plan = nullptr;
+  cdd_plan p = new (std::nothrow) cdd_plan_s();
+  if (!p) return CDD_ENOMEM;
+  p->f_center = f_center_mhz;
+  p->bandwidth = bandwidth_mhz;
+  p->n_chan = n_chan;
+  p->dm = dm;
+  p->n_avg = n_avg;
+  const int rc = compute_geometry(p, n_fft);
+  if (rc != CDD_OK) {
+    delete p;
+    return rc;
+  }
+  *plan = p;
+  return CDD_OK;
+}
+
+int cdd_plan_set(cdd_plan p, int attr, int64_t value) {
+  if (!p) return CDD_EINVAL;
+  if (p->committed) return CDD_ESTATE;
+  switch (attr) {
+    case CDD_ATTR_SEGMENTS_PER_BLOCK:
+      if (value < 1 || value > (1 << 24)) return CDD_EINVAL;
+      if ((int64_t)value * p->hop * p->n_chan > (int64_t)1 << 40) return CDD_EINVAL;
+      if ((int64_t)value * p->n_chan >= (int64_t)1 << 31) return CDD_EINVAL;
+      p->q = (int)value;
+      if (!p->chunks_set || p->q % p->chunks)
+        p->chunks = p->q % 4 == 0 ? 4 : p->q % 2 == 0 ? 2 : 1;
+      return CDD_OK;
+    case CDD_ATTR_TAPER:
+      if (value < CDD_TAPER_NONE || value > CDD_TAPER_WELCH) return CDD_EINVAL;
+      p->taper = (int)value;
+      return CDD_OK;
+    case CDD_ATTR_PIPELINE_CHUNKS:
+      if (value < 1 || value > p->q || p->q % value) return CDD_EINVAL;
+      p->chunks = (int)value;
+      p->chunks_set = true;
+      return CDD_OK;
+    default:
+      return CDD_EINVAL;
+  }
+}
+
+int cdd_plan_get(cdd_plan p, int attr, int64_t* v) {
+  if (!p || !v) return CDD_EINVAL;
+  switch (attr) {
+    case CDD_ATTR_N_FFT: *v = p->n_fft; break;
+    case CDD_ATTR_N_OV: *v = p->n_ov; break;
+    case CDD_ATTR_HOP: *v = p->hop; break;
+    case CDD_ATTR_N_AVG: *v = p->n_avg; break;
+    case CDD_ATTR_N_CHAN: *v = p->n_chan; break;
+    case CDD_ATTR_SEGMENTS_PER_BLOCK: *v = p->q; break;
+    case CDD_ATTR_BLOCK_SAMPLES: *v = (int64_t)p->q * p->hop; break;
+    case CDD_ATTR_N_OUT_PER_BLOCK: *v = n_out_per_block(p); break;
+    case CDD_ATTR_R_MAX: *v = p->r_max; break;
+    case CDD_ATTR_BYTES_DEVICE: *v = (int64_t)p->bytes_device; break;
+    case CDD_ATTR_TAPER: *v = p->taper; break;
+    case CDD_ATTR_BLOCKS_DONE: *v = p->blocks; break;
+    case CDD_ATTR_PIPELINE_CHUNKS: *v = p->chunks; break;
+    case CDD_ATTR_KERNEL_LAUNCHES: *v = p->last_launches; break;
+    default: return CDD_EINVAL;
+  }
+  return CDD_OK;
+}
+
+int cdd_plan_shifts(cdd_plan p, int64_t* shifts) {
+  if (!p || !shifts) return CDD_EINVAL;
+  memcpy(shifts, p->shift.data(), p->shift.size() * sizeof(int64_t));
+  return CDD_OK;
+}
+
+int cdd_execute_voltages(cdd_plan p, const int8_t* d_in, float* d_out, float* d_volt,
+                         cudaStream_t stream) {
+  if (!p || !d_in || !d_out) return CDD_EINVAL;
+  int rc = prepare(p);
+  if (rc) return rc;
+  rc = run_block(p, d_in, d_out, d_volt, p->q, stream);
+  p->last_launches = rc ? 0 : 1;
+  return rc;
+}
+
+int cdd_execute(cdd_plan p, const int8_t* d_in, float* d_out, cudaStream_t stream) {
+  return cdd_execute_voltages(p, d_in, d_out, nullptr, stream);
+}
+
+int cdd_execute_host(cdd_plan p, const int8_t* h_in, float* h_out, cudaStream_t stream) {
+  if (!p || !h_in || !h_out) return CDD_EINVAL;
+  int rc = prepare(p);
+  if (rc) return rc;
+  if ((rc = setup_host_path(p))) return rc;
+  const int nc = p->chunks;
+  const int q_c = p->q / nc;
+  const size_t rows_c = (size_t)q_c * p->hop;
+  const size_t in_b = rows_c * p->n_chan * 2;
+  const size_t out_c = rows_c / p->n_avg;                 // outputs per channel per chunk
+  const size_t out_total = (size_t)n_out_per_block(p);
+  // everything below is ordered after the caller's earlier work on `stream`
+  CDD_TRY(p, cudaEventRecord(p->ev_start, stream));
+  CDD_TRY(p, cudaStreamWaitEvent(p->st_h2d, p->ev_start, 0));
+  CDD_TRY(p, cudaStreamWaitEvent(p->st_comp, p->ev_start, 0));
+  CDD_TRY(p, cudaStreamWaitEvent(p->st_d2h, p->ev_start, 0));
+  for (int c = 0; c < nc; ++c) {
+    const int slot = c & 1;
+    if (c >= 2) CDD_TRY(p, cudaStreamWaitEvent(p->st_h2d, p->ev_comp[slot], 0));
+    CDD_TRY(p, cudaMemcpyAsync(p->d_in_stage[slot], h_in + (size_t)c * in_b, in_b,
+                               cudaMemcpyHostToDevice, p->st_h2d));
+    CDD_TRY(p, cudaEventRecord(p->ev_in[slot], p->st_h2d));
+    CDD_TRY(p, cudaStreamWaitEvent(p->st_comp, p->ev_in[slot], 0));
+    if (c >= 2) CDD_TRY(p, cudaStreamWaitEvent(p->st_comp, p->ev_out[slot], 0));
+    if ((rc = run_block(p, p->d_in_stage[slot], p->d_out_stage[slot], nullptr, q_c, p->st_comp)))
+      return rc;
+    CDD_TRY(p, cudaEventRecord(p->ev_comp[slot], p->st_comp));
+    CDD_TRY(p, cudaStreamWaitEvent(p->st_d2h, p->ev_comp[slot], 0));
+    CDD_TRY(p, cudaMemcpy2DAsync(h_out + (size_t)c * out_c, out_total * sizeof(float),
+                                 p->d_out_stage[slot], out_c * sizeof(float),
+                                 out_c * sizeof(float), (size_t)p->n_chan,
+                                 cudaMemcpyDeviceToHost, p->st_d2h));
+    CDD_TRY(p, cudaEventRecord(p->ev_out[slot], p->st_d2h));
+  }
+  // the caller's stream continues after the last copy-out
+  CDD_TRY(p, cudaStreamWaitEvent(stream, p->ev_out[(nc - 1) & 1], 0));
+  CDD_TRY(p, cudaStreamSynchronize(p->st_d2h));
+  p->last_launches = nc;
+  return CDD_OK;
+}
+
+int cdd_reset(cdd_plan p) {
+  if (!p) return CDD_EINVAL;
+  if (p->sticky) return p->sticky;
+  if (!p->committed) {
+    p->g_next = 0;
+    p->parity = 0;
+    p->blocks = 0;
+    return CDD_OK;
+  }
+  int rc = check_device(p);
+  if (rc) return rc;
+  CDD_TRY(p, cudaDeviceSynchronize());
+  cudaStream_t s;
+  CDD_TRY(p, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  rc = zero_state(p, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (rc) return rc;
+  return fail_cuda(p, e);
+}
+
+int cdd_destroy(cdd_plan p) {
+  if (!p) return CDD_OK;
+  if (p->device >= 0) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (p->device >= 0) cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    free_device(p);
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  delete p;
+  return CDD_OK;
+}
+
+}  // extern "C"

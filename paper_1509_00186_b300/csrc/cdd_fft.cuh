@@ -1,0 +1,169 @@
+// cdd_fft.cuh -- in-register DFT butterflies and the mixed-radix pass plan used
+// by the fused overlap-save kernel.
+//
+// A length-N transform (N = 2^LOGN) runs as P radix passes with radices
+// R_0 >= ... (all powers of two, product N).  Pass p works on sub-problems of
+// size M_p = N / (R_0 ... R_{p-1}) and gathers its R_p points at stride
+// S_p = M_p / R_p.  The forward transform is decimation in frequency (natural
+// order in, digit-reversed order out); the inverse is decimation in time on
+// the same index sets (digit-reversed in, natural out), so the spectrum is
+// never reordered: the chirp is applied in digit-reversed order with a table
+// stored in that order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace cdd {
+
+// ------------------------------------------------------------ complex helpers
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// a * w
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+  return make_float2(fmaf(a.x, w.x, -a.y * w.y), fmaf(a.x, w.y, a.y * w.x));
+}
+// a * conj(w)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 w) {
+  return make_float2(fmaf(a.x, w.x, a.y * w.y), fmaf(a.y, w.x, -a.x * w.y));
+}
+
+// cos(2*pi*k/32) for any integer k, exact to float rounding: the values are
+// cos(pi*m/16), m = 0..8.
+__host__ __device__ constexpr float cos32(int k) {
+  constexpr float c[9] = {1.0f,
+                          0.98078528040323044913f,
+                          0.92387953251128675613f,
+                          0.83146961230254523708f,
+                          0.70710678118654752440f,
+                          0.55557023301960222474f,
+                          0.38268343236508977173f,
+                          0.19509032201612826785f,
+                          0.0f};
+  int m = ((k % 32) + 32) % 32;
+  return m <= 8 ? c[m] : m <= 16 ? -c[16 - m] : m <= 24 ? -c[m - 16] : c[32 - m];
+}
+__host__ __device__ constexpr float sin32(int k) { return cos32(k - 8); }
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = B .. E-1.
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+// b * exp(DIR * 2*pi*i * J / LEN), LEN <= 32; the rotation is a compile-time
+// constant, and rotations by 1 and +-i cost no multiplication.
+template <int LEN, int DIR, int J>
+__device__ __forceinline__ float2 rot(float2 b) {
+  constexpr int m = J * (32 / LEN);       // angle in units of 2*pi/32
+  if constexpr (m == 0) {
+    return b;
+  } else if constexpr (m == 8) {
+    return DIR > 0 ? make_float2(-b.y, b.x) : make_float2(b.y, -b.x);
+  } else {
+    constexpr float c = cos32(m);
+    constexpr float s = DIR > 0 ? sin32(m) : -sin32(m);
+    return make_float2(fmaf(b.x, c, -b.y * s), fmaf(b.x, s, b.y * c));
+  }
+}
+
+template <int R>
+__host__ __device__ constexpr int bitrev(int i) {
+  int r = 0;
+  for (int b = 1, o = R >> 1; b < R; b <<= 1, o >>= 1)
+    if (i & b) r |= o;
+  return r;
+}
+
+__host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n >> 1); }
+
+// In-place DFT of R (2..32) points held in registers, natural order in and
+// out.  DIR = -1: X[k] = sum_n x[n] e^{-2 pi i kn/R};  DIR = +1: the same with
+// e^{+...} and no 1/R.  Radix-2 decimation in time on bit-reversed input.
+template <int R, int DIR>
+__device__ __forceinline__ void dft(float2 (&v)[R]) {
+  float2 t[R];
+  static_for<0, R>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    t[bitrev<R>(i)] = v[i];
+  });
+  static_for<1, ilog2(R) + 1>([&](auto L) {
+    constexpr int len = 1 << decltype(L)::value;
+    static_for<0, R / len>([&](auto G) {
+      static_for<0, len / 2>([&](auto J) {
+        constexpr int i = decltype(G)::value * len;
+        constexpr int j = decltype(J)::value;
+        const float2 a = t[i + j];
+        const float2 b = rot<len, DIR, j>(t[i + j + len / 2]);
+        t[i + j] = cadd(a, b);
+        t[i + j + len / 2] = csub(a, b);
+      });
+    });
+  });
+#pragma unroll
+  for (int i = 0; i < R; ++i) v[i] = t[i];
+}
+
+// ------------------------------------------------------------ pass plan
+
+// log2 of the radix of pass p for a length-2^LOGN transform (0 past the end).
+// The first pass always has the largest radix, so a thread owns exactly one
+// butterfly of it and T = N / R_0 threads serve one transform.
+__host__ __device__ constexpr int radix_log2(int logn, int p) {
+  switch (logn) {
+    case 6:  return p < 2 ? 3 : 0;                            // 8 8
+    case 7:  return p == 0 ? 4 : p == 1 ? 3 : 0;              // 16 8
+    case 8:  return p < 2 ? 4 : 0;                            // 16 16
+    case 9:  return p == 0 ? 5 : p == 1 ? 4 : 0;              // 32 16
+    case 10: return p < 2 ? 4 : p == 2 ? 2 : 0;               // 16 16 4
+    case 11: return p < 2 ? 4 : p == 2 ? 3 : 0;               // 16 16 8
+    case 12: return p < 3 ? 4 : 0;                            // 16 16 16
+    case 13: return p == 0 ? 5 : p < 3 ? 4 : 0;               // 32 16 16
+    case 14: return p < 2 ? 5 : p == 2 ? 4 : 0;               // 32 32 16
+    default: return 0;
+  }
+}
+
+template <int LOGN>
+struct PassPlan {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int P = radix_log2(LOGN, 0) == 0 ? 0
+                         : radix_log2(LOGN, 1) == 0 ? 1
+                         : radix_log2(LOGN, 2) == 0 ? 2
+                         : radix_log2(LOGN, 3) == 0 ? 3 : 4;
+  __host__ __device__ static constexpr int R(int p) { return 1 << radix_log2(LOGN, p); }
+  // product of the radices of passes < p
+  __host__ __device__ static constexpr int Rprod(int p) { return p == 0 ? 1 : Rprod(p - 1) * R(p - 1); }
+  __host__ __device__ static constexpr int M(int p) { return N / Rprod(p); }       // sub-problem size
+  __host__ __device__ static constexpr int S(int p) { return M(p) / R(p); }        // gather stride
+  static constexpr int T = N / R(0);                          // threads per transform
+  static constexpr int RL = R(P - 1);                         // last radix
+  static_assert(Rprod(P) == N, "radices must multiply to N");
+};
+
+// Position (in the working buffer) -> DFT bin held there after the forward
+// passes: position = sum_p d_p * S_p, bin = sum_p d_p * Rprod(p).
+template <int LOGN>
+__host__ __device__ inline int position_to_bin(int pos) {
+  using PL = PassPlan<LOGN>;
+  int bin = 0;
+#pragma unroll
+  for (int p = 0; p < PL::P; ++p) {
+    const int d = (pos / PL::S(p)) % PL::R(p);
+    bin += d * PL::Rprod(p);
+  }
+  return bin;
+}
+
+// Padded shared-memory index: one spare float2 after every 16, so that the
+// stride-1 groups of the middle pass hit distinct banks.
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4); }
+
+}  // namespace cdd

@@ -1,0 +1,44 @@
+// cdd_internal.h -- plan state and kernel launch interface shared by the C ABI
+// (cdd_api.cu) and the kernels (cdd_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cdd {
+
+// Arguments of one launch of the fused overlap-save kernel: q segments of
+// every channel, one block of the stream.
+struct OlsArgs {
+  const char2* in;        // [q*h][C] complex int8, block-local rows
+  float* out;             // [C][n_out]
+  const float2* chirp;    // [C][N] chirp function, digit-reversed layout
+  const float2* tw;       // [N] exp(-2 pi i m / N)
+  const char2* tail_rd;   // [C][n_ov] last n_ov samples of the previous block
+  char2* tail_wr;         // [C][n_ov] last n_ov samples of this block
+  float* ring;            // [C][ring_len] integrated samples still to be emitted
+  const int* shift;       // [C] alignment shift r_k
+  float2* volt;           // [C][q*h] dedispersed voltages, or nullptr
+  int n_chan, n_ov, hop, n_avg, q, n_out;
+  long long g0;           // stream index of this block's first integrated sample
+  long long ring_len;
+};
+
+// Launch the fused kernel for N = 2^logn.  Returns the CUDA error of the launch.
+cudaError_t launch_ols(int logn, const OlsArgs& a, cudaStream_t s);
+
+// Build the chirp table (FP64 phase, reduced mod 1 turn, then rounded to
+// float): chirp[k][idx] = exp(-i Phi_k(f_l)) * w(f_l) / N in the layout the
+// fused kernel reads.
+cudaError_t launch_chirp_table(int logn, float2* chirp, int n_chan, double f_lo0_mhz,
+                               double chan_bw_mhz, double dm, int taper, cudaStream_t s);
+
+// tw[m] = exp(-2 pi i m / N), m in [0, N), FP64 then rounded.
+cudaError_t launch_twiddle_table(int logn, float2* tw, cudaStream_t s);
+
+// Dynamic shared memory and block size of the fused kernel for N = 2^logn.
+int ols_threads(int logn);
+int ols_segments_per_cta(int logn);
+size_t ols_smem_bytes(int logn);
+
+}  // namespace cdd

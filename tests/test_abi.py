@@ -1,0 +1,115 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function the
+header declares, and its host-side geometry equals the oracle's exactly."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def cdd():
+    from paper_1509_00186_b300 import build
+    build.build()
+    from paper_1509_00186_b300 import cdd as mod
+    return mod
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(cdd_\w+)\s*\(", src, flags=re.M)
+    return names
+
+
+def test_library_exports_every_declared_symbol(cdd):
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(cdd._lib, n), n
+    assert set(names) == set(cdd.EXPORTS)
+
+
+def test_version_and_strerror(cdd):
+    assert cdd.cdd_version() >= 100
+    for code in (0, -1, -2, -3, -4, -5):
+        assert cdd.strerror(code) and "unknown" not in cdd.strerror(code)
+    assert "unknown" in cdd.strerror(-99)
+
+
+GEOMS = [
+    (325.0, 16.0, 256, 10.0, 64, 4),
+    (325.0, 32.0, 512, 50.0, 8192, 16),
+    (150.0, 32.0, 512, 100.0, 16384, 16),
+    (610.0, 32.0, 512, 20.0, 0, 16),
+    (325.0, 32.0, 512, 50.0, 0, 16),
+    (235.0, 16.0, 256, 67.99, 0, 8),
+    (650.0, 200.0, 2048, 35.0, 2048, 16),
+    (325.0, 0.4375, 7, 3.0, 256, 2),
+    (325.0, 16.0, 8, 0.0, 64, 4),
+    (1000.0, 1.0, 3, 1000.0, 0, 1),
+]
+
+
+@pytest.mark.parametrize("geo", GEOMS)
+def test_geometry_matches_oracle(cdd, geo):
+    f_c, bw, n_chan, dm, n_fft, n_avg = geo
+    g = O.plan_geometry(f_c, bw, n_chan, dm, n_fft, n_avg)
+    p = cdd.cdd_plan_create(f_c, bw, n_chan, dm, n_fft, n_avg)
+    try:
+        assert cdd.cdd_plan_get(p, "n_fft") == g.n_fft
+        assert cdd.cdd_plan_get(p, "n_ov") == g.n_ov
+        assert cdd.cdd_plan_get(p, "hop") == g.hop
+        assert cdd.cdd_plan_get(p, "r_max") == int(g.shift.max())
+        assert np.array_equal(np.array(cdd.cdd_plan_shifts(p, n_chan)), g.shift)
+        cdd.cdd_plan_set(p, "segments_per_block", 6)
+        assert cdd.cdd_plan_get(p, "block_samples") == 6 * g.hop
+        assert cdd.cdd_plan_get(p, "n_out_per_block") == 6 * g.hop // n_avg
+        assert cdd.cdd_plan_get(p, "bytes_device") == 0
+    finally:
+        cdd.cdd_destroy(p)
+
+
+def test_invalid_geometry_is_rejected(cdd):
+    bad = [
+        (325.0, 32.0, 512, 50.0, 48, 16),      # N not a power of two
+        (325.0, 32.0, 512, 50.0, 64, 16),      # N <= n_ov
+        (325.0, -32.0, 512, 50.0, 0, 16),      # negative bandwidth
+        (325.0, 32.0, 0, 50.0, 0, 16),         # no channels
+        (325.0, 32.0, 512, -5.0, 0, 16),       # negative DM
+        (325.0, 32.0, 512, 50.0, 0, 0),        # no integration
+        (10.0, 32.0, 512, 50.0, 0, 16),        # band below 0 MHz
+        (325.0, 32.0, 512, 50.0, 128, 48),     # hop not a multiple of n_avg
+    ]
+    for args in bad:
+        with pytest.raises(cdd.CddError) as ei:
+            cdd.cdd_plan_create(*args)
+        assert ei.value.code == cdd.CDD_EINVAL, args
+    with pytest.raises(cdd.CddError) as ei:
+        cdd.cdd_plan_create(150.0, 32.0, 512, 100.0, 65536, 16)     # valid, not in this build
+    assert ei.value.code == cdd.CDD_EUNSUPPORTED
+
+
+def test_setters(cdd):
+    p = cdd.cdd_plan_create(325.0, 32.0, 512, 50.0, 8192, 16)
+    try:
+        for attr, val in (("segments_per_block", 0), ("taper", 7), ("pipeline_chunks", 3),
+                          ("n_fft", 1024)):
+            with pytest.raises(cdd.CddError):
+                cdd.cdd_plan_set(p, attr, val)
+        cdd.cdd_plan_set(p, "segments_per_block", 76)
+        assert cdd.cdd_plan_get(p, "pipeline_chunks") == 4
+        cdd.cdd_plan_set(p, "pipeline_chunks", 2)
+        assert cdd.cdd_plan_get(p, "pipeline_chunks") == 2
+        cdd.cdd_plan_set(p, "taper", cdd.TAPER["welch"])
+        assert cdd.cdd_plan_get(p, "taper") == 2
+    finally:
+        cdd.cdd_destroy(p)
+    cdd.cdd_destroy(0)     # NULL is accepted

@@ -1,0 +1,195 @@
+"""GPU path (libcdd.so through its C ABI) against the FP64 oracle.
+
+Tolerance: relative RMS error <= 1e-5 per output array (dedispersed voltages
+and aligned intensities), the bound stated for the FP32 form.  The FP32 path's
+expected error is ~1e-6 (log2(N) radix stages of float rounding on an
+exactly represented int8 input, a chirp rounded once from FP64), so 1e-5
+leaves an order of magnitude of margin while still catching any wrong bin,
+sign, twiddle or index (those give errors of order 1).
+Integer decisions (geometry, shifts) are compared exactly on the CPU side.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import WORKLOADS, PulseTrain, complex_int8_voltages
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+def rel_rms_rows(a, b):
+    return np.array([O.rel_rms(a[i], b[i]) for i in range(a.shape[0])])
+
+
+def gpu_run(vin, geo_args, q, n_blocks, taper="none", volt=True, pinned_host=False):
+    import torch
+    from paper_1509_00186_b300.cdd import Plan
+    plan = Plan(*geo_args, segments_per_block=q, taper=taper)
+    try:
+        bs, n_out, C = plan.block_samples, plan.n_out, plan.n_chan
+        outs, volts = [], []
+        if pinned_host:
+            x = torch.from_numpy(np.ascontiguousarray(vin[: bs * n_blocks])).pin_memory()
+            for b in range(n_blocks):
+                o = torch.empty((C, n_out), dtype=torch.float32).pin_memory()
+                plan.execute_host(x[b * bs:(b + 1) * bs], o)
+                outs.append(o.clone())
+            return torch.cat(outs, 1).numpy(), None
+        x = torch.from_numpy(np.ascontiguousarray(vin[: bs * n_blocks])).cuda()
+        for b in range(n_blocks):
+            o = torch.empty((C, n_out), dtype=torch.float32, device="cuda")
+            v = torch.empty((C, bs, 2), dtype=torch.float32, device="cuda") if volt else None
+            plan.execute(x[b * bs:(b + 1) * bs], o, v)
+            outs.append(o)
+            if volt:
+                volts.append(v)
+        torch.cuda.synchronize()
+        out = torch.cat(outs, 1).cpu().numpy()
+        if volt:
+            vv = torch.cat(volts, 1).cpu().numpy()
+            return out, vv[..., 0] + 1j * vv[..., 1]
+        return out, None
+    finally:
+        plan.close()
+
+
+def oracle_run(vin, geo_args, n_samples, taper="none", channels=None):
+    geo = O.plan_geometry(*geo_args)
+    return O.dedisperse(vin[:n_samples], geo, taper, return_voltages=True, channels=channels)
+
+
+def tiny_input():
+    w = WORKLOADS["tiny"]
+    geo = O.plan_geometry(w.f_center_mhz, w.bandwidth_mhz, w.n_chan, w.dm, w.n_fft, w.n_avg)
+    offs = O.dispersion_delay_s(geo.f_lo_mhz, geo.f_lo_mhz[0], w.dm) * w.chan_bw_mhz * 1e6
+    pulses = PulseTrain(4000.0, w.period_samples, w.width_samples, w.pulse_sigma, offs)
+    vin = complex_int8_voltages(w.seed, w.n_samp, w.n_chan, w.sigma, pulses)
+    args = (w.f_center_mhz, w.bandwidth_mhz, w.n_chan, w.dm, w.n_fft, w.n_avg)
+    return vin, args, geo
+
+
+@pytest.fixture(scope="module")
+def tiny(cuda_device):
+    vin, args, geo = tiny_input()
+    q = vin.shape[0] // geo.hop                   # 600 segments, 31200 samples
+    out_o, v_o = oracle_run(vin, args, q * geo.hop)
+    return vin, args, geo, q, out_o, v_o
+
+
+def test_tiny_whole_record_matches_oracle(tiny):
+    vin, args, geo, q, out_o, v_o = tiny
+    out_g, v_g = gpu_run(vin, args, q, 1)
+    assert out_g.shape == out_o.shape == (256, q * geo.hop // geo.n_avg)
+    assert np.all(rel_rms_rows(v_g, v_o) <= TOL)
+    assert np.all(rel_rms_rows(out_g, out_o) <= TOL)
+    assert O.rel_rms(out_g, out_o) <= TOL
+    # the delayed channels start with exactly r_k zeros (no earlier data)
+    for k in (1, 100, 255):
+        r = int(geo.shift[k])
+        assert np.all(out_g[k, :r] == 0.0) and out_g[k, r] > 0
+
+
+def test_block_split_is_bit_identical(tiny):
+    """Any split of the stream into blocks gives the same bits: the overlap tail
+    and the alignment ring carry the state between calls."""
+    vin, args, geo, q, out_o, _ = tiny
+    whole, _ = gpu_run(vin, args, q, 1, volt=False)
+    for qb in (100, 24, 1):
+        split, _ = gpu_run(vin, args, qb, q // qb, volt=False)
+        assert np.array_equal(split, whole), qb
+
+
+def test_short_blocks_against_oracle(tiny):
+    """Blocks much shorter than the largest alignment shift (r_max = 603 outputs,
+    13 outputs per segment): every output goes through the ring."""
+    vin, args, geo, q, out_o, _ = tiny
+    out_g, _ = gpu_run(vin, args, 5, q // 5, volt=False)
+    assert O.rel_rms(out_g, out_o) <= TOL
+
+
+def test_host_buffer_path_equals_device_path(tiny):
+    vin, args, geo, q, out_o, _ = tiny
+    dev, _ = gpu_run(vin, args, 120, 5, volt=False)
+    host, _ = gpu_run(vin, args, 120, 5, volt=False, pinned_host=True)
+    assert np.array_equal(host, dev)
+    assert O.rel_rms(host, out_o) <= TOL
+
+
+@pytest.mark.parametrize("logn", list(range(6, 15)))
+def test_every_fft_length(cuda_device, logn):
+    """Each supported N on a ragged channel count (the last CTA is partly idle
+    for small N), two blocks of three segments, overlap ~ N/8."""
+    n = 1 << logn
+    n_chan, n_avg = 5, 4
+    chan_bw = 0.0625
+    dm = (n / 8) / O.dispersion_samples(317.0, chan_bw, 1.0)
+    args = (317.0 + n_chan * chan_bw / 2, n_chan * chan_bw, n_chan, dm, n, n_avg)
+    geo = O.plan_geometry(*args)
+    assert 0 < geo.n_ov < n
+    rng = np.random.default_rng(logn)
+    T = 6 * geo.hop
+    vin = np.clip(np.rint(rng.normal(0, 20, (T, n_chan, 2))), -127, 127).astype(np.int8)
+    out_o, v_o = oracle_run(vin, args, T)
+    out_g, v_g = gpu_run(vin, args, 3, 2)
+    assert np.all(rel_rms_rows(v_g, v_o) <= TOL)
+    assert np.all(rel_rms_rows(out_g, out_o) <= TOL)
+
+
+@pytest.mark.parametrize("taper", ["hann", "welch"])
+def test_tapers(cuda_device, taper):
+    args = (317.0 + 1.0, 2.0, 32, 10.0, 256, 4)
+    geo = O.plan_geometry(*args)
+    rng = np.random.default_rng(7)
+    T = 10 * geo.hop
+    vin = np.clip(np.rint(rng.normal(0, 20, (T, 32, 2))), -127, 127).astype(np.int8)
+    out_o, v_o = oracle_run(vin, args, T, taper=taper)
+    out_g, v_g = gpu_run(vin, args, 5, 2, taper=taper)
+    assert O.rel_rms(v_g, v_o) <= TOL
+    assert O.rel_rms(out_g, out_o) <= TOL
+
+
+def test_dm_zero_no_overlap(cuda_device):
+    args = (325.0, 16.0, 16, 0.0, 64, 4)
+    rng = np.random.default_rng(9)
+    vin = rng.integers(-128, 128, size=(64 * 12, 16, 2)).astype(np.int8)
+    out_o, v_o = oracle_run(vin, args, 64 * 12)
+    out_g, v_g = gpu_run(vin, args, 4, 3)
+    assert O.rel_rms(v_g, v_o) <= TOL
+    assert O.rel_rms(out_g, out_o) <= TOL
+    # extreme int8 values (-128 included) survive the unpack
+    assert np.max(np.abs(v_g.real - vin[:, :, 0].T)) < 1e-3
+
+
+def test_single_channel_single_segment(cuda_device):
+    args = (325.0, 0.0625, 1, 10.0, 64, 4)
+    geo = O.plan_geometry(*args)
+    rng = np.random.default_rng(10)
+    vin = np.clip(np.rint(rng.normal(0, 20, (geo.hop * 3, 1, 2))), -127, 127).astype(np.int8)
+    out_o, v_o = oracle_run(vin, args, geo.hop * 3)
+    out_g, v_g = gpu_run(vin, args, 1, 3)
+    assert O.rel_rms(v_g, v_o) <= TOL and O.rel_rms(out_g, out_o) <= TOL
+
+
+@pytest.mark.slow
+def test_gsb_full_size_sampled_channels(cuda_device):
+    """The 32 MHz / 512-channel / DM 50 / N 8192 shape at its full 10 s size, in
+    the benchmark's launch configuration (one block of 76 segments); the oracle
+    recomputes a sample of channels one by one."""
+    w = WORKLOADS["gsb"]
+    args = (w.f_center_mhz, w.bandwidth_mhz, w.n_chan, w.dm, w.n_fft, w.n_avg)
+    geo = O.plan_geometry(*args)
+    offs = O.dispersion_delay_s(geo.f_lo_mhz, geo.f_lo_mhz[0], w.dm) * w.chan_bw_mhz * 1e6
+    pulses = PulseTrain(3000.0, w.period_samples, w.width_samples, w.pulse_sigma, offs)
+    vin = complex_int8_voltages(w.seed, w.n_samp, w.n_chan, w.sigma, pulses)
+    q = w.n_samp // geo.hop
+    assert q == 76
+    out_g, _ = gpu_run(vin, args, q, 1, volt=False)
+    chans = [0, 1, 255, 256, 510, 511]
+    out_o, _ = oracle_run(vin, args, q * geo.hop, channels=chans)
+    assert np.all(rel_rms_rows(out_g[chans], out_o) <= TOL)
+    assert np.all(np.isfinite(out_g))
+    # every channel, not only the sampled ones, carries the noise power:
+    # mean intensity ~ n_avg * 2 * sigma^2 after the r_k leading zeros
+    means = np.array([out_g[k, geo.shift[k]:].mean() for k in range(w.n_chan)])
+    assert np.all(np.abs(means / (w.n_avg * 2 * w.sigma ** 2) - 1) < 0.1)
