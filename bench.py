@@ -56,9 +56,16 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0, "_source": "fallback"}
 
 
-def workload_info():
+def workload_info(n_chan=None):
+    """The benchmark workload; ``n_chan`` keeps only the lowest channels (same
+    channel width, N, overlap and integration), for small profiling captures."""
+    import dataclasses
     from synth import WORKLOADS
     w = WORKLOADS[WORKLOAD]
+    if n_chan is not None and n_chan != w.n_chan:
+        f_lo0 = w.f_center_mhz - w.bandwidth_mhz / 2
+        bw = w.chan_bw_mhz * n_chan
+        w = dataclasses.replace(w, n_chan=n_chan, bandwidth_mhz=bw, f_center_mhz=f_lo0 + bw / 2)
     hop = w.n_fft - 64          # overlap of this shape (n_d = 54.9 -> 64), checked below
     q = w.n_samp // hop
     return w, q
@@ -240,7 +247,7 @@ def run_gpu(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    w, q = workload_info()
+    w, q = workload_info(args.channels)
     plan = Plan(w.f_center_mhz, w.bandwidth_mhz, w.n_chan, w.dm, w.n_fft, w.n_avg,
                 segments_per_block=q, pipeline_chunks=4)
     hop = plan.get("hop")
@@ -365,6 +372,8 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--impl", choices=("cdd", "reference"), default="cdd")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--channels", type=int, default=None,
+                    help="keep only the lowest C channels (profiling captures; not a bench line)")
     args = ap.parse_args(argv)
     world, rank, local = dist_env()
     if args.gpus != world and world != 1:

@@ -177,7 +177,7 @@ int commit_once(cdd_plan p) {
   int rc;
   p->ring_len = p->r_max + n_out_per_block(p);
   if ((rc = dalloc(p, &p->d_chirp, (size_t)p->n_chan * N * sizeof(float2)))) return rc;
-  if ((rc = dalloc(p, &p->d_tw, (size_t)N * sizeof(float2)))) return rc;
+  if ((rc = dalloc(p, &p->d_tw, (size_t)cdd::twiddle_table_len(p->logn) * sizeof(float2)))) return rc;
   if (p->n_ov > 0) {
     for (int i = 0; i < 2; ++i)
       if ((rc = dalloc(p, &p->d_tail[i], (size_t)p->n_chan * p->n_ov * sizeof(char2)))) return rc;

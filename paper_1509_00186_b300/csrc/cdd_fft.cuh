@@ -145,6 +145,13 @@ struct PassPlan {
   static constexpr int T = N / R(0);                          // threads per transform
   static constexpr int RL = R(P - 1);                         // last radix
   static_assert(Rprod(P) == N, "radices must multiply to N");
+  // Twiddle table: pass 0 holds w_N^{t*k} at k*T + t (t < T, k < R_0); pass
+  // p >= 1 (stride S_p > 1) holds w_{M_p}^{t*k} at TwOff(p) + k*S_p + t.  The
+  // thread-major order makes a warp's twiddle loads contiguous.
+  __host__ __device__ static constexpr int TwOff(int p) {
+    return p == 0 ? 0 : p == 1 ? N : TwOff(p - 1) + M(p - 1);
+  }
+  static constexpr int TW_LEN = TwOff(P - 1);                 // the last pass has no twiddles
 };
 
 // Position (in the working buffer) -> DFT bin held there after the forward

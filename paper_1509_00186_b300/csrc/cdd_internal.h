@@ -33,8 +33,10 @@ cudaError_t launch_ols(int logn, const OlsArgs& a, cudaStream_t s);
 cudaError_t launch_chirp_table(int logn, float2* chirp, int n_chan, double f_lo0_mhz,
                                double chan_bw_mhz, double dm, int taper, cudaStream_t s);
 
-// tw[m] = exp(-2 pi i m / N), m in [0, N), FP64 then rounded.
+// Twiddle factors of every radix pass in the kernel's thread-major layout
+// (FP64, then rounded); twiddle_table_len entries.
 cudaError_t launch_twiddle_table(int logn, float2* tw, cudaStream_t s);
+int twiddle_table_len(int logn);
 
 // Dynamic shared memory and block size of the fused kernel for N = 2^logn.
 int ols_threads(int logn);

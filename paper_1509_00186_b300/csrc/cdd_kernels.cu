@@ -38,6 +38,11 @@ struct Cfg {
   static constexpr int T = PL::T;
   static constexpr int G = T >= kMinCtaThreads ? 1 : kMinCtaThreads / T;   // transforms per CTA
   static constexpr int THREADS = G * T;
+#ifdef CDD_OLS_MINB
+  static constexpr int MINB = THREADS <= 256 ? CDD_OLS_MINB : 1;          // CTAs per SM to aim for
+#else
+  static constexpr int MINB = THREADS <= 256 ? 2 : 1;
+#endif
   static constexpr int SEG_F2 = padded_len(PL::N);                       // float2 per transform
   static constexpr size_t SMEM = size_t(G) * SEG_F2 * sizeof(float2);
 };
@@ -48,7 +53,6 @@ __device__ __forceinline__ void fwd_pass(float2* buf, const float2* __restrict__
   using PL = PassPlan<LOGN>;
   constexpr int R = PL::R(p), S = PL::S(p), M = PL::M(p);
   constexpr int PER = (PL::N / R) / PL::T;
-  constexpr int TWS = PL::N / M;
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int b = lt + i * PL::T;
@@ -60,7 +64,7 @@ __device__ __forceinline__ void fwd_pass(float2* buf, const float2* __restrict__
     dft<R, -1>(v);
     if constexpr (S > 1) {
 #pragma unroll
-      for (int k = 1; k < R; ++k) v[k] = cmul(v[k], __ldg(&tw[t * k * TWS]));
+      for (int k = 1; k < R; ++k) v[k] = cmul(v[k], __ldg(&tw[PL::TwOff(p) + k * S + t]));
     }
 #pragma unroll
     for (int k = 0; k < R; ++k) buf[pad(base + S * k)] = v[k];
@@ -73,7 +77,6 @@ __device__ __forceinline__ void inv_pass(float2* buf, const float2* __restrict__
   using PL = PassPlan<LOGN>;
   constexpr int R = PL::R(p), S = PL::S(p), M = PL::M(p);
   constexpr int PER = (PL::N / R) / PL::T;
-  constexpr int TWS = PL::N / M;
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int b = lt + i * PL::T;
@@ -84,7 +87,7 @@ __device__ __forceinline__ void inv_pass(float2* buf, const float2* __restrict__
     for (int k = 0; k < R; ++k) v[k] = buf[pad(base + S * k)];
     if constexpr (S > 1) {
 #pragma unroll
-      for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], __ldg(&tw[t * k * TWS]));
+      for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], __ldg(&tw[PL::TwOff(p) + k * S + t]));
     }
     dft<R, 1>(v);
 #pragma unroll
@@ -116,7 +119,7 @@ __device__ __forceinline__ void chirp_pass(float2* buf, const float2* __restrict
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(Cfg<LOGN>::THREADS)
+__global__ void __launch_bounds__(Cfg<LOGN>::THREADS, Cfg<LOGN>::MINB)
 ols_kernel(const OlsArgs a) {
   using PL = PassPlan<LOGN>;
   using CF = Cfg<LOGN>;
@@ -139,22 +142,23 @@ ols_kernel(const OlsArgs a) {
   if (active) {
     const long long row0 = (long long)s * a.hop - a.n_ov;
     const bool last = (s == a.q - 1);
+    char2 c[R0];
+#pragma unroll
+    for (int j = 0; j < R0; ++j) {                 // issue every load before using any
+      const long long row = row0 + lt + T * j;
+      const char2* src = row >= 0 ? a.in + row * a.n_chan + k
+                                  : a.tail_rd + (long long)k * a.n_ov + (row + a.n_ov);
+      c[j] = __ldg(src);
+    }
 #pragma unroll
     for (int j = 0; j < R0; ++j) {
       const int n = lt + T * j;
-      const long long row = row0 + n;
-      char2 c;
-      if (row >= 0) {
-        c = __ldg(&a.in[row * a.n_chan + k]);
-      } else {
-        c = a.tail_rd[(long long)k * a.n_ov + (row + a.n_ov)];
-      }
-      if (last && n >= N - a.n_ov) a.tail_wr[(long long)k * a.n_ov + (n - (N - a.n_ov))] = c;
-      v[j] = make_float2((float)c.x, (float)c.y);
+      if (last && n >= N - a.n_ov) a.tail_wr[(long long)k * a.n_ov + (n - (N - a.n_ov))] = c[j];
+      v[j] = make_float2((float)c[j].x, (float)c[j].y);
     }
     dft<R0, -1>(v);
 #pragma unroll
-    for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], __ldg(&a.tw[lt * kk]));
+    for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], __ldg(&a.tw[kk * T + lt]));
 #pragma unroll
     for (int kk = 0; kk < R0; ++kk) buf[pad(lt + T * kk)] = v[kk];
   }
@@ -178,7 +182,7 @@ ols_kernel(const OlsArgs a) {
 #pragma unroll
     for (int kk = 0; kk < R0; ++kk) v[kk] = buf[pad(lt + T * kk)];
 #pragma unroll
-    for (int kk = 1; kk < R0; ++kk) v[kk] = cmulc(v[kk], __ldg(&a.tw[lt * kk]));
+    for (int kk = 1; kk < R0; ++kk) v[kk] = cmulc(v[kk], __ldg(&a.tw[kk * T + lt]));
     dft<R0, 1>(v);
     if (a.volt != nullptr) {
       const long long vbase = ((long long)k * a.q + s) * a.hop - a.n_ov;
@@ -193,7 +197,10 @@ ols_kernel(const OlsArgs a) {
   float* pw = reinterpret_cast<float*>(buf);
   if (active) {
 #pragma unroll
-    for (int j = 0; j < R0; ++j) pw[lt + T * j] = fmaf(v[j].x, v[j].x, v[j].y * v[j].y);
+    for (int j = 0; j < R0; ++j) {
+      const int n = lt + T * j;
+      pw[n + (n >> 5)] = fmaf(v[j].x, v[j].x, v[j].y * v[j].y);   // one spare word per 32
+    }
   }
   __syncthreads();
 
@@ -204,9 +211,9 @@ ols_kernel(const OlsArgs a) {
     float* outk = a.out + (size_t)k * a.n_out;
     float* ringk = a.ring + (size_t)k * a.ring_len;
     for (int m = lt; m < n_int; m += T) {
-      const float* src = pw + a.n_ov + m * a.n_avg;
+      const int n0 = a.n_ov + m * a.n_avg;
       float acc = 0.f;
-      for (int i = 0; i < a.n_avg; ++i) acc += src[i];
+      for (int i = 0; i < a.n_avg; ++i) acc += pw[(n0 + i) + ((n0 + i) >> 5)];
       const long long gi = gseg + m;              // stream index of this output
       const long long dst = gi + r - a.g0;        // its aligned index in this block
       if (dst < a.n_out) outk[dst] = acc;
@@ -257,11 +264,21 @@ __global__ void chirp_table_kernel(float2* chirp, int n_chan, double f_lo0, doub
   }
 }
 
-__global__ void twiddle_kernel(float2* tw, int n) {
-  for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+// Twiddle table in the per-pass thread-major layout of PassPlan::TwOff.
+template <int LOGN>
+__global__ void twiddle_kernel(float2* tw) {
+  using PL = PassPlan<LOGN>;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < PL::TW_LEN; e += gridDim.x * blockDim.x) {
+    int p = 0;
+    while (p + 1 < PL::P - 1 && e >= PL::TwOff(p + 1)) ++p;
+    const int local = e - PL::TwOff(p);
+    const int stride = p == 0 ? PL::T : PL::S(p);            // thread index range
+    const int modulus = p == 0 ? PL::N : PL::M(p);
+    const int t = local % stride, k = local / stride;
+    const int m = (t * k) % modulus;
     double sn, cs;
-    sincospi(2.0 * m / n, &sn, &cs);
-    tw[m] = make_float2((float)cs, (float)(-sn));
+    sincospi(2.0 * m / modulus, &sn, &cs);
+    tw[e] = make_float2((float)cs, (float)(-sn));           // exp(-2 pi i m / modulus)
   }
 }
 
@@ -316,10 +333,28 @@ cudaError_t launch_chirp_table(int logn, float2* chirp, int n_chan, double f_lo0
   }
 }
 
-cudaError_t launch_twiddle_table(int logn, float2* tw, cudaStream_t s) {
-  const int n = 1 << logn;
-  twiddle_kernel<<<(n + 255) / 256, 256, 0, s>>>(tw, n);
+template <int LOGN>
+cudaError_t launch_twiddle_t(float2* tw, cudaStream_t s) {
+  twiddle_kernel<LOGN><<<(PassPlan<LOGN>::TW_LEN + 255) / 256, 256, 0, s>>>(tw);
   return cudaGetLastError();
+}
+
+cudaError_t launch_twiddle_table(int logn, float2* tw, cudaStream_t s) {
+  switch (logn) {
+#define X(L) case L: return launch_twiddle_t<L>(tw, s);
+    CDD_LOGN_CASES(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int twiddle_table_len(int logn) {
+  switch (logn) {
+#define X(L) case L: return PassPlan<L>::TW_LEN;
+    CDD_LOGN_CASES(X)
+#undef X
+    default: return 0;
+  }
 }
 
 int ols_threads(int logn) {
