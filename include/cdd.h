@@ -55,6 +55,11 @@ extern "C" {
 #define CDD_ECUDA        -3   /* a CUDA call failed (sticky)                  */
 #define CDD_EUNSUPPORTED -4   /* valid request this build does not run       */
 #define CDD_ESTATE       -5   /* call not allowed in the plan's current state */
+#define CDD_ETOOBIG      -6   /* request needs more than the fixed scratch of
+                                 cdd_execute_static                          */
+
+/* Size of the fixed device scratch array behind cdd_execute_static. */
+#define CDD_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
 
 /* Attributes for cdd_plan_get (all) and cdd_plan_set (marked "settable",
  * only before the first execute). */
@@ -124,6 +129,36 @@ int cdd_execute_voltages(cdd_plan plan, const int8_t* d_in, float* d_out,
  * asynchronous copies; pageable memory works but serialises them.
  * `stream` orders the call after earlier work on it. */
 int cdd_execute_host(cdd_plan plan, const int8_t* h_in, float* h_out, cudaStream_t stream);
+
+/* No-allocation form.  The paper has no counterpart: this entry point exists
+ * for callers that must not allocate device memory -- code running where
+ * cudaMalloc is unavailable or forbidden, such as real-time loops that may only
+ * allocate at start-up, callers whose memory is owned by another allocator, or
+ * hosts that link the library into a process with a fixed memory budget.
+ *
+ * It dedisperses ONE block as the first call of a fresh plan with the same
+ * arguments would (zero history before the block; the outputs of the block's
+ * last r_k samples of each channel, which belong to a later block, are
+ * dropped): d_in device int8 [n_seg*h][C][2], d_out device float
+ * [C][n_seg*h/n_avg], h = N - n_ov as in cdd_plan_create.  taper is an
+ * enum cdd_taper.  Asynchronous on `stream`.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its chirp
+ * and twiddle tables, shifts, zero history and alignment spill all live in one
+ * file-scope device array of CDD_STATIC_SCRATCH_BYTES (64 MiB) that every GPU
+ * which loads the library holds until the process exits.  The tables are
+ * rebuilt on every call; the zero history is cleared on every call.  A request
+ * whose tables need more than the array returns CDD_ETOOBIG (the 512-channel,
+ * N = 8192 shape needs about 36 MB).
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current), so make it before any stream capture.  Every call on
+ * a device shares the one array: calls that overlap on the GPU (on different
+ * streams, or from different threads) race on it and give wrong results, so
+ * serialise them. */
+int cdd_execute_static(double f_center_mhz, double bandwidth_mhz, int n_chan, double dm,
+                       int n_fft, int n_avg, int n_seg, int taper, const int8_t* d_in,
+                       float* d_out, cudaStream_t stream);
 
 /* Restart the stream: zero the overlap tails and the alignment ring and the
  * block counter.  Waits for the plan's outstanding work. */

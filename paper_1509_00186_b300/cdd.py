@@ -21,6 +21,8 @@ CDD_ENOMEM = -2
 CDD_ECUDA = -3
 CDD_EUNSUPPORTED = -4
 CDD_ESTATE = -5
+CDD_ETOOBIG = -6
+STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
 
 ATTR = {
     "n_fft": 0, "n_ov": 1, "hop": 2, "n_avg": 3, "n_chan": 4, "segments_per_block": 5,
@@ -31,8 +33,8 @@ TAPER = {"none": 0, "hann": 1, "welch": 2}
 
 # every symbol include/cdd.h declares
 EXPORTS = ("cdd_plan_create", "cdd_plan_set", "cdd_plan_get", "cdd_plan_shifts", "cdd_execute",
-           "cdd_execute_voltages", "cdd_execute_host", "cdd_reset", "cdd_destroy",
-           "cdd_strerror", "cdd_version")
+           "cdd_execute_voltages", "cdd_execute_host", "cdd_execute_static", "cdd_reset",
+           "cdd_destroy", "cdd_strerror", "cdd_version")
 
 
 class CddError(RuntimeError):
@@ -55,6 +57,9 @@ def _load() -> ctypes.CDLL:
     lib.cdd_execute.argtypes = [vp, vp, vp, vp]
     lib.cdd_execute_voltages.argtypes = [vp, vp, vp, vp, vp]
     lib.cdd_execute_host.argtypes = [vp, vp, vp, vp]
+    lib.cdd_execute_static.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, vp, vp, vp]
     lib.cdd_reset.argtypes = [vp]
     lib.cdd_destroy.argtypes = [vp]
     lib.cdd_strerror.argtypes = [ctypes.c_int]
@@ -125,6 +130,16 @@ def cdd_execute_host(plan: int, h_in: int, h_out: int, stream: int = 0) -> None:
     _check(_lib.cdd_execute_host(ctypes.c_void_p(plan), ctypes.c_void_p(h_in),
                                  ctypes.c_void_p(h_out), ctypes.c_void_p(stream)),
            "cdd_execute_host")
+
+
+def cdd_execute_static(f_center_mhz: float, bandwidth_mhz: float, n_chan: int, dm: float,
+                       n_fft: int, n_avg: int, n_seg: int, taper: int, d_in: int, d_out: int,
+                       stream: int = 0) -> None:
+    """One block from a fresh stream without any device allocation (see cdd.h)."""
+    _check(_lib.cdd_execute_static(float(f_center_mhz), float(bandwidth_mhz), int(n_chan),
+                                   float(dm), int(n_fft), int(n_avg), int(n_seg), int(taper),
+                                   ctypes.c_void_p(d_in), ctypes.c_void_p(d_out),
+                                   ctypes.c_void_p(stream)), "cdd_execute_static")
 
 
 def cdd_reset(plan: int) -> None:

@@ -56,6 +56,69 @@ struct cdd_plan_s {
   bool host_ready = false;
 };
 
+namespace cdd {
+
+int64_t shift_of(const Geometry& g, int k) {
+  const double ref = pow(g.f_lo0, -2.0);
+  const double f_k = g.f_lo0 + g.chan_bw * k;
+  const double delay = kDispD * g.dm * (pow(f_k, -2.0) - ref);   // <= 0: f_k arrives first
+  const double r = rint(-delay * g.chan_bw * 1e6 / g.n_avg);
+  return (r >= 0 && r < 2e9) ? (int64_t)r : -1;
+}
+
+static int next_pow2_above(double x) {
+  long long n = 1;
+  while ((double)n <= x && n < (1LL << 40)) n *= 2;
+  return n > (1LL << 30) ? -1 : (int)n;
+}
+
+int geometry(Geometry* g, double f_center, double bandwidth, int n_chan, double dm, int n_fft,
+             int n_avg) {
+  if (!(f_center > 0) || !(bandwidth > 0) || n_chan <= 0 || !(dm >= 0) || n_avg <= 0 ||
+      n_fft < 0 || !isfinite(dm))
+    return CDD_EINVAL;
+  g->f_center = f_center;
+  g->bandwidth = bandwidth;
+  g->dm = dm;
+  g->n_chan = n_chan;
+  g->n_avg = n_avg;
+  g->chan_bw = bandwidth / n_chan;
+  g->f_lo0 = f_center - bandwidth / 2.0;
+  if (!(g->f_lo0 > 0)) return CDD_EINVAL;
+  // dispersion time across the lowest (most smeared) channel, in samples
+  const double t_d = kDispD * dm * (pow(g->f_lo0, -2.0) - pow(g->f_lo0 + g->chan_bw, -2.0));
+  g->n_disp = t_d * g->chan_bw * 1e6;
+  if (!(g->n_disp < 1e9)) return CDD_EINVAL;
+  long long n_ov = (long long)ceil(g->n_disp);
+  n_ov = (n_ov + n_avg - 1) / n_avg * n_avg;
+  if (n_fft == 0) {
+    int a = next_pow2_above(2.0 * g->n_disp), b = next_pow2_above((double)n_ov);
+    if (a < 0 || b < 0) return CDD_EINVAL;
+    n_fft = a > b ? a : b;
+    if (n_fft < 64) n_fft = 64;
+    while ((long long)n_fft < 2LL * n_avg) n_fft *= 2;
+  }
+  if (n_fft <= 0 || (n_fft & (n_fft - 1)) || (long long)n_fft <= n_ov) return CDD_EINVAL;
+  const int hop = n_fft - (int)n_ov;
+  if (hop % n_avg) return CDD_EINVAL;
+  int logn = 0;
+  while ((1 << logn) < n_fft) ++logn;
+  g->n_fft = n_fft;
+  g->logn = logn;
+  g->n_ov = (int)n_ov;
+  g->hop = hop;
+  g->r_max = 0;
+  for (int k = 0; k < n_chan; ++k) {
+    const int64_t r = shift_of(*g, k);
+    if (r < 0) return CDD_EINVAL;
+    if (r > g->r_max) g->r_max = r;
+  }
+  if (logn < kMinLogN || logn > kMaxLogN) return CDD_EUNSUPPORTED;
+  return CDD_OK;
+}
+
+}  // namespace cdd
+
 namespace {
 
 int fail_cuda(cdd_plan p, cudaError_t e) {
@@ -72,54 +135,22 @@ int fail_cuda(cdd_plan p, cudaError_t e) {
 
 int64_t n_out_per_block(const cdd_plan p) { return (int64_t)p->q * p->hop / p->n_avg; }
 
-int next_pow2_above(double x) {
-  long long n = 1;
-  while ((double)n <= x && n < (1LL << 40)) n *= 2;
-  return n > (1LL << 30) ? -1 : (int)n;
-}
-
-// Geometry of Sec. 2.2 / 2.3 and the channel alignment of Sec. 1.2.
+// Geometry of Sec. 2.2 / 2.3 and the channel alignment of Sec. 1.2, held by
+// the plan (with its per-channel shifts).
 int compute_geometry(cdd_plan p, int n_fft) {
-  if (!(p->f_center > 0) || !(p->bandwidth > 0) || p->n_chan <= 0 || !(p->dm >= 0) ||
-      p->n_avg <= 0 || n_fft < 0 || !isfinite(p->dm))
-    return CDD_EINVAL;
-  p->chan_bw = p->bandwidth / p->n_chan;
-  p->f_lo0 = p->f_center - p->bandwidth / 2.0;
-  if (!(p->f_lo0 > 0)) return CDD_EINVAL;
-  // dispersion time across the lowest (most smeared) channel, in samples
-  const double t_d = kDispD * p->dm * (pow(p->f_lo0, -2.0) - pow(p->f_lo0 + p->chan_bw, -2.0));
-  p->n_disp = t_d * p->chan_bw * 1e6;
-  if (!(p->n_disp < 1e9)) return CDD_EINVAL;
-  long long n_ov = (long long)ceil(p->n_disp);
-  n_ov = (n_ov + p->n_avg - 1) / p->n_avg * p->n_avg;
-  if (n_fft == 0) {
-    int a = next_pow2_above(2.0 * p->n_disp), b = next_pow2_above((double)n_ov);
-    if (a < 0 || b < 0) return CDD_EINVAL;
-    n_fft = a > b ? a : b;
-    if (n_fft < 64) n_fft = 64;
-    while ((long long)n_fft < 2LL * p->n_avg) n_fft *= 2;
-  }
-  if (n_fft <= 0 || (n_fft & (n_fft - 1)) || (long long)n_fft <= n_ov) return CDD_EINVAL;
-  const int hop = n_fft - (int)n_ov;
-  if (hop % p->n_avg) return CDD_EINVAL;
-  int logn = 0;
-  while ((1 << logn) < n_fft) ++logn;
-  p->n_fft = n_fft;
-  p->logn = logn;
-  p->n_ov = (int)n_ov;
-  p->hop = hop;
+  cdd::Geometry g;
+  const int rc = cdd::geometry(&g, p->f_center, p->bandwidth, p->n_chan, p->dm, n_fft, p->n_avg);
+  if (rc != CDD_OK) return rc;
+  p->chan_bw = g.chan_bw;
+  p->f_lo0 = g.f_lo0;
+  p->n_disp = g.n_disp;
+  p->n_fft = g.n_fft;
+  p->logn = g.logn;
+  p->n_ov = g.n_ov;
+  p->hop = g.hop;
+  p->r_max = g.r_max;
   p->shift.assign(p->n_chan, 0);
-  p->r_max = 0;
-  const double ref = pow(p->f_lo0, -2.0);
-  for (int k = 0; k < p->n_chan; ++k) {
-    const double f_k = p->f_lo0 + p->chan_bw * k;
-    const double delay = kDispD * p->dm * (pow(f_k, -2.0) - ref);   // <= 0
-    const double r = rint(-delay * p->chan_bw * 1e6 / p->n_avg);
-    if (!(r >= 0 && r < 2e9)) return CDD_EINVAL;
-    p->shift[k] = (int64_t)r;
-    if (p->shift[k] > p->r_max) p->r_max = p->shift[k];
-  }
-  if (logn < kMinLogN || logn > kMaxLogN) return CDD_EUNSUPPORTED;
+  for (int k = 0; k < p->n_chan; ++k) p->shift[k] = cdd::shift_of(g, k);
   return CDD_OK;
 }
 
@@ -287,6 +318,7 @@ const char* cdd_strerror(int code) {
     case CDD_ECUDA: return "CUDA error (sticky for this plan)";
     case CDD_EUNSUPPORTED: return "not supported by this build";
     case CDD_ESTATE: return "not allowed in the plan's current state";
+    case CDD_ETOOBIG: return "request exceeds the fixed scratch of cdd_execute_static";
     default: return "unknown error code";
   }
 }

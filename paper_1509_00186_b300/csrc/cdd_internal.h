@@ -24,6 +24,18 @@ struct OlsArgs {
   long long ring_len;
 };
 
+// Observation geometry (Sec. 2.2 / 2.3, alignment of Sec. 1.2) without the
+// per-channel shifts; geometry() returns a CDD_* code and allocates nothing.
+struct Geometry {
+  double f_center, bandwidth, dm, chan_bw, f_lo0, n_disp;
+  int n_chan, n_fft, logn, n_ov, hop, n_avg;
+  int64_t r_max;
+};
+int geometry(Geometry* g, double f_center, double bandwidth, int n_chan, double dm, int n_fft,
+             int n_avg);
+// Alignment shift r_k of channel k in integrated samples (-1 if out of range).
+int64_t shift_of(const Geometry& g, int k);
+
 // Launch the fused kernel for N = 2^logn.  Returns the CUDA error of the launch.
 cudaError_t launch_ols(int logn, const OlsArgs& a, cudaStream_t s);
 
@@ -37,6 +49,10 @@ cudaError_t launch_chirp_table(int logn, float2* chirp, int n_chan, double f_lo0
 // (FP64, then rounded); twiddle_table_len entries.
 cudaError_t launch_twiddle_table(int logn, float2* tw, cudaStream_t s);
 int twiddle_table_len(int logn);
+
+// shift[k] = r_k for k < n_chan, computed on the device in FP64.
+cudaError_t launch_shift_table(int* shift, int n_chan, double f_lo0_mhz, double chan_bw_mhz,
+                               double dm, int n_avg, cudaStream_t s);
 
 // Dynamic shared memory and block size of the fused kernel for N = 2^logn.
 int ols_threads(int logn);

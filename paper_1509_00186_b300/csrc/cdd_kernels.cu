@@ -282,6 +282,18 @@ __global__ void twiddle_kernel(float2* tw) {
   }
 }
 
+// Alignment shifts r_k (Sec. 1.2) computed on the device, for callers that
+// keep no host-side copy of them.
+__global__ void shift_kernel(int* shift, int n_chan, double f_lo0, double chan_bw, double dm,
+                             int n_avg) {
+  const double ref = pow(f_lo0, -2.0);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_chan; k += gridDim.x * blockDim.x) {
+    const double f_k = f_lo0 + chan_bw * k;
+    const double delay = kDispD * dm * (pow(f_k, -2.0) - ref);
+    shift[k] = (int)rint(-delay * chan_bw * 1e6 / n_avg);
+  }
+}
+
 template <int LOGN>
 cudaError_t launch_ols_t(const OlsArgs& a, cudaStream_t s) {
   using CF = Cfg<LOGN>;
@@ -346,6 +358,13 @@ cudaError_t launch_twiddle_table(int logn, float2* tw, cudaStream_t s) {
 #undef X
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_shift_table(int* shift, int n_chan, double f_lo0_mhz, double chan_bw_mhz,
+                               double dm, int n_avg, cudaStream_t s) {
+  const int grid = (n_chan + 255) / 256 < 1024 ? (n_chan + 255) / 256 : 1024;
+  shift_kernel<<<grid, 256, 0, s>>>(shift, n_chan, f_lo0_mhz, chan_bw_mhz, dm, n_avg);
+  return cudaGetLastError();
 }
 
 int twiddle_table_len(int logn) {

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol(cdd):
 
 def test_version_and_strerror(cdd):
     assert cdd.cdd_version() >= 100
-    for code in (0, -1, -2, -3, -4, -5):
+    for code in (0, -1, -2, -3, -4, -5, -6):
         assert cdd.strerror(code) and "unknown" not in cdd.strerror(code)
     assert "unknown" in cdd.strerror(-99)
 
@@ -113,3 +113,16 @@ def test_setters(cdd):
     finally:
         cdd.cdd_destroy(p)
     cdd.cdd_destroy(0)     # NULL is accepted
+
+
+def test_static_entry_rejects_before_touching_the_gpu(cdd):
+    """cdd_execute_static checks geometry and its fixed scratch size first."""
+    with pytest.raises(cdd.CddError) as ei:       # 2048 x 16384 chirp table = 256 MiB
+        cdd.cdd_execute_static(650.0, 200.0, 2048, 35.0, 16384, 16, 1, 0, 1, 1)
+    assert ei.value.code == cdd.CDD_ETOOBIG
+    with pytest.raises(cdd.CddError) as ei:
+        cdd.cdd_execute_static(325.0, 32.0, 512, 50.0, 48, 16, 1, 0, 1, 1)
+    assert ei.value.code == cdd.CDD_EINVAL
+    with pytest.raises(cdd.CddError) as ei:
+        cdd.cdd_execute_static(325.0, 32.0, 512, 50.0, 8192, 16, 0, 0, 1, 1)
+    assert ei.value.code == cdd.CDD_EINVAL
