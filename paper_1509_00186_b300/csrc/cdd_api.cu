@@ -39,6 +39,7 @@ struct cdd_plan_s {
   char2* d_tail[2] = {nullptr, nullptr};
   float* d_ring = nullptr;
   int* d_shift = nullptr;
+  char2* d_in_cm = nullptr;  // channel-major copy of the block (corner-turn path)
   long long ring_len = 0;
   size_t bytes_device = 0;
   // stream position
@@ -161,6 +162,7 @@ void free_device(cdd_plan p) {
   cudaFree(p->d_tail[1]);
   cudaFree(p->d_ring);
   cudaFree(p->d_shift);
+  cudaFree(p->d_in_cm);
   for (int i = 0; i < 2; ++i) {
     cudaFree(p->d_in_stage[i]);
     cudaFree(p->d_out_stage[i]);
@@ -215,6 +217,8 @@ int commit_once(cdd_plan p) {
   }
   if ((rc = dalloc(p, &p->d_ring, (size_t)p->n_chan * p->ring_len * sizeof(float)))) return rc;
   if ((rc = dalloc(p, &p->d_shift, (size_t)p->n_chan * sizeof(int)))) return rc;
+  // channel-major copy of a block: the fused kernel then reads each segment contiguously
+  if ((rc = dalloc(p, &p->d_in_cm, (size_t)p->n_chan * p->q * p->hop * sizeof(char2)))) return rc;
   std::vector<int> sh(p->shift.begin(), p->shift.end());
   CDD_TRY(p, cudaMemcpy(p->d_shift, sh.data(), sh.size() * sizeof(int), cudaMemcpyHostToDevice));
   cudaStream_t s;
@@ -252,6 +256,10 @@ int check_device(cdd_plan p) {
 int run_block(cdd_plan p, const int8_t* d_in, float* d_out, float* d_volt, int q, cudaStream_t s) {
   cdd::OlsArgs a;
   a.in = reinterpret_cast<const char2*>(d_in);
+  a.in_cm = nullptr;
+  a.rows = (long long)q * p->hop;
+  CDD_TRY(p, cdd::launch_corner_turn(a.in, p->d_in_cm, a.rows, p->n_chan, s));
+  a.in_cm = p->d_in_cm;
   a.out = d_out;
   a.chirp = p->d_chirp;
   a.tw = p->d_tw;
@@ -403,7 +411,7 @@ int cdd_execute_voltages(cdd_plan p, const int8_t* d_in, float* d_out, float* d_
   int rc = prepare(p);
   if (rc) return rc;
   rc = run_block(p, d_in, d_out, d_volt, p->q, stream);
-  p->last_launches = rc ? 0 : 1;
+  p->last_launches = rc ? 0 : 2;
   return rc;
 }
 
@@ -448,7 +456,7 @@ int cdd_execute_host(cdd_plan p, const int8_t* h_in, float* h_out, cudaStream_t 
   // the caller's stream continues after the last copy-out
   CDD_TRY(p, cudaStreamWaitEvent(stream, p->ev_out[(nc - 1) & 1], 0));
   CDD_TRY(p, cudaStreamSynchronize(p->st_d2h));
-  p->last_launches = nc;
+  p->last_launches = 2 * nc;
   return CDD_OK;
 }
 

@@ -11,6 +11,8 @@ namespace cdd {
 // every channel, one block of the stream.
 struct OlsArgs {
   const char2* in;        // [q*h][C] complex int8, block-local rows
+  const char2* in_cm;     // the same block channel-major [C][rows], or nullptr
+  long long rows;         // rows of in_cm (q*h)
   float* out;             // [C][n_out]
   const float2* chirp;    // [C][N] chirp function, digit-reversed layout
   const float2* tw;       // [N] exp(-2 pi i m / N)
@@ -38,6 +40,10 @@ int64_t shift_of(const Geometry& g, int k);
 
 // Launch the fused kernel for N = 2^logn.  Returns the CUDA error of the launch.
 cudaError_t launch_ols(int logn, const OlsArgs& a, cudaStream_t s);
+
+// out[k][row] = in[row][k]: channel-major copy of a block of int8 pairs.
+cudaError_t launch_corner_turn(const char2* in, char2* out, long long rows, int n_chan,
+                               cudaStream_t s);
 
 // Build the chirp table (FP64 phase, reduced mod 1 turn, then rounded to
 // float): chirp[k][idx] = exp(-i Phi_k(f_l)) * w(f_l) / N in the layout the

@@ -30,6 +30,13 @@ namespace cdd {
 namespace {
 
 constexpr double kDispD = 4.148808e3;   // s MHz^2 cm^3 / pc (Eq. 3)
+
+// Butterflies per thread in a pass are looped, not unrolled, by default: the
+// fully unrolled passes overflow the instruction cache.
+#ifndef CDD_PASS_UNROLL
+#define CDD_PASS_UNROLL 1
+#endif
+constexpr int kPassUnroll = CDD_PASS_UNROLL;
 constexpr int kMinCtaThreads = 256;
 
 template <int LOGN>
@@ -47,27 +54,44 @@ struct Cfg {
   static constexpr size_t SMEM = size_t(G) * SEG_F2 * sizeof(float2);
 };
 
+// pad(base + S*j) - pad(base) for the index sets the passes touch: base is a
+// multiple of 16 plus t < max(S, 16)... so the offset is a compile-time constant.
+template <int S>
+__device__ __forceinline__ constexpr int poff(int j) { return S * j + ((S * j) >> 4); }
+
+// int8 pair (re, im) held in the low 16 bits -> float2 without I2F: bias each
+// byte to unsigned, drop it into the mantissa of 2^23 and subtract 2^23 + 128
+// (exact for every int8 value).
+__device__ __forceinline__ float2 unpack_i8x2(uint32_t raw16) {
+  const uint32_t w = raw16 ^ 0x8080u;
+  const float re = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540)) - 8388736.0f;
+  const float im = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7541)) - 8388736.0f;
+  return make_float2(re, im);
+}
+
 // Forward (DIF) radix pass p >= 1, in place.
 template <int LOGN, int p>
 __device__ __forceinline__ void fwd_pass(float2* buf, const float2* __restrict__ tw, int lt) {
   using PL = PassPlan<LOGN>;
   constexpr int R = PL::R(p), S = PL::S(p), M = PL::M(p);
   constexpr int PER = (PL::N / R) / PL::T;
-#pragma unroll
+#pragma unroll kPassUnroll
   for (int i = 0; i < PER; ++i) {
     const int b = lt + i * PL::T;
     const int t = b % S;
     const int base = (b / S) * M + t;
+    float2* pb = buf + pad(base);
     float2 v[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) v[j] = buf[pad(base + S * j)];
+    for (int j = 0; j < R; ++j) v[j] = pb[poff<S>(j)];
     dft<R, -1>(v);
     if constexpr (S > 1) {
+      const float2* twp = tw + PL::TwOff(p) + t;
 #pragma unroll
-      for (int k = 1; k < R; ++k) v[k] = cmul(v[k], __ldg(&tw[PL::TwOff(p) + k * S + t]));
+      for (int k = 1; k < R; ++k) v[k] = cmul(v[k], __ldg(twp + k * S));
     }
 #pragma unroll
-    for (int k = 0; k < R; ++k) buf[pad(base + S * k)] = v[k];
+    for (int k = 0; k < R; ++k) pb[poff<S>(k)] = v[k];
   }
 }
 
@@ -77,21 +101,23 @@ __device__ __forceinline__ void inv_pass(float2* buf, const float2* __restrict__
   using PL = PassPlan<LOGN>;
   constexpr int R = PL::R(p), S = PL::S(p), M = PL::M(p);
   constexpr int PER = (PL::N / R) / PL::T;
-#pragma unroll
+#pragma unroll kPassUnroll
   for (int i = 0; i < PER; ++i) {
     const int b = lt + i * PL::T;
     const int t = b % S;
     const int base = (b / S) * M + t;
+    float2* pb = buf + pad(base);
     float2 v[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) v[k] = buf[pad(base + S * k)];
+    for (int k = 0; k < R; ++k) v[k] = pb[poff<S>(k)];
     if constexpr (S > 1) {
+      const float2* twp = tw + PL::TwOff(p) + t;
 #pragma unroll
-      for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], __ldg(&tw[PL::TwOff(p) + k * S + t]));
+      for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], __ldg(twp + k * S));
     }
     dft<R, 1>(v);
 #pragma unroll
-    for (int j = 0; j < R; ++j) buf[pad(base + S * j)] = v[j];
+    for (int j = 0; j < R; ++j) pb[poff<S>(j)] = v[j];
   }
 }
 
@@ -102,23 +128,24 @@ __device__ __forceinline__ void chirp_pass(float2* buf, const float2* __restrict
   constexpr int R = PL::RL;
   constexpr int NG = PL::N / R;
   constexpr int PER = NG / PL::T;
-#pragma unroll
+#pragma unroll kPassUnroll
   for (int i = 0; i < PER; ++i) {
     const int q = lt + i * PL::T;
-    const int base = q * R;
+    static_assert(R <= 16, "stride-1 groups must not cross a padding word");
+    float2* pb = buf + pad(q * R);
     float2 v[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) v[j] = buf[pad(base + j)];
+    for (int j = 0; j < R; ++j) v[j] = pb[j];
     dft<R, -1>(v);
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = cmul(v[k], __ldg(&chirp_k[k * NG + q]));
     dft<R, 1>(v);
 #pragma unroll
-    for (int j = 0; j < R; ++j) buf[pad(base + j)] = v[j];
+    for (int j = 0; j < R; ++j) pb[j] = v[j];
   }
 }
 
-template <int LOGN>
+template <int LOGN, bool CM>
 __global__ void __launch_bounds__(Cfg<LOGN>::THREADS, Cfg<LOGN>::MINB)
 ols_kernel(const OlsArgs a) {
   using PL = PassPlan<LOGN>;
@@ -138,29 +165,42 @@ ols_kernel(const OlsArgs a) {
   const int s = active ? w / a.n_chan : 0;     // share the input rows in L2
 
   // ---- pass 0, forward: unpack and gather x[lt + T*j] of this segment
+  float2* pb0 = buf + pad(lt);
   float2 v[R0];
   if (active) {
     const long long row0 = (long long)s * a.hop - a.n_ov;
-    const bool last = (s == a.q - 1);
-    char2 c[R0];
+    // element (row, k): row-major input [row][C], or the channel-major copy [k][row]
+    const unsigned short* src = CM ? reinterpret_cast<const unsigned short*>(a.in_cm) + (long long)k * a.rows
+                                   : reinterpret_cast<const unsigned short*>(a.in) + k;
+    const long long rstride = CM ? 1 : a.n_chan;
+    unsigned short c[R0];
+    if (row0 >= 0) {                                // no sample from the previous block
+      const unsigned short* p0 = src + (row0 + lt) * rstride;
 #pragma unroll
-    for (int j = 0; j < R0; ++j) {                 // issue every load before using any
-      const long long row = row0 + lt + T * j;
-      const char2* src = row >= 0 ? a.in + row * a.n_chan + k
-                                  : a.tail_rd + (long long)k * a.n_ov + (row + a.n_ov);
-      c[j] = __ldg(src);
+      for (int j = 0; j < R0; ++j) c[j] = __ldg(p0 + (long long)T * j * rstride);
+    } else {
+      const unsigned short* tail = reinterpret_cast<const unsigned short*>(a.tail_rd) + (long long)k * a.n_ov;
+#pragma unroll
+      for (int j = 0; j < R0; ++j) {
+        const long long row = row0 + lt + T * j;
+        c[j] = __ldg(row >= 0 ? src + row * rstride : tail + (row + a.n_ov));
+      }
+    }
+    if (s == a.q - 1 && a.n_ov > 0) {             // keep this block's last n_ov samples
+      unsigned short* tw_out = reinterpret_cast<unsigned short*>(a.tail_wr) + (long long)k * a.n_ov;
+#pragma unroll
+      for (int j = 0; j < R0; ++j) {
+        const int n = lt + T * j;
+        if (n >= N - a.n_ov) tw_out[n - (N - a.n_ov)] = c[j];
+      }
     }
 #pragma unroll
-    for (int j = 0; j < R0; ++j) {
-      const int n = lt + T * j;
-      if (last && n >= N - a.n_ov) a.tail_wr[(long long)k * a.n_ov + (n - (N - a.n_ov))] = c[j];
-      v[j] = make_float2((float)c[j].x, (float)c[j].y);
-    }
+    for (int j = 0; j < R0; ++j) v[j] = unpack_i8x2(c[j]);
     dft<R0, -1>(v);
 #pragma unroll
     for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], __ldg(&a.tw[kk * T + lt]));
 #pragma unroll
-    for (int kk = 0; kk < R0; ++kk) buf[pad(lt + T * kk)] = v[kk];
+    for (int kk = 0; kk < R0; ++kk) pb0[poff<T>(kk)] = v[kk];
   }
   __syncthreads();
 
@@ -180,7 +220,7 @@ ols_kernel(const OlsArgs a) {
   // ---- pass 0, inverse: natural-order voltages v[j] = z[lt + T*j]
   if (active) {
 #pragma unroll
-    for (int kk = 0; kk < R0; ++kk) v[kk] = buf[pad(lt + T * kk)];
+    for (int kk = 0; kk < R0; ++kk) v[kk] = pb0[poff<T>(kk)];
 #pragma unroll
     for (int kk = 1; kk < R0; ++kk) v[kk] = cmulc(v[kk], __ldg(&a.tw[kk * T + lt]));
     dft<R0, 1>(v);
@@ -294,22 +334,92 @@ __global__ void shift_kernel(int* shift, int n_chan, double f_lo0, double chan_b
   }
 }
 
+// Corner turn of int8 pairs: out[k][row] = in[row][k] for row < rows, k < n_chan.
+// 64 x 64 tiles.  A whole tile moves as 16-byte loads of 8 channels and 16-byte
+// stores of 8 rows; eight lanes cover one channel's 128-byte line, and the tile
+// is held as 32-bit channel pairs with an XOR swizzle so both sides are free of
+// bank conflicts.
+constexpr int kTT = 64;
+__global__ void __launch_bounds__(256) corner_turn_kernel(const char2* __restrict__ in,
+                                                          char2* __restrict__ out,
+                                                          long long rows, int n_chan) {
+  __shared__ __align__(16) uint32_t tile[kTT][kTT / 2];    // [row][channel pair ^ swizzle]
+  const long long r0 = (long long)blockIdx.x * kTT;
+  const int c0 = blockIdx.y * kTT;
+  const unsigned short* src = reinterpret_cast<const unsigned short*>(in);
+  unsigned short* dst = reinterpret_cast<unsigned short*>(out);
+  const bool whole = r0 + kTT <= rows && c0 + kTT <= n_chan && (n_chan % 8) == 0 && (rows % 8) == 0;
+  auto sw = [](int r) { return ((r >> 3) & 15) << 1; };
+  if (whole) {
+    uint4 x[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {              // 64 rows x 8 chunks of 8 channels
+      const int v = threadIdx.x + 256 * i;
+      const int r = v >> 3, cq = v & 7;
+      x[i] = __ldg(reinterpret_cast<const uint4*>(src + (r0 + r) * n_chan + c0 + cq * 8));
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int v = threadIdx.x + 256 * i;
+      const int r = v >> 3, cq = v & 7;
+      tile[r][(cq * 4 + 0) ^ sw(r)] = x[i].x;
+      tile[r][(cq * 4 + 1) ^ sw(r)] = x[i].y;
+      tile[r][(cq * 4 + 2) ^ sw(r)] = x[i].z;
+      tile[r][(cq * 4 + 3) ^ sw(r)] = x[i].w;
+    }
+  } else {
+    for (int v = threadIdx.x; v < kTT * kTT; v += 256) {
+      const int r = v / kTT, ch = v % kTT;
+      if (r0 + r < rows && c0 + ch < n_chan) {
+        unsigned short* t = reinterpret_cast<unsigned short*>(&tile[r][(ch >> 1) ^ sw(r)]);
+        t[ch & 1] = src[(r0 + r) * n_chan + c0 + ch];
+      }
+    }
+  }
+  __syncthreads();
+  if (whole) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {              // 64 channels x 8 chunks of 8 rows
+      const int v = threadIdx.x + 256 * i;
+      const int ch = v >> 3, rb = (v & 7) * 8;
+      uint4 y;
+      unsigned short* e = reinterpret_cast<unsigned short*>(&y);
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int r = rb + t;
+        e[t] = reinterpret_cast<const unsigned short*>(&tile[r][(ch >> 1) ^ sw(r)])[ch & 1];
+      }
+      *reinterpret_cast<uint4*>(dst + (long long)(c0 + ch) * rows + r0 + rb) = y;
+    }
+  } else {
+    for (int v = threadIdx.x; v < kTT * kTT; v += 256) {
+      const int ch = v / kTT, r = v % kTT;
+      if (r0 + r < rows && c0 + ch < n_chan)
+        dst[(long long)(c0 + ch) * rows + r0 + r] =
+            reinterpret_cast<const unsigned short*>(&tile[r][(ch >> 1) ^ sw(r)])[ch & 1];
+    }
+  }
+}
+
 template <int LOGN>
 cudaError_t launch_ols_t(const OlsArgs& a, cudaStream_t s) {
   using CF = Cfg<LOGN>;
-  static bool attr_set[128] = {};            // per device
+  static bool attr_set[128][2] = {};         // per device and input layout
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
-  if (!attr_set[dev]) {
-    e = cudaFuncSetAttribute(ols_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CF::SMEM);
+  const bool cm = a.in_cm != nullptr;
+  if (!attr_set[dev][cm]) {
+    e = cm ? cudaFuncSetAttribute(ols_kernel<LOGN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CF::SMEM)
+           : cudaFuncSetAttribute(ols_kernel<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CF::SMEM);
     if (e != cudaSuccess) return e;
-    attr_set[dev] = true;
+    attr_set[dev][cm] = true;
   }
   const long long work = (long long)a.n_chan * a.q;
   const unsigned grid = (unsigned)((work + CF::G - 1) / CF::G);
-  ols_kernel<LOGN><<<grid, CF::THREADS, CF::SMEM, s>>>(a);
+  if (cm) ols_kernel<LOGN, true><<<grid, CF::THREADS, CF::SMEM, s>>>(a);
+  else ols_kernel<LOGN, false><<<grid, CF::THREADS, CF::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -364,6 +474,13 @@ cudaError_t launch_shift_table(int* shift, int n_chan, double f_lo0_mhz, double 
                                double dm, int n_avg, cudaStream_t s) {
   const int grid = (n_chan + 255) / 256 < 1024 ? (n_chan + 255) / 256 : 1024;
   shift_kernel<<<grid, 256, 0, s>>>(shift, n_chan, f_lo0_mhz, chan_bw_mhz, dm, n_avg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_corner_turn(const char2* in, char2* out, long long rows, int n_chan,
+                               cudaStream_t s) {
+  const dim3 grid((unsigned)((rows + kTT - 1) / kTT), (unsigned)((n_chan + kTT - 1) / kTT));
+  corner_turn_kernel<<<grid, 256, 0, s>>>(in, out, rows, n_chan);
   return cudaGetLastError();
 }
 

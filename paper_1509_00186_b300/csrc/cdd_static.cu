@@ -85,6 +85,8 @@ extern "C" int cdd_execute_static(double f_center_mhz, double bandwidth_mhz, int
 
   cdd::OlsArgs a;
   a.in = reinterpret_cast<const char2*>(d_in);
+  a.in_cm = nullptr;
+  a.rows = 0;
   a.out = d_out;
   a.chirp = chirp;
   a.tw = tw;
