@@ -88,7 +88,9 @@ typedef struct cdd_plan_s* cdd_plan;
 /* Create a plan for one polarisation of a C-channel band.
  *   f_center_mhz, bandwidth_mhz > 0: observing band (Sec. 2.1 f_o, Delta f).
  *   n_chan > 0: channels.  dm >= 0: dispersion measure in pc cm^-3 (Eq. 3).
- *   n_fft: FFT length N (power of two, 64..16384 in this build), or 0 for the
+ *   n_fft: FFT length N (power of two, 64..65536 in this build; above 16384
+ *     a segment runs on a cluster of N/16384 CTAs and n_avg must be at most
+ *     16384*16384/N), or 0 for the
  *     Sec. 2.3 rule: the smallest power of two > 2*n_d (raised so that
  *     N > n_ov, N >= 2*n_avg and N >= 64).
  *   n_avg > 0: detected samples summed per output; h must be a multiple of it.
@@ -141,7 +143,9 @@ int cdd_execute_host(cdd_plan plan, const int8_t* h_in, float* h_out, cudaStream
  * last r_k samples of each channel, which belong to a later block, are
  * dropped): d_in device int8 [n_seg*h][C][2], d_out device float
  * [C][n_seg*h/n_avg], h = N - n_ov as in cdd_plan_create.  taper is an
- * enum cdd_taper.  Asynchronous on `stream`.
+ * enum cdd_taper.  Asynchronous on `stream`.  N above 16384 (the cluster
+ * form, which needs a channel-major copy of the block) returns
+ * CDD_EUNSUPPORTED here.
  *
  * It calls no cudaMalloc, cudaFree or other allocating routine.  Its chirp
  * and twiddle tables, shifts, zero history and alignment spill all live in one

@@ -15,7 +15,7 @@ namespace {
 
 constexpr double kDispD = 4.148808e3;   // s MHz^2 cm^3 / pc (Sec. 2.1, Eq. 3)
 constexpr int kMinLogN = 6;
-constexpr int kMaxLogN = 14;
+constexpr int kMaxLogN = 16;
 
 }  // namespace
 
@@ -115,6 +115,9 @@ int geometry(Geometry* g, double f_center, double bandwidth, int n_chan, double 
     if (r > g->r_max) g->r_max = r;
   }
   if (logn < kMinLogN || logn > kMaxLogN) return CDD_EUNSUPPORTED;
+  // N > 16384 runs as a cluster of N/16384 CTAs; an integration window must not
+  // span two of them
+  if (logn > 14 && n_avg > (1 << 14) / (n_fft >> 14)) return CDD_EUNSUPPORTED;
   return CDD_OK;
 }
 

@@ -55,6 +55,8 @@ cudaError_t launch_chirp_table(int logn, float2* chirp, int n_chan, double f_lo0
 // (FP64, then rounded); twiddle_table_len entries.
 cudaError_t launch_twiddle_table(int logn, float2* tw, cudaStream_t s);
 int twiddle_table_len(int logn);
+// N = 2^logn runs as a CTA cluster and reads only the channel-major copy.
+bool needs_channel_major(int logn);
 
 // shift[k] = r_k for k < n_chan, computed on the device in FP64.
 cudaError_t launch_shift_table(int* shift, int n_chan, double f_lo0_mhz, double chan_bw_mhz,

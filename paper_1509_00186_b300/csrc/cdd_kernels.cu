@@ -22,6 +22,8 @@
 // The overlap of segment 0 (the last n_ov samples of the previous block) is
 // read from a per-channel tail that the last segment of every block rewrites
 // (Sec. 4.3: the samples lost at the end of a block are prefixed to the next).
+#include <cooperative_groups.h>
+
 #include "cdd_fft.cuh"
 #include "cdd_internal.h"
 
@@ -269,19 +271,166 @@ ols_kernel(const OlsArgs a) {
   }
 }
 
-template <int LOGN>
+// ------------------------------------------------------------------ clusters
+//
+// N = CL * 2^LOGS (32768 and 65536) does not fit one SM's shared memory, so a
+// cluster of CL CTAs holds one segment, 2^LOGS points per CTA.  A radix-CL pass
+// across the cluster (DIF; inputs straight from global memory, outputs written
+// through distributed shared memory) leaves CTA r with the independent
+// sub-transform r (bins r + CL*b).  Each CTA then runs the single-CTA forward
+// passes, chirp pass and inverse passes on it; the inverse radix-CL pass reads
+// the CL sub-results back across the cluster and the epilogue detects,
+// integrates and stores the CTA's quarter of the butterflies.
+template <int LOGS, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(PassPlan<LOGS>::T, 1)
+ols_cluster_kernel(const OlsArgs a) {
+  namespace cg = cooperative_groups;
+  using PL = PassPlan<LOGS>;
+  constexpr int NS = PL::N;
+  constexpr int N = NS * CL;
+  constexpr int T = PL::T;
+  constexpr int NB = NS / CL;            // cross-pass butterflies of this CTA
+  constexpr int PERX = NB / T;           // ... per thread
+  static_assert(PERX * T == NB, "cross pass must split evenly over the threads");
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  extern __shared__ float2 smem[];
+  float2* buf = smem;
+  const int lt = threadIdx.x;
+  const int w = blockIdx.x / CL;         // one segment per cluster
+  const int k = w % a.n_chan;
+  const int s = w / a.n_chan;
+  float2* rbuf[CL];
+#pragma unroll
+  for (int j = 0; j < CL; ++j) rbuf[j] = cluster.map_shared_rank(buf, j);
+  const float2* twx = a.tw + PL::TW_LEN;
+  cluster.sync();                        // every CTA of the cluster has started: DSMEM is live
+
+  // ---- cross pass, forward: x[t + NS*j] -> DFT_CL -> w_N^{t*kk} -> CTA kk, index t
+  {
+    const long long row0 = (long long)s * a.hop - a.n_ov;
+    const unsigned short* src = reinterpret_cast<const unsigned short*>(a.in_cm) + (long long)k * a.rows;
+    const unsigned short* tail = reinterpret_cast<const unsigned short*>(a.tail_rd) + (long long)k * a.n_ov;
+    unsigned short* tail_out = reinterpret_cast<unsigned short*>(a.tail_wr) + (long long)k * a.n_ov;
+    const bool last = (s == a.q - 1) && a.n_ov > 0;
+#pragma unroll 1
+    for (int i = 0; i < PERX; ++i) {
+      const int t = rank * NB + lt + i * T;
+      unsigned short c[CL];
+#pragma unroll
+      for (int j = 0; j < CL; ++j) {
+        const long long row = row0 + t + (long long)NS * j;
+        c[j] = __ldg(row >= 0 ? src + row : tail + (row + a.n_ov));
+      }
+      float2 v[CL];
+#pragma unroll
+      for (int j = 0; j < CL; ++j) {
+        const int n = t + NS * j;
+        if (last && n >= N - a.n_ov) tail_out[n - (N - a.n_ov)] = c[j];
+        v[j] = unpack_i8x2(c[j]);
+      }
+      dft<CL, -1>(v);
+#pragma unroll
+      for (int kk = 1; kk < CL; ++kk) v[kk] = cmul(v[kk], __ldg(&twx[(kk - 1) * NS + t]));
+#pragma unroll
+      for (int kk = 0; kk < CL; ++kk) rbuf[kk][pad(t)] = v[kk];
+    }
+  }
+  cluster.sync();
+
+  // ---- sub-transform r of 2^LOGS points, all in this CTA
+  static_for<0, PL::P - 1>([&](auto P_) {
+    fwd_pass<LOGS, decltype(P_)::value>(buf, a.tw, lt);
+    __syncthreads();
+  });
+  chirp_pass<LOGS>(buf, a.chirp + (size_t)k * N + (size_t)rank * NS, lt);
+  __syncthreads();
+  static_for<0, PL::P - 1>([&](auto I_) {
+    inv_pass<LOGS, PL::P - 2 - decltype(I_)::value>(buf, a.tw, lt);
+    __syncthreads();
+  });
+  cluster.sync();
+
+  // ---- cross pass, inverse: u_kk[t] from CTA kk -> w_N^{-t*kk} -> IDFT_CL -> z[t + NS*j]
+  float2 z[PERX][CL];
+#pragma unroll
+  for (int i = 0; i < PERX; ++i) {
+    const int t = rank * NB + lt + i * T;
+#pragma unroll
+    for (int kk = 0; kk < CL; ++kk) z[i][kk] = rbuf[kk][pad(t)];
+#pragma unroll
+    for (int kk = 1; kk < CL; ++kk) z[i][kk] = cmulc(z[i][kk], __ldg(&twx[(kk - 1) * NS + t]));
+    dft<CL, 1>(z[i]);
+    if (a.volt != nullptr) {
+      const long long vbase = ((long long)k * a.q + s) * a.hop - a.n_ov;
+#pragma unroll
+      for (int j = 0; j < CL; ++j) {
+        const int n = t + NS * j;
+        if (n >= a.n_ov) a.volt[vbase + n] = z[i][j];
+      }
+    }
+  }
+  cluster.sync();                        // no CTA reads another's buffer after this
+
+  // ---- detect into this CTA's buffer: (j, tt) -> j*NB + tt, one spare word per 32
+  float* pw = reinterpret_cast<float*>(buf);
+#pragma unroll
+  for (int i = 0; i < PERX; ++i) {
+#pragma unroll
+    for (int j = 0; j < CL; ++j) {
+      const int nl = j * NB + lt + i * T;
+      pw[nl + (nl >> 5)] = fmaf(z[i][j].x, z[i][j].x, z[i][j].y * z[i][j].y);
+    }
+  }
+  __syncthreads();
+
+  // ---- integrate, discard, align: n in [NS*j + rank*NB, NS*j + (rank+1)*NB)
+  const int n_int = a.hop / a.n_avg;
+  const int r = __ldg(&a.shift[k]);
+  const long long gseg = a.g0 + (long long)s * n_int;
+  float* outk = a.out + (size_t)k * a.n_out;
+  float* ringk = a.ring + (size_t)k * a.ring_len;
+  const int per_j = NB / a.n_avg;
+  for (int e = lt; e < CL * per_j; e += T) {
+    const int j = e / per_j, mm = e % per_j;
+    const int n0 = NS * j + rank * NB + mm * a.n_avg;
+    if (n0 < a.n_ov) continue;                          // the overlap is discarded
+    const int nl0 = j * NB + mm * a.n_avg;
+    float acc = 0.f;
+    for (int i = 0; i < a.n_avg; ++i) acc += pw[(nl0 + i) + ((nl0 + i) >> 5)];
+    const long long gi = gseg + (n0 - a.n_ov) / a.n_avg;
+    const long long dst = gi + r - a.g0;
+    if (dst < a.n_out) outk[dst] = acc;
+    else ringk[gi % a.ring_len] = acc;
+  }
+  if (s == 0 && rank == 0) {
+    const int lim = r < a.n_out ? r : a.n_out;
+    for (int m = lt; m < lim; m += T) {
+      const long long src = a.g0 + m - r;
+      outk[m] = src >= 0 ? ringk[src % a.ring_len] : 0.f;
+    }
+  }
+}
+
+// Chirp table for a transform of CL * 2^LOGS points held as CL sub-transforms
+// of 2^LOGS (CL = 1: one CTA).  Entry (k, r, idx) multiplies the bin that
+// sub-transform r holds at table index idx after its forward passes:
+// bin = r + CL * position_to_bin(pos), pos = (idx % NG) * R_last + idx / NG.
+template <int LOGS, int CL>
 __global__ void chirp_table_kernel(float2* chirp, int n_chan, double f_lo0, double chan_bw,
                                    double dm, int taper) {
-  using PL = PassPlan<LOGN>;
-  constexpr int N = PL::N;
-  constexpr int NG = N / PL::RL;
+  using PL = PassPlan<LOGS>;
+  constexpr int NS = PL::N;
+  constexpr int N = NS * CL;
+  constexpr int NG = NS / PL::RL;
   const long long total = (long long)n_chan * N;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     const int k = (int)(e / N);
-    const int idx = (int)(e % N);
-    const int pos = (idx % NG) * PL::RL + idx / NG;       // table index kk*NG + q
-    const int bin = position_to_bin<LOGN>(pos);
+    const int rem = (int)(e % N);
+    const int r = rem / NS, idx = rem % NS;
+    const int pos = (idx % NG) * PL::RL + idx / NG;
+    const int bin = r + CL * position_to_bin<LOGS>(pos);
     const int sbin = bin < N / 2 ? bin : bin - N;
     const double f_lo = f_lo0 + chan_bw * k;
     const double f_l = sbin * (chan_bw / N) + 0.5 * chan_bw;
@@ -304,18 +453,29 @@ __global__ void chirp_table_kernel(float2* chirp, int n_chan, double f_lo0, doub
   }
 }
 
-// Twiddle table in the per-pass thread-major layout of PassPlan::TwOff.
-template <int LOGN>
+// Twiddle table in the per-pass thread-major layout of PassPlan::TwOff, then,
+// for a CL-CTA cluster, the cross-CTA pass: w_N^{t*k} at TW_LEN + (k-1)*NS + t.
+template <int LOGS, int CL>
 __global__ void twiddle_kernel(float2* tw) {
-  using PL = PassPlan<LOGN>;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < PL::TW_LEN; e += gridDim.x * blockDim.x) {
-    int p = 0;
-    while (p + 1 < PL::P - 1 && e >= PL::TwOff(p + 1)) ++p;
-    const int local = e - PL::TwOff(p);
-    const int stride = p == 0 ? PL::T : PL::S(p);            // thread index range
-    const int modulus = p == 0 ? PL::N : PL::M(p);
-    const int t = local % stride, k = local / stride;
-    const int m = (t * k) % modulus;
+  using PL = PassPlan<LOGS>;
+  constexpr int NS = PL::N;
+  constexpr int TOTAL = PL::TW_LEN + (CL - 1) * NS;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < TOTAL; e += gridDim.x * blockDim.x) {
+    int m, modulus;
+    if (e >= PL::TW_LEN) {
+      const int local = e - PL::TW_LEN;
+      const int k = 1 + local / NS, t = local % NS;
+      modulus = NS * CL;
+      m = (int)(((long long)t * k) % modulus);
+    } else {
+      int p = 0;
+      while (p + 1 < PL::P - 1 && e >= PL::TwOff(p + 1)) ++p;
+      const int local = e - PL::TwOff(p);
+      const int stride = p == 0 ? PL::T : PL::S(p);            // thread index range
+      modulus = p == 0 ? PL::N : PL::M(p);
+      const int t = local % stride, k = local / stride;
+      m = (t * k) % modulus;
+    }
     double sn, cs;
     sincospi(2.0 * m / modulus, &sn, &cs);
     tw[e] = make_float2((float)cs, (float)(-sn));           // exp(-2 pi i m / modulus)
@@ -423,12 +583,32 @@ cudaError_t launch_ols_t(const OlsArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int LOGN>
+template <int LOGS, int CL>
+cudaError_t launch_cluster_t(const OlsArgs& a, cudaStream_t s) {
+  constexpr size_t SMEM = size_t(padded_len(PassPlan<LOGS>::N)) * sizeof(float2);
+  static bool attr_set[128] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  if (a.in_cm == nullptr) return cudaErrorInvalidValue;     // needs the channel-major copy
+  if (!attr_set[dev]) {
+    e = cudaFuncSetAttribute(ols_cluster_kernel<LOGS, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  const unsigned grid = (unsigned)((long long)a.n_chan * a.q * CL);
+  ols_cluster_kernel<LOGS, CL><<<grid, PassPlan<LOGS>::T, SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int LOGS, int CL>
 cudaError_t launch_chirp_t(float2* chirp, int n_chan, double f_lo0, double chan_bw, double dm,
                            int taper, cudaStream_t s) {
-  const long long total = (long long)n_chan << LOGN;
+  const long long total = (long long)n_chan * (CL << LOGS);
   const unsigned grid = (unsigned)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
-  chirp_table_kernel<LOGN><<<grid, 256, 0, s>>>(chirp, n_chan, f_lo0, chan_bw, dm, taper);
+  chirp_table_kernel<LOGS, CL><<<grid, 256, 0, s>>>(chirp, n_chan, f_lo0, chan_bw, dm, taper);
   return cudaGetLastError();
 }
 
@@ -441,6 +621,8 @@ cudaError_t launch_ols(int logn, const OlsArgs& a, cudaStream_t s) {
 #define X(L) case L: return launch_ols_t<L>(a, s);
     CDD_LOGN_CASES(X)
 #undef X
+    case 15: return launch_cluster_t<14, 2>(a, s);
+    case 16: return launch_cluster_t<14, 4>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -448,24 +630,31 @@ cudaError_t launch_ols(int logn, const OlsArgs& a, cudaStream_t s) {
 cudaError_t launch_chirp_table(int logn, float2* chirp, int n_chan, double f_lo0_mhz,
                                double chan_bw_mhz, double dm, int taper, cudaStream_t s) {
   switch (logn) {
-#define X(L) case L: return launch_chirp_t<L>(chirp, n_chan, f_lo0_mhz, chan_bw_mhz, dm, taper, s);
+#define X(L) case L: return launch_chirp_t<L, 1>(chirp, n_chan, f_lo0_mhz, chan_bw_mhz, dm, taper, s);
     CDD_LOGN_CASES(X)
 #undef X
+    case 15: return launch_chirp_t<14, 2>(chirp, n_chan, f_lo0_mhz, chan_bw_mhz, dm, taper, s);
+    case 16: return launch_chirp_t<14, 4>(chirp, n_chan, f_lo0_mhz, chan_bw_mhz, dm, taper, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-template <int LOGN>
+template <int LOGS, int CL>
+constexpr int twiddle_len_t() { return PassPlan<LOGS>::TW_LEN + (CL - 1) * PassPlan<LOGS>::N; }
+
+template <int LOGS, int CL>
 cudaError_t launch_twiddle_t(float2* tw, cudaStream_t s) {
-  twiddle_kernel<LOGN><<<(PassPlan<LOGN>::TW_LEN + 255) / 256, 256, 0, s>>>(tw);
+  twiddle_kernel<LOGS, CL><<<(twiddle_len_t<LOGS, CL>() + 255) / 256, 256, 0, s>>>(tw);
   return cudaGetLastError();
 }
 
 cudaError_t launch_twiddle_table(int logn, float2* tw, cudaStream_t s) {
   switch (logn) {
-#define X(L) case L: return launch_twiddle_t<L>(tw, s);
+#define X(L) case L: return launch_twiddle_t<L, 1>(tw, s);
     CDD_LOGN_CASES(X)
 #undef X
+    case 15: return launch_twiddle_t<14, 2>(tw, s);
+    case 16: return launch_twiddle_t<14, 4>(tw, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -486,12 +675,16 @@ cudaError_t launch_corner_turn(const char2* in, char2* out, long long rows, int 
 
 int twiddle_table_len(int logn) {
   switch (logn) {
-#define X(L) case L: return PassPlan<L>::TW_LEN;
+#define X(L) case L: return twiddle_len_t<L, 1>();
     CDD_LOGN_CASES(X)
 #undef X
+    case 15: return twiddle_len_t<14, 2>();
+    case 16: return twiddle_len_t<14, 4>();
     default: return 0;
   }
 }
+
+bool needs_channel_major(int logn) { return logn > 14; }
 
 int ols_threads(int logn) {
   switch (logn) {

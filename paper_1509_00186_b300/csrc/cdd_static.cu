@@ -45,6 +45,7 @@ extern "C" int cdd_execute_static(double f_center_mhz, double bandwidth_mhz, int
   cdd::Geometry g;
   int rc = cdd::geometry(&g, f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft, n_avg);
   if (rc != CDD_OK) return rc;
+  if (cdd::needs_channel_major(g.logn)) return CDD_EUNSUPPORTED;   // cluster form needs a copy
   if (!d_in || !d_out || n_seg < 1 || taper < CDD_TAPER_NONE || taper > CDD_TAPER_WELCH)
     return CDD_EINVAL;
   if ((int64_t)n_seg * n_chan >= ((int64_t)1 << 31)) return CDD_EINVAL;

@@ -48,6 +48,8 @@ GEOMS = [
     (325.0, 16.0, 256, 10.0, 64, 4),
     (325.0, 32.0, 512, 50.0, 8192, 16),
     (150.0, 32.0, 512, 100.0, 16384, 16),
+    (150.0, 32.0, 512, 100.0, 65536, 16),
+    (150.0, 32.0, 512, 100.0, 32768, 16),
     (610.0, 32.0, 512, 20.0, 0, 16),
     (325.0, 32.0, 512, 50.0, 0, 16),
     (235.0, 16.0, 256, 67.99, 0, 8),
@@ -93,8 +95,11 @@ def test_invalid_geometry_is_rejected(cdd):
             cdd.cdd_plan_create(*args)
         assert ei.value.code == cdd.CDD_EINVAL, args
     with pytest.raises(cdd.CddError) as ei:
-        cdd.cdd_plan_create(150.0, 32.0, 512, 100.0, 65536, 16)     # valid, not in this build
+        cdd.cdd_plan_create(150.0, 32.0, 512, 100.0, 131072, 16)    # valid, not in this build
     assert ei.value.code == cdd.CDD_EUNSUPPORTED
+    with pytest.raises(cdd.CddError) as ei:                         # window spans two CTAs
+        cdd.cdd_plan_create(150.0, 32.0, 512, 100.0, 65536, 8192)
+    assert ei.value.code in (cdd.CDD_EUNSUPPORTED, cdd.CDD_EINVAL)
 
 
 def test_setters(cdd):

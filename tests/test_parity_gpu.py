@@ -116,7 +116,7 @@ def test_host_buffer_path_equals_device_path(tiny):
     assert O.rel_rms(host, out_o) <= TOL
 
 
-@pytest.mark.parametrize("logn", list(range(6, 15)))
+@pytest.mark.parametrize("logn", list(range(6, 17)))
 def test_every_fft_length(cuda_device, logn):
     """Each supported N on a ragged channel count (the last CTA is partly idle
     for small N), two blocks of three segments, overlap ~ N/8."""
@@ -193,3 +193,21 @@ def test_gsb_full_size_sampled_channels(cuda_device):
     # mean intensity ~ n_avg * 2 * sigma^2 after the r_k leading zeros
     means = np.array([out_g[k, geo.shift[k]:].mean() for k in range(w.n_chan)])
     assert np.all(np.abs(means / (w.n_avg * 2 * w.sigma ** 2) - 1) < 0.1)
+
+
+@pytest.mark.slow
+def test_precision_shape_full_size_sampled_channels(cuda_device):
+    """The 32 MHz / 512-channel band at 150 MHz, DM 100, N 65536 (a cluster of
+    four CTAs per segment) at its full 10 s size, one block of 9 segments;
+    sampled channels against the oracle."""
+    w = WORKLOADS["precision"]
+    args = (w.f_center_mhz, w.bandwidth_mhz, w.n_chan, w.dm, w.n_fft, w.n_avg)
+    geo = O.plan_geometry(*args)
+    assert (geo.n_ov, geo.hop) == (1360, 64176)
+    vin = complex_int8_voltages(w.seed, w.n_samp, w.n_chan, w.sigma)
+    q = w.n_samp // geo.hop
+    out_g, _ = gpu_run(vin, args, q, 1, volt=False)
+    chans = [0, 7, 300, 511]
+    out_o, _ = oracle_run(vin, args, q * geo.hop, channels=chans)
+    assert np.all(rel_rms_rows(out_g[chans], out_o) <= TOL)
+    assert np.all(np.isfinite(out_g))
