@@ -164,6 +164,39 @@ int cdd_execute_static(double f_center_mhz, double bandwidth_mhz, int n_chan, do
                        int n_fft, int n_avg, int n_seg, int taper, const int8_t* d_in,
                        float* d_out, cudaStream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Batched form: n_dm DM trials over one band, the channels cut into n_tiers
+ * equal groups (lowest frequencies first) that dedisperse with their own N.
+ * Each segment's forward transform is computed once and shared by every DM
+ * trial (Sec. 2.2 deconvolution repeated per trial DM; Sec. 1.2 alignment per
+ * trial).  Tier t uses N_t = tier_nfft[t] (power of two, 64..16384) and the
+ * overlap max(N_t/32, dispersion samples of its lowest channel at the largest
+ * DM) rounded up to a multiple of n_avg; the hops must nest (each divides the
+ * longest).  A block is q longest hops (CDD_ATTR_SEGMENTS_PER_BLOCK), so every
+ * channel emits n_out = q*h_max/n_avg outputs per block; the block must be at
+ * least as long as the largest alignment shift (CDD_ATTR_R_MAX), and the
+ * default q is the smallest such value.
+ *   d_in: device int8 [q*h_max][C][2];  d_out: device float [n_dm][C][n_out]
+ *   (DM-major planes laid out like cdd_execute's output).
+ * Streams continue across calls as for cdd_execute.  The DM list is copied. */
+typedef struct cdd_batch_s* cdd_batch;
+
+int cdd_batch_create(cdd_batch* batch, double f_center_mhz, double bandwidth_mhz, int n_chan,
+                     const double* dms, int n_dm, const int* tier_nfft, int n_tiers, int n_avg);
+/* Only CDD_ATTR_SEGMENTS_PER_BLOCK, before the first execute. */
+int cdd_batch_set(cdd_batch batch, int attr, int64_t value);
+/* SEGMENTS_PER_BLOCK, BLOCK_SAMPLES, N_OUT_PER_BLOCK, R_MAX, BYTES_DEVICE,
+ * BLOCKS_DONE, KERNEL_LAUNCHES, N_CHAN, N_AVG, HOP (the longest hop). */
+int cdd_batch_get(cdd_batch batch, int attr, int64_t* value);
+/* Geometry of tier t (any output pointer may be NULL). */
+int cdd_batch_tier(cdd_batch batch, int t, int64_t* n_fft, int64_t* n_ov, int64_t* first_chan,
+                   int64_t* n_tier_chan);
+/* Alignment shifts, host int64 [n_dm][n_chan]. */
+int cdd_batch_shifts(cdd_batch batch, int64_t* shifts);
+int cdd_batch_execute(cdd_batch batch, const int8_t* d_in, float* d_out, cudaStream_t stream);
+int cdd_batch_reset(cdd_batch batch);
+int cdd_batch_destroy(cdd_batch batch);
+
 /* Restart the stream: zero the overlap tails and the alignment ring and the
  * block counter.  Waits for the plan's outstanding work. */
 int cdd_reset(cdd_plan plan);

@@ -282,3 +282,75 @@ def rel_rms(a: np.ndarray, b: np.ndarray) -> float:
     if den == 0.0:
         return 0.0 if num == 0.0 else float("inf")
     return math.sqrt(num / den)
+
+
+# --------------------------------------------------------------------------
+# Batched form: many DM trials over a band whose channel groups (tiers) use
+# different transform lengths
+# --------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class BatchGeometry:
+    n_chan: int
+    chan_bw_mhz: float
+    f_lo_mhz: np.ndarray      # [C]
+    dms: np.ndarray           # [D]
+    tier_nfft: tuple          # N of each tier, lowest-frequency tier first
+    tier_nov: tuple           # overlap of each tier
+    n_avg: int
+    tier_of: np.ndarray       # [C] tier index of each channel
+    shift: np.ndarray         # [D][C] alignment shifts, integrated samples
+
+    def hop(self, t: int) -> int:
+        return self.tier_nfft[t] - self.tier_nov[t]
+
+
+def batch_geometry(f_center_mhz: float, bandwidth_mhz: float, n_chan: int, dms, tier_nfft,
+                   n_avg: int) -> BatchGeometry:
+    """Geometry of the batched form.
+
+    The band is cut into len(tier_nfft) equal groups of channels, lowest
+    frequencies first; tier t coherently dedisperses with N_t points.  Its
+    overlap is N_t/32, raised if needed to the dispersion samples of the tier's
+    lowest channel at the largest DM (Sec. 2.2: at least the impulse response)
+    and rounded up to a multiple of n_avg.  Shifts follow the single-DM rule for
+    every DM (Sec. 1.2)."""
+    dms = np.asarray(dms, dtype=np.float64)
+    n_t = len(tier_nfft)
+    if n_chan % n_t or np.any(dms < 0) or dms.size == 0:
+        raise ValueError("channels must split evenly into tiers; DMs >= 0")
+    f_lo, chan_bw = channel_lower_edges(f_center_mhz, bandwidth_mhz, n_chan)
+    per = n_chan // n_t
+    nov = []
+    for t, n in enumerate(tier_nfft):
+        n_d = dispersion_samples(float(f_lo[t * per]), chan_bw, float(dms.max()))
+        ov = max(n // 32, int(math.ceil(n_d)))
+        ov = -(-ov // n_avg) * n_avg
+        if n & (n - 1) or n <= ov or (n - ov) % n_avg:
+            raise ValueError(f"tier {t}: N={n} does not fit overlap {ov} and n_avg {n_avg}")
+        nov.append(ov)
+    shift = np.stack([np.rint(-dispersion_delay_s(f_lo, f_lo[0], dm) * chan_bw * 1e6 / n_avg)
+                      for dm in dms]).astype(np.int64)
+    return BatchGeometry(n_chan, chan_bw, f_lo, dms, tuple(int(n) for n in tier_nfft),
+                         tuple(nov), int(n_avg), np.arange(n_chan) // per, shift)
+
+
+def dedisperse_batch(vin: np.ndarray, geo: BatchGeometry, channels=None, dm_index=None):
+    """Out[d][k][m] for every DM trial d: channel k runs the single-DM steps
+    (overlap-save with its tier's N and overlap, detection, integration,
+    alignment) once per DM.  All channels are cut to the same number of
+    outputs: whole segments of the longest hop."""
+    chans = range(geo.n_chan) if channels is None else list(channels)
+    dsel = range(len(geo.dms)) if dm_index is None else list(dm_index)
+    h_max = max(geo.hop(t) for t in range(len(geo.tier_nfft)))
+    n_samp = (vin.shape[0] // h_max) * h_max
+    out = np.zeros((len(dsel), len(chans), n_samp // geo.n_avg))
+    for ci, k in enumerate(chans):
+        t = int(geo.tier_of[k])
+        x = unpack(vin[:n_samp], k)
+        for di, d in enumerate(dsel):
+            filt = dedispersion_filter(float(geo.f_lo_mhz[k]), geo.chan_bw_mhz, float(geo.dms[d]),
+                                       geo.tier_nfft[t])
+            v = overlap_save(x, filt, geo.tier_nov[t])
+            out[di, ci] = align(integrate(detect(v), geo.n_avg), int(geo.shift[d, k]))
+    return out

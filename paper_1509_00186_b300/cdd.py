@@ -34,7 +34,9 @@ TAPER = {"none": 0, "hann": 1, "welch": 2}
 # every symbol include/cdd.h declares
 EXPORTS = ("cdd_plan_create", "cdd_plan_set", "cdd_plan_get", "cdd_plan_shifts", "cdd_execute",
            "cdd_execute_voltages", "cdd_execute_host", "cdd_execute_static", "cdd_reset",
-           "cdd_destroy", "cdd_strerror", "cdd_version")
+           "cdd_destroy", "cdd_strerror", "cdd_version",
+           "cdd_batch_create", "cdd_batch_set", "cdd_batch_get", "cdd_batch_tier",
+           "cdd_batch_shifts", "cdd_batch_execute", "cdd_batch_reset", "cdd_batch_destroy")
 
 
 class CddError(RuntimeError):
@@ -60,6 +62,16 @@ def _load() -> ctypes.CDLL:
     lib.cdd_execute_static.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_int, vp, vp, vp]
+    lib.cdd_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int]
+    lib.cdd_batch_set.argtypes = [vp, ctypes.c_int, ctypes.c_int64]
+    lib.cdd_batch_get.argtypes = [vp, ctypes.c_int, i64p]
+    lib.cdd_batch_tier.argtypes = [vp, ctypes.c_int, i64p, i64p, i64p, i64p]
+    lib.cdd_batch_shifts.argtypes = [vp, i64p]
+    lib.cdd_batch_execute.argtypes = [vp, vp, vp, vp]
+    lib.cdd_batch_reset.argtypes = [vp]
+    lib.cdd_batch_destroy.argtypes = [vp]
     lib.cdd_reset.argtypes = [vp]
     lib.cdd_destroy.argtypes = [vp]
     lib.cdd_strerror.argtypes = [ctypes.c_int]
@@ -150,6 +162,55 @@ def cdd_destroy(plan: int) -> None:
     _check(_lib.cdd_destroy(ctypes.c_void_p(plan)), "cdd_destroy")
 
 
+def cdd_batch_create(f_center_mhz, bandwidth_mhz, n_chan, dms, tier_nfft, n_avg) -> int:
+    h = ctypes.c_void_p()
+    d = (ctypes.c_double * len(dms))(*[float(x) for x in dms])
+    t = (ctypes.c_int * len(tier_nfft))(*[int(x) for x in tier_nfft])
+    _check(_lib.cdd_batch_create(ctypes.byref(h), float(f_center_mhz), float(bandwidth_mhz),
+                                 int(n_chan), d, len(dms), t, len(tier_nfft), int(n_avg)),
+           "cdd_batch_create")
+    return h.value
+
+
+def cdd_batch_set(batch: int, attr, value: int) -> None:
+    a = ATTR[attr] if isinstance(attr, str) else int(attr)
+    _check(_lib.cdd_batch_set(ctypes.c_void_p(batch), a, int(value)), "cdd_batch_set")
+
+
+def cdd_batch_get(batch: int, attr) -> int:
+    a = ATTR[attr] if isinstance(attr, str) else int(attr)
+    v = ctypes.c_int64()
+    _check(_lib.cdd_batch_get(ctypes.c_void_p(batch), a, ctypes.byref(v)), "cdd_batch_get")
+    return int(v.value)
+
+
+def cdd_batch_tier(batch: int, t: int):
+    vals = [ctypes.c_int64() for _ in range(4)]
+    _check(_lib.cdd_batch_tier(ctypes.c_void_p(batch), int(t), *[ctypes.byref(v) for v in vals]),
+           "cdd_batch_tier")
+    return tuple(int(v.value) for v in vals)
+
+
+def cdd_batch_shifts(batch: int, n_dm: int, n_chan: int):
+    buf = (ctypes.c_int64 * (n_dm * n_chan))()
+    _check(_lib.cdd_batch_shifts(ctypes.c_void_p(batch), buf), "cdd_batch_shifts")
+    return [list(buf[d * n_chan:(d + 1) * n_chan]) for d in range(n_dm)]
+
+
+def cdd_batch_execute(batch: int, d_in: int, d_out: int, stream: int = 0) -> None:
+    _check(_lib.cdd_batch_execute(ctypes.c_void_p(batch), ctypes.c_void_p(d_in),
+                                  ctypes.c_void_p(d_out), ctypes.c_void_p(stream)),
+           "cdd_batch_execute")
+
+
+def cdd_batch_reset(batch: int) -> None:
+    _check(_lib.cdd_batch_reset(ctypes.c_void_p(batch)), "cdd_batch_reset")
+
+
+def cdd_batch_destroy(batch: int) -> None:
+    _check(_lib.cdd_batch_destroy(ctypes.c_void_p(batch)), "cdd_batch_destroy")
+
+
 # ------------------------------------------------------------------ convenience
 
 class Plan:
@@ -225,6 +286,72 @@ class Plan:
     def close(self):
         if self.handle:
             cdd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Owning wrapper of a batched (many-DM, tiered-N) plan."""
+
+    def __init__(self, f_center_mhz, bandwidth_mhz, n_chan, dms, tier_nfft, n_avg,
+                 segments_per_block=None):
+        self.handle = cdd_batch_create(f_center_mhz, bandwidth_mhz, n_chan, dms, tier_nfft, n_avg)
+        try:
+            if segments_per_block is not None:
+                cdd_batch_set(self.handle, "segments_per_block", segments_per_block)
+        except Exception:
+            cdd_batch_destroy(self.handle)
+            raise
+        self.n_chan, self.n_dm, self.n_tiers = int(n_chan), len(dms), len(tier_nfft)
+
+    def get(self, attr) -> int:
+        return cdd_batch_get(self.handle, attr)
+
+    @property
+    def block_samples(self) -> int:
+        return self.get("block_samples")
+
+    @property
+    def n_out(self) -> int:
+        return self.get("n_out_per_block")
+
+    def tier(self, t):
+        return cdd_batch_tier(self.handle, t)
+
+    def shifts(self):
+        return cdd_batch_shifts(self.handle, self.n_dm, self.n_chan)
+
+    def execute(self, vin, out=None):
+        import torch
+        if vin.dtype != torch.int8 or tuple(vin.shape) != (self.block_samples, self.n_chan, 2) \
+                or not vin.is_contiguous() or vin.device.type != "cuda":
+            raise ValueError(f"input must be contiguous device int8 [{self.block_samples}][{self.n_chan}][2]")
+        if out is None:
+            out = torch.empty((self.n_dm, self.n_chan, self.n_out), dtype=torch.float32, device=vin.device)
+        if out.dtype != torch.float32 or tuple(out.shape) != (self.n_dm, self.n_chan, self.n_out) \
+                or not out.is_contiguous() or out.device.type != "cuda":
+            raise ValueError("output must be contiguous device float32 [n_dm][C][n_out]")
+        cdd_batch_execute(self.handle, vin.data_ptr(), out.data_ptr(),
+                          torch.cuda.current_stream(vin.device).cuda_stream)
+        return out
+
+    def reset(self):
+        cdd_batch_reset(self.handle)
+
+    def close(self):
+        if self.handle:
+            cdd_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

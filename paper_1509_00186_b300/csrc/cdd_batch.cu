@@ -1,0 +1,635 @@
+// cdd_batch.cu -- the batched form: many DM trials share each segment's
+// forward transform, over a band whose channel groups (tiers) use different
+// transform lengths.
+//
+// One CTA per (channel, segment) of a tier: int8 unpack and the forward radix
+// passes as in the single-DM kernel, the spectrum (scaled by 1/N) parked in a
+// global scratch row that stays in L2, then for every DM trial: the chirp of
+// that DM applied on the fly (its phase is DM times a per-bin FP64 table of the
+// DM = 1 phase held as two floats, so the product keeps FP64-like accuracy),
+// the inverse radix passes, detection, integration, discard and the aligned
+// store into the DM's output plane.  Sec. 2.1 Eq. 3 (chirp), Sec. 2.2
+// (overlap-save), Sec. 3.1 (detect, integrate), Sec. 1.2 (alignment).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/cdd.h"
+#include "cdd_fft.cuh"
+#include "cdd_internal.h"
+#include "cdd_passes.cuh"
+
+namespace cdd {
+namespace {
+
+using namespace passes;
+
+struct BatchArgs {
+  const char2* in_cm;       // [C][rows] channel-major block
+  long long rows;
+  float* out;               // [n_dm][C][n_out]
+  const float2* t1;         // [n_tchan][N] DM = 1 chirp phase in turns (hi, lo), chirp-pass order
+  const float2* tw;         // twiddles of this N
+  const char2* tail_rd;     // [C][tail_stride] last samples of the previous block
+  char2* tail_wr;
+  const float* ring_rd;     // [n_dm][C][r_max] previous block's last r outputs
+  float* ring_wr;
+  const int* shift;         // [n_dm][C]
+  const float2* dms;        // [n_dm] DM as (hi, lo)
+  float2* xs;               // [n_tchan * q][N] spectra
+  int n_chan, chan0, n_tchan, n_ov, hop, n_avg, q, n_out, n_dm, r_max, tail_stride;
+};
+
+// exp(-2 pi i * DM * T1): the product and its reduction modulo one turn in
+// two-float arithmetic, then the hardware sine/cosine on [-pi, pi].
+__device__ __forceinline__ float2 dm_chirp(float2 t1, float2 dm) {
+  const float p = dm.x * t1.x;
+  const float e = fmaf(dm.x, t1.x, -p);                    // rounding error of the product
+  const float lo = fmaf(dm.x, t1.y, fmaf(dm.y, t1.x, e));
+  const float frac = (p - rintf(p)) + lo;
+  float sn, cs;
+  __sincosf(6.28318530717958647692f * frac, &sn, &cs);
+  return make_float2(cs, -sn);
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(Cfg<LOGN>::THREADS, Cfg<LOGN>::MINB)
+batch_kernel(const BatchArgs a) {
+  using PL = PassPlan<LOGN>;
+  using CF = Cfg<LOGN>;
+  constexpr int N = PL::N;
+  constexpr int T = PL::T;
+  constexpr int R0 = PL::R(0);
+  constexpr int RL = PL::RL;
+  constexpr int NG = N / RL;
+  constexpr int PERC = NG / T;
+  static_assert(RL <= 16, "stride-1 groups must not cross a padding word");
+
+  extern __shared__ float2 smem[];
+  const int g = threadIdx.x / T;
+  const int lt = threadIdx.x % T;
+  float2* buf = smem + g * CF::SEG_F2;
+  const int w = blockIdx.x * CF::G + g;
+  const bool active = w < a.n_tchan * a.q;
+  const int kt = active ? w % a.n_tchan : 0;     // channel within the tier, fastest
+  const int s = active ? w / a.n_tchan : 0;
+  const int k = a.chan0 + kt;
+  float2* pb0 = buf + pad(lt);
+  float2 v[R0];
+
+  // ---- pass 0, forward, straight from the channel-major block
+  if (active) {
+    const long long row0 = (long long)s * a.hop - a.n_ov;
+    const unsigned short* src = reinterpret_cast<const unsigned short*>(a.in_cm) + (long long)k * a.rows;
+    const unsigned short* tail = reinterpret_cast<const unsigned short*>(a.tail_rd) + (long long)k * a.tail_stride;
+    unsigned short c[R0];
+#pragma unroll
+    for (int j = 0; j < R0; ++j) {
+      const long long row = row0 + lt + T * j;
+      c[j] = __ldg(row >= 0 ? src + row : tail + (row + a.n_ov));
+    }
+    if (s == a.q - 1 && a.n_ov > 0) {
+      unsigned short* tout = reinterpret_cast<unsigned short*>(a.tail_wr) + (long long)k * a.tail_stride;
+#pragma unroll
+      for (int j = 0; j < R0; ++j) {
+        const int n = lt + T * j;
+        if (n >= N - a.n_ov) tout[n - (N - a.n_ov)] = c[j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < R0; ++j) v[j] = unpack_i8x2(c[j]);
+    dft<R0, -1>(v);
+#pragma unroll
+    for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], __ldg(&a.tw[kk * T + lt]));
+#pragma unroll
+    for (int kk = 0; kk < R0; ++kk) pb0[poff<T>(kk)] = v[kk];
+  }
+  __syncthreads();
+  static_for<1, PL::P - 1>([&](auto P_) {
+    if (active) fwd_pass<LOGN, decltype(P_)::value>(buf, a.tw, lt);
+    __syncthreads();
+  });
+
+  // ---- last forward radix: the spectrum, scaled by 1/N, to this segment's scratch row
+  float2* xk = a.xs + (size_t)w * N;
+  if (active) {
+#pragma unroll 1
+    for (int i = 0; i < PERC; ++i) {
+      const int q = lt + i * T;
+      const float2* pb = buf + pad(q * RL);
+      float2 x[RL];
+#pragma unroll
+      for (int j = 0; j < RL; ++j) x[j] = pb[j];
+      dft<RL, -1>(x);
+#pragma unroll
+      for (int kk = 0; kk < RL; ++kk)
+        xk[kk * NG + q] = make_float2(x[kk].x * (1.0f / N), x[kk].y * (1.0f / N));
+    }
+  }
+
+  const float2* t1k = a.t1 + (size_t)kt * N;
+  const int n_int = a.hop / a.n_avg;
+  float* pw = reinterpret_cast<float*>(buf);
+#pragma unroll 1
+  for (int d = 0; d < a.n_dm; ++d) {
+    __syncthreads();                          // buf is free again
+    // ---- chirp of DM d and first inverse radix (each thread re-reads its own rows)
+    if (active) {
+      const float2 dm = a.dms[d];
+#pragma unroll 1
+      for (int i = 0; i < PERC; ++i) {
+        const int q = lt + i * T;
+        float2 x[RL];
+#pragma unroll
+        for (int kk = 0; kk < RL; ++kk)
+          x[kk] = cmul(xk[kk * NG + q], dm_chirp(__ldg(&t1k[kk * NG + q]), dm));
+        dft<RL, 1>(x);
+        float2* pb = buf + pad(q * RL);
+#pragma unroll
+        for (int j = 0; j < RL; ++j) pb[j] = x[j];
+      }
+    }
+    __syncthreads();
+    static_for<1, PL::P - 1>([&](auto I_) {
+      if (active) inv_pass<LOGN, PL::P - 1 - decltype(I_)::value>(buf, a.tw, lt);
+      __syncthreads();
+    });
+    // ---- pass 0, inverse, detection
+    if (active) {
+#pragma unroll
+      for (int kk = 0; kk < R0; ++kk) v[kk] = pb0[poff<T>(kk)];
+#pragma unroll
+      for (int kk = 1; kk < R0; ++kk) v[kk] = cmulc(v[kk], __ldg(&a.tw[kk * T + lt]));
+      dft<R0, 1>(v);
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int j = 0; j < R0; ++j) {
+        const int n = lt + T * j;
+        pw[n + (n >> 5)] = fmaf(v[j].x, v[j].x, v[j].y * v[j].y);
+      }
+    }
+    __syncthreads();
+    // ---- integrate, discard the overlap, align into DM d's plane
+    if (active) {
+      const size_t row = (size_t)d * a.n_chan + k;
+      const int r = __ldg(&a.shift[row]);
+      float* outk = a.out + row * a.n_out;
+      float* rw = a.ring_wr + row * a.r_max;
+      for (int m = lt; m < n_int; m += T) {
+        const int n0 = a.n_ov + m * a.n_avg;
+        float acc = 0.f;
+        for (int i = 0; i < a.n_avg; ++i) acc += pw[(n0 + i) + ((n0 + i) >> 5)];
+        const int dst = s * n_int + m + r;     // aligned index within this block
+        if (dst < a.n_out) outk[dst] = acc;
+        else rw[dst - a.n_out] = acc;          // the next block's first r outputs
+      }
+      if (s == 0) {
+        const float* rr = a.ring_rd + row * a.r_max;
+        for (int m = lt; m < r; m += T) outk[m] = rr[m];
+      }
+    }
+  }
+}
+
+// T1[kt][idx]: Eq. 3 phase in turns at DM = 1 for channel chan0 + kt and the
+// bin held at table index idx (FP64, split into two floats).
+template <int LOGN>
+__global__ void t1_table_kernel(float2* t1, int n_tchan, int chan0, double f_lo0, double chan_bw) {
+  using PL = PassPlan<LOGN>;
+  constexpr int N = PL::N;
+  constexpr int NG = N / PL::RL;
+  const long long total = (long long)n_tchan * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int kt = (int)(e / N);
+    const int idx = (int)(e % N);
+    const int pos = (idx % NG) * PL::RL + idx / NG;
+    const int bin = position_to_bin<LOGN>(pos);
+    const int sbin = bin < N / 2 ? bin : bin - N;
+    const double f_lo = f_lo0 + chan_bw * (chan0 + kt);
+    const double f_l = sbin * (chan_bw / N) + 0.5 * chan_bw;
+    const double turns = kDispD * 1e6 * f_l * f_l / ((f_l + f_lo) * f_lo * f_lo);
+    const float hi = (float)turns;
+    t1[e] = make_float2(hi, (float)(turns - (double)hi));
+  }
+}
+
+template <int LOGN>
+cudaError_t launch_batch_t(const BatchArgs& a, cudaStream_t s) {
+  using CF = Cfg<LOGN>;
+  static bool attr_set[128] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  if (!attr_set[dev]) {
+    e = cudaFuncSetAttribute(batch_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CF::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  const long long work = (long long)a.n_tchan * a.q;
+  batch_kernel<LOGN><<<(unsigned)((work + CF::G - 1) / CF::G), CF::THREADS, CF::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int LOGN>
+cudaError_t launch_t1_t(float2* t1, int n_tchan, int chan0, double f_lo0, double chan_bw,
+                        cudaStream_t s) {
+  const long long total = (long long)n_tchan << LOGN;
+  const unsigned grid = (unsigned)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
+  t1_table_kernel<LOGN><<<grid, 256, 0, s>>>(t1, n_tchan, chan0, f_lo0, chan_bw);
+  return cudaGetLastError();
+}
+
+#define CDD_BATCH_CASES(X) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14)
+
+cudaError_t launch_batch(int logn, const BatchArgs& a, cudaStream_t s) {
+  switch (logn) {
+#define X(L) case L: return launch_batch_t<L>(a, s);
+    CDD_BATCH_CASES(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_t1(int logn, float2* t1, int n_tchan, int chan0, double f_lo0, double chan_bw,
+                      cudaStream_t s) {
+  switch (logn) {
+#define X(L) case L: return launch_t1_t<L>(t1, n_tchan, chan0, f_lo0, chan_bw, s);
+    CDD_BATCH_CASES(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+}  // namespace cdd
+
+// ------------------------------------------------------------------ host side
+
+struct cdd_batch_s {
+  struct Tier {
+    int n_fft = 0, logn = 0, n_ov = 0, hop = 0, chan0 = 0, n_tchan = 0;
+    float2* d_tw = nullptr;
+    float2* d_t1 = nullptr;
+  };
+  double f_center = 0, bandwidth = 0, chan_bw = 0, f_lo0 = 0;
+  int n_chan = 0, n_avg = 0, n_dm = 0;
+  std::vector<double> dms;
+  std::vector<Tier> tiers;
+  std::vector<int64_t> shift;            // [n_dm][C]
+  int64_t r_max = 0;
+  int hop_max = 0, n_ov_max = 0;
+  int q = 1;                             // block = q * hop_max samples per channel
+  bool committed = false;
+  int device = -1;
+  int sticky = CDD_OK;
+  char2* d_in_cm = nullptr;
+  char2* d_tail[2] = {nullptr, nullptr};
+  float* d_ring[2] = {nullptr, nullptr};
+  int* d_shift = nullptr;
+  float2* d_dms = nullptr;
+  float2* d_xs = nullptr;
+  size_t bytes_device = 0;
+  int parity = 0;
+  int64_t blocks = 0;
+  int last_launches = 0;
+};
+
+namespace {
+
+constexpr double kDispDHost = 4.148808e3;   // s MHz^2 cm^3 / pc (Eq. 3)
+
+int bfail(cdd_batch b, cudaError_t e) {
+  if (e == cudaSuccess) return CDD_OK;
+  b->sticky = CDD_ECUDA;
+  return CDD_ECUDA;
+}
+
+#define BTRY(b, call)                              \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return bfail(b, e_);    \
+  } while (0)
+
+template <class T>
+int balloc(cdd_batch b, T** p, size_t bytes) {
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    *p = nullptr;
+    return CDD_ENOMEM;
+  }
+  if (e != cudaSuccess) return bfail(b, e);
+  b->bytes_device += bytes;
+  return CDD_OK;
+}
+
+int64_t block_samples(const cdd_batch b) { return (int64_t)b->q * b->hop_max; }
+int64_t n_out(const cdd_batch b) { return block_samples(b) / b->n_avg; }
+
+void bfree(cdd_batch b) {
+  for (auto& t : b->tiers) {
+    cudaFree(t.d_tw);
+    cudaFree(t.d_t1);
+  }
+  cudaFree(b->d_in_cm);
+  cudaFree(b->d_tail[0]);
+  cudaFree(b->d_tail[1]);
+  cudaFree(b->d_ring[0]);
+  cudaFree(b->d_ring[1]);
+  cudaFree(b->d_shift);
+  cudaFree(b->d_dms);
+  cudaFree(b->d_xs);
+}
+
+int bzero_state(cdd_batch b, cudaStream_t s) {
+  const size_t tb = (size_t)b->n_chan * (b->n_ov_max > 0 ? b->n_ov_max : 1) * sizeof(char2);
+  const size_t rb = (size_t)b->n_dm * b->n_chan * (b->r_max > 0 ? b->r_max : 1) * sizeof(float);
+  for (int i = 0; i < 2; ++i) {
+    BTRY(b, cudaMemsetAsync(b->d_tail[i], 0, tb, s));
+    BTRY(b, cudaMemsetAsync(b->d_ring[i], 0, rb, s));
+  }
+  b->parity = 0;
+  b->blocks = 0;
+  return CDD_OK;
+}
+
+int bcommit_once(cdd_batch b) {
+  BTRY(b, cudaGetDevice(&b->device));
+  if (n_out(b) < b->r_max) return CDD_EINVAL;        // a block must outlast the largest delay
+  int rc;
+  const int64_t rows = block_samples(b);
+  if ((rc = balloc(b, &b->d_in_cm, (size_t)b->n_chan * rows * sizeof(char2)))) return rc;
+  const size_t tb = (size_t)b->n_chan * (b->n_ov_max > 0 ? b->n_ov_max : 1) * sizeof(char2);
+  const size_t rb = (size_t)b->n_dm * b->n_chan * (b->r_max > 0 ? b->r_max : 1) * sizeof(float);
+  for (int i = 0; i < 2; ++i) {
+    if ((rc = balloc(b, &b->d_tail[i], tb))) return rc;
+    if ((rc = balloc(b, &b->d_ring[i], rb))) return rc;
+  }
+  if ((rc = balloc(b, &b->d_shift, b->shift.size() * sizeof(int)))) return rc;
+  if ((rc = balloc(b, &b->d_dms, (size_t)b->n_dm * sizeof(float2)))) return rc;
+  size_t xs = 0;
+  for (auto& t : b->tiers) {
+    const size_t segs = (size_t)t.n_tchan * (rows / t.hop);
+    if (segs * t.n_fft > xs) xs = segs * t.n_fft;
+    if ((rc = balloc(b, &t.d_tw, (size_t)cdd::twiddle_table_len(t.logn) * sizeof(float2)))) return rc;
+    if ((rc = balloc(b, &t.d_t1, (size_t)t.n_tchan * t.n_fft * sizeof(float2)))) return rc;
+  }
+  if ((rc = balloc(b, &b->d_xs, xs * sizeof(float2)))) return rc;
+
+  std::vector<int> sh(b->shift.begin(), b->shift.end());
+  BTRY(b, cudaMemcpy(b->d_shift, sh.data(), sh.size() * sizeof(int), cudaMemcpyHostToDevice));
+  std::vector<float2> dm2(b->n_dm);
+  for (int d = 0; d < b->n_dm; ++d) {
+    const float hi = (float)b->dms[d];
+    dm2[d] = make_float2(hi, (float)(b->dms[d] - (double)hi));
+  }
+  BTRY(b, cudaMemcpy(b->d_dms, dm2.data(), dm2.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  cudaStream_t s;
+  BTRY(b, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaError_t e = cudaSuccess;
+  for (auto& t : b->tiers) {
+    if (e == cudaSuccess) e = cdd::launch_twiddle_table(t.logn, t.d_tw, s);
+    if (e == cudaSuccess) e = cdd::launch_t1(t.logn, t.d_t1, t.n_tchan, t.chan0, b->f_lo0, b->chan_bw, s);
+  }
+  if (e == cudaSuccess && (rc = bzero_state(b, s)) != CDD_OK) {
+    cudaStreamDestroy(s);
+    return rc;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess) return bfail(b, e);
+  b->committed = true;
+  return CDD_OK;
+}
+
+int bprepare(cdd_batch b) {
+  if (!b) return CDD_EINVAL;
+  if (b->sticky) return b->sticky;
+  if (!b->committed) {
+    const int rc = bcommit_once(b);
+    if (rc != CDD_OK) {
+      b->sticky = rc;
+      return rc;
+    }
+  }
+  int dev = -1;
+  BTRY(b, cudaGetDevice(&dev));
+  return dev == b->device ? CDD_OK : CDD_EINVAL;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cdd_batch_create(cdd_batch* out, double f_center_mhz, double bandwidth_mhz, int n_chan,
+                     const double* dms, int n_dm, const int* tier_nfft, int n_tiers, int n_avg) {
+  if (!out) return CDD_EINVAL;
+  *out = nullptr;
+  if (!dms || n_dm <= 0 || !tier_nfft || n_tiers <= 0 || n_chan <= 0 || n_chan % n_tiers ||
+      n_avg <= 0 || !(f_center_mhz > 0) || !(bandwidth_mhz > 0))
+    return CDD_EINVAL;
+  cdd_batch b = new (std::nothrow) cdd_batch_s();
+  if (!b) return CDD_ENOMEM;
+  b->f_center = f_center_mhz;
+  b->bandwidth = bandwidth_mhz;
+  b->n_chan = n_chan;
+  b->n_avg = n_avg;
+  b->n_dm = n_dm;
+  b->chan_bw = bandwidth_mhz / n_chan;
+  b->f_lo0 = f_center_mhz - bandwidth_mhz / 2.0;
+  b->dms.assign(dms, dms + n_dm);
+  double dm_max = 0;
+  for (double d : b->dms) {
+    if (!(d >= 0) || !isfinite(d)) {
+      delete b;
+      return CDD_EINVAL;
+    }
+    dm_max = d > dm_max ? d : dm_max;
+  }
+  if (!(b->f_lo0 > 0)) {
+    delete b;
+    return CDD_EINVAL;
+  }
+  const int per = n_chan / n_tiers;
+  int rc = CDD_OK;
+  for (int t = 0; t < n_tiers && rc == CDD_OK; ++t) {
+    cdd_batch_s::Tier tr;
+    tr.n_fft = tier_nfft[t];
+    tr.chan0 = t * per;
+    tr.n_tchan = per;
+    // overlap: N/32, raised to the tier's lowest-channel smear at the largest DM,
+    // rounded up to a multiple of n_avg
+    const double f = b->f_lo0 + b->chan_bw * tr.chan0;
+    const double n_d = kDispDHost * dm_max * (pow(f, -2.0) - pow(f + b->chan_bw, -2.0)) * b->chan_bw * 1e6;
+    long long ov = tr.n_fft / 32;
+    if ((long long)ceil(n_d) > ov) ov = (long long)ceil(n_d);
+    ov = (ov + n_avg - 1) / n_avg * n_avg;
+    if (tr.n_fft < 64 || tr.n_fft > 16384 || (tr.n_fft & (tr.n_fft - 1))) rc = CDD_EUNSUPPORTED;
+    else if (tr.n_fft <= ov || (tr.n_fft - ov) % n_avg) rc = CDD_EINVAL;
+    tr.n_ov = (int)ov;
+    tr.hop = tr.n_fft - tr.n_ov;
+    while ((1 << tr.logn) < tr.n_fft) ++tr.logn;
+    b->tiers.push_back(tr);
+    if (tr.hop > b->hop_max) b->hop_max = tr.hop;
+    if (tr.n_ov > b->n_ov_max) b->n_ov_max = tr.n_ov;
+  }
+  for (auto& t : b->tiers)
+    if (rc == CDD_OK && b->hop_max % t.hop) rc = CDD_EINVAL;   // hops must nest
+  if (rc == CDD_OK) {
+    b->shift.resize((size_t)n_dm * n_chan);
+    for (int d = 0; d < n_dm && rc == CDD_OK; ++d) {
+      cdd::Geometry g{};
+      g.f_lo0 = b->f_lo0;
+      g.chan_bw = b->chan_bw;
+      g.dm = b->dms[d];
+      g.n_avg = n_avg;
+      for (int k = 0; k < n_chan; ++k) {
+        const int64_t r = cdd::shift_of(g, k);
+        if (r < 0) {
+          rc = CDD_EINVAL;
+          break;
+        }
+        b->shift[(size_t)d * n_chan + k] = r;
+        if (r > b->r_max) b->r_max = r;
+      }
+    }
+  }
+  if (rc != CDD_OK) {
+    delete b;
+    return rc;
+  }
+  // default block: the shortest whole number of longest hops that outlasts every delay
+  b->q = (int)((b->r_max * n_avg + b->hop_max - 1) / b->hop_max);
+  if (b->q < 1) b->q = 1;
+  if (n_out(b) < b->r_max) b->q += 1;
+  *out = b;
+  return CDD_OK;
+}
+
+int cdd_batch_set(cdd_batch b, int attr, int64_t value) {
+  if (!b) return CDD_EINVAL;
+  if (b->committed) return CDD_ESTATE;
+  if (attr != CDD_ATTR_SEGMENTS_PER_BLOCK) return CDD_EINVAL;
+  if (value < 1 || value * b->hop_max * b->n_chan > ((int64_t)1 << 40)) return CDD_EINVAL;
+  if (value * b->hop_max / b->n_avg < b->r_max) return CDD_EINVAL;
+  for (auto& t : b->tiers)
+    if ((int64_t)t.n_tchan * (value * b->hop_max / t.hop) >= ((int64_t)1 << 31)) return CDD_EINVAL;
+  b->q = (int)value;
+  return CDD_OK;
+}
+
+int cdd_batch_get(cdd_batch b, int attr, int64_t* v) {
+  if (!b || !v) return CDD_EINVAL;
+  switch (attr) {
+    case CDD_ATTR_SEGMENTS_PER_BLOCK: *v = b->q; break;
+    case CDD_ATTR_BLOCK_SAMPLES: *v = block_samples(b); break;
+    case CDD_ATTR_N_OUT_PER_BLOCK: *v = n_out(b); break;
+    case CDD_ATTR_R_MAX: *v = b->r_max; break;
+    case CDD_ATTR_BYTES_DEVICE: *v = (int64_t)b->bytes_device; break;
+    case CDD_ATTR_BLOCKS_DONE: *v = b->blocks; break;
+    case CDD_ATTR_KERNEL_LAUNCHES: *v = b->last_launches; break;
+    case CDD_ATTR_N_CHAN: *v = b->n_chan; break;
+    case CDD_ATTR_N_AVG: *v = b->n_avg; break;
+    case CDD_ATTR_HOP: *v = b->hop_max; break;
+    default: return CDD_EINVAL;
+  }
+  return CDD_OK;
+}
+
+int cdd_batch_tier(cdd_batch b, int t, int64_t* n_fft, int64_t* n_ov, int64_t* chan0,
+                   int64_t* n_tchan) {
+  if (!b || t < 0 || t >= (int)b->tiers.size()) return CDD_EINVAL;
+  const auto& tr = b->tiers[t];
+  if (n_fft) *n_fft = tr.n_fft;
+  if (n_ov) *n_ov = tr.n_ov;
+  if (chan0) *chan0 = tr.chan0;
+  if (n_tchan) *n_tchan = tr.n_tchan;
+  return CDD_OK;
+}
+
+int cdd_batch_shifts(cdd_batch b, int64_t* shifts) {
+  if (!b || !shifts) return CDD_EINVAL;
+  memcpy(shifts, b->shift.data(), b->shift.size() * sizeof(int64_t));
+  return CDD_OK;
+}
+
+int cdd_batch_execute(cdd_batch b, const int8_t* d_in, float* d_out, cudaStream_t stream) {
+  if (!b || !d_in || !d_out) return CDD_EINVAL;
+  int rc = bprepare(b);
+  if (rc) return rc;
+  const int64_t rows = block_samples(b);
+  BTRY(b, cdd::launch_corner_turn(reinterpret_cast<const char2*>(d_in), b->d_in_cm, rows, b->n_chan, stream));
+  for (auto& t : b->tiers) {
+    cdd::BatchArgs a;
+    a.in_cm = b->d_in_cm;
+    a.rows = rows;
+    a.out = d_out;
+    a.t1 = t.d_t1;
+    a.tw = t.d_tw;
+    a.tail_rd = b->d_tail[b->parity];
+    a.tail_wr = b->d_tail[b->parity ^ 1];
+    a.ring_rd = b->d_ring[b->parity];
+    a.ring_wr = b->d_ring[b->parity ^ 1];
+    a.shift = b->d_shift;
+    a.dms = b->d_dms;
+    a.xs = b->d_xs;
+    a.n_chan = b->n_chan;
+    a.chan0 = t.chan0;
+    a.n_tchan = t.n_tchan;
+    a.n_ov = t.n_ov;
+    a.hop = t.hop;
+    a.n_avg = b->n_avg;
+    a.q = (int)(rows / t.hop);
+    a.n_out = (int)n_out(b);
+    a.n_dm = b->n_dm;
+    a.r_max = (int)(b->r_max > 0 ? b->r_max : 1);
+    a.tail_stride = b->n_ov_max > 0 ? b->n_ov_max : 1;
+    BTRY(b, cdd::launch_batch(t.logn, a, stream));
+  }
+  b->parity ^= 1;
+  b->blocks += 1;
+  b->last_launches = 1 + (int)b->tiers.size();
+  return CDD_OK;
+}
+
+int cdd_batch_reset(cdd_batch b) {
+  if (!b) return CDD_EINVAL;
+  if (b->sticky) return b->sticky;
+  if (!b->committed) {
+    b->parity = 0;
+    b->blocks = 0;
+    return CDD_OK;
+  }
+  BTRY(b, cudaDeviceSynchronize());
+  cudaStream_t s;
+  BTRY(b, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  const int rc = bzero_state(b, s);
+  const cudaError_t e = cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (rc) return rc;
+  return bfail(b, e);
+}
+
+int cdd_batch_destroy(cdd_batch b) {
+  if (!b) return CDD_OK;
+  if (b->device >= 0) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    bfree(b);
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  delete b;
+  return CDD_OK;
+}
+
+}  // extern "C"

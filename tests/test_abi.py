@@ -131,3 +131,47 @@ def test_static_entry_rejects_before_touching_the_gpu(cdd):
     with pytest.raises(cdd.CddError) as ei:
         cdd.cdd_execute_static(325.0, 32.0, 512, 50.0, 8192, 16, 0, 0, 1, 1)
     assert ei.value.code == cdd.CDD_EINVAL
+
+
+BATCH_GEOMS = [
+    (650.0, 200.0, 2048, 20.0 + 0.5 * np.arange(64), (16384, 8192, 4096, 2048), 16),
+    (650.0, 6.25, 64, [5.0, 10.0, 15.0, 20.0], (2048, 1024, 512, 256), 4),
+    (325.0, 0.25, 4, [20.0], (256,), 4),
+]
+
+
+@pytest.mark.parametrize("geo", BATCH_GEOMS)
+def test_batch_geometry_matches_oracle(cdd, geo):
+    f_c, bw, n_chan, dms, tiers, n_avg = geo
+    g = O.batch_geometry(f_c, bw, n_chan, dms, tiers, n_avg)
+    b = cdd.cdd_batch_create(f_c, bw, n_chan, list(dms), tiers, n_avg)
+    try:
+        for t in range(len(tiers)):
+            n_fft, n_ov, chan0, n_t = cdd.cdd_batch_tier(b, t)
+            assert (n_fft, n_ov) == (g.tier_nfft[t], g.tier_nov[t])
+            assert chan0 == t * (n_chan // len(tiers)) and n_t == n_chan // len(tiers)
+        assert np.array_equal(np.array(cdd.cdd_batch_shifts(b, len(dms), n_chan)), g.shift)
+        assert cdd.cdd_batch_get(b, "r_max") == int(g.shift.max())
+        n_out = cdd.cdd_batch_get(b, "n_out_per_block")
+        assert n_out >= int(g.shift.max())
+        assert cdd.cdd_batch_get(b, "block_samples") % max(g.hop(t) for t in range(len(tiers))) == 0
+    finally:
+        cdd.cdd_batch_destroy(b)
+
+
+def test_batch_rejects_bad_requests(cdd):
+    with pytest.raises(cdd.CddError):              # hops that do not nest
+        cdd.cdd_batch_create(650.0, 6.25, 64, [51.5], (1024, 512, 256, 128), 4)
+    with pytest.raises(cdd.CddError) as ei:        # tier N beyond the single-CTA shapes
+        cdd.cdd_batch_create(650.0, 6.25, 64, [5.0], (32768, 16384), 4)
+    assert ei.value.code == cdd.CDD_EUNSUPPORTED
+    with pytest.raises(cdd.CddError):              # channels do not split into tiers
+        cdd.cdd_batch_create(650.0, 6.25, 63, [5.0], (2048, 1024), 4)
+    b = cdd.cdd_batch_create(650.0, 6.25, 64, [5.0, 20.0], (2048, 1024, 512, 256), 4)
+    try:
+        r_max = cdd.cdd_batch_get(b, "r_max")
+        with pytest.raises(cdd.CddError):          # a block shorter than the largest delay
+            cdd.cdd_batch_set(b, "segments_per_block", 1) if r_max > 1984 // 4 else \
+                cdd.cdd_batch_set(b, "segments_per_block", 0)
+    finally:
+        cdd.cdd_batch_destroy(b)

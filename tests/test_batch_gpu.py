@@ -1,0 +1,76 @@
+"""Batched form on the GPU (many DM trials sharing each forward transform,
+tiered N) against the FP64 oracle, relative RMS <= 1e-5 per DM plane."""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import complex_int8_voltages
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+SMALL = (650.0, 6.25, 64, [5.0, 10.0, 15.0, 20.0], (2048, 1024, 512, 256), 4)
+
+
+def run_batch(vin, args, q, n_blocks):
+    import torch
+    from paper_1509_00186_b300.cdd import Batch
+    with Batch(*args, segments_per_block=q) as b:
+        bs = b.block_samples
+        x = torch.from_numpy(np.ascontiguousarray(vin[: bs * n_blocks])).cuda()
+        outs = [b.execute(x[i * bs:(i + 1) * bs]) for i in range(n_blocks)]
+        torch.cuda.synchronize()
+        return torch.cat(outs, 2).cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def small(cuda_device):
+    g = O.batch_geometry(*SMALL)
+    vin = complex_int8_voltages(3, 1984 * 8, 64, 20.0)
+    want = O.dedisperse_batch(vin, g)
+    return vin, g, want
+
+
+def test_small_batch_matches_oracle(small):
+    vin, g, want = small
+    got = run_batch(vin, SMALL, 2, 4)
+    assert got.shape == want.shape == (4, 64, 1984 * 8 // 4)
+    for d in range(4):
+        assert O.rel_rms(got[d], want[d]) <= TOL, d
+        for k in (0, 17, 40, 63):                 # one channel in each tier
+            assert O.rel_rms(got[d, k], want[d, k]) <= TOL, (d, k)
+    # the last tier (N = 256) and the first (N = 2048) both carry the shifts
+    for d in range(4):
+        r = int(g.shift[d, 63])
+        assert np.all(got[d, 63, :r] == 0.0)
+
+
+def test_batch_block_split_is_bit_identical(small):
+    vin, g, _ = small
+    a = run_batch(vin, SMALL, 8, 1)
+    b = run_batch(vin, SMALL, 2, 4)
+    c = run_batch(vin, SMALL, 1, 8)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+@pytest.mark.slow
+def test_upgraded_gmrt_batch_full_size_sampled(cuda_device):
+    """200 MHz at 650 MHz, 2048 channels, 64 DM trials 20.0..51.5, tiers
+    N = 16384 / 8192 / 4096 / 2048, 4 s, one block of 24 longest hops; sampled
+    (DM, channel) pairs against the oracle."""
+    import torch
+    from paper_1509_00186_b300.cdd import Batch
+    dms = list(20.0 + 0.5 * np.arange(64))
+    args = (650.0, 200.0, 2048, dms, (16384, 8192, 4096, 2048), 16)
+    g = O.batch_geometry(*args)
+    n_samp = int(round(4.0 * 200e6 / 2048))        # 390,625
+    q = n_samp // g.hop(0)
+    vin = complex_int8_voltages(4, q * g.hop(0), 2048, 20.0)
+    with Batch(*args, segments_per_block=q) as b:
+        out = b.execute(torch.from_numpy(vin).cuda())
+        pairs = [(0, 0), (63, 511), (30, 512), (5, 1500), (63, 2047), (17, 1024)]
+        got = np.stack([out[d, k].cpu().numpy() for d, k in pairs])
+        assert bool(torch.isfinite(out).all())
+    for i, (d, k) in enumerate(pairs):
+        want = O.dedisperse_batch(vin, g, channels=[k], dm_index=[d])[0, 0]
+        assert O.rel_rms(got[i], want) <= TOL, (d, k)

@@ -256,3 +256,51 @@ def test_oracle_digest_unchanged():
     assert np.allclose(got["row_max"], want["row_max"], rtol=1e-12, atol=0)
     for k, v in want["samples"].items():
         assert np.allclose(got["samples"][k], v, rtol=1e-12, atol=1e-9)
+
+
+# ---------------------------------------------------------------- batched form
+
+def test_batch_geometry_of_the_upgraded_gmrt_shape():
+    """200 MHz at 650 MHz, 2048 channels, DM 20..51.5, tiers N = 16384..2048:
+    overlaps N/32 (larger than the smear), hops that nest."""
+    dms = 20.0 + 0.5 * np.arange(64)
+    g = O.batch_geometry(650.0, 200.0, 2048, dms, (16384, 8192, 4096, 2048), 16)
+    assert g.tier_nov == (512, 256, 128, 64)
+    hops = [g.hop(t) for t in range(4)]
+    assert hops == [15872, 7936, 3968, 1984] and all(hops[0] % h == 0 for h in hops)
+    n_d = O.dispersion_samples(550.0, 200.0 / 2048, 51.5)
+    assert 20 < n_d < 64
+    assert g.shift.shape == (64, 2048) and np.all(g.shift[:, 0] == 0)
+    # the shift grows with DM and falls to the top of the band like the delay law
+    top = (textbook_delay_s(550.0, 51.5) - textbook_delay_s(749.90234375, 51.5)) * (200e6 / 2048) / 16
+    assert abs(g.shift[-1, -1] - top) <= 0.5
+
+
+def test_batch_with_one_dm_and_one_tier_is_the_single_dm_path():
+    rng = np.random.default_rng(21)
+    vin = rng.integers(-60, 60, size=(256 * 6, 4, 2)).astype(np.int8)
+    g1 = O.plan_geometry(325.0, 0.25, 4, 20.0, 256, 4)
+    gb = O.batch_geometry(325.0, 0.25, 4, [20.0], (256,), 4)
+    # the batch overlap is N/32 = 8 or the smear, whichever is larger: here the smear
+    assert g1.n_ov > 8 and gb.tier_nov[0] == g1.n_ov
+    a = O.dedisperse(vin, g1)
+    b = O.dedisperse_batch(vin, gb)[0]
+    assert a.shape == b.shape and np.array_equal(a, b)
+
+
+def test_batch_dm_trials_are_independent_single_dm_runs():
+    """Each DM trial of a batch equals the single-DM overlap-save with the same
+    N and overlap (one DM at a time, written with the plain steps)."""
+    rng = np.random.default_rng(22)
+    vin = rng.integers(-60, 60, size=(992 * 3, 8, 2)).astype(np.int8)
+    dms = [5.0, 7.5, 30.0]
+    g = O.batch_geometry(610.0, 0.5, 8, dms, (1024, 512), 8)
+    out = O.dedisperse_batch(vin, g)
+    for d, dm in enumerate(dms):
+        for k in (0, 5):
+            t = int(g.tier_of[k])
+            x = vin[: out.shape[2] * 8, k, 0].astype(float) + 1j * vin[: out.shape[2] * 8, k, 1]
+            filt = O.dedispersion_filter(float(g.f_lo_mhz[k]), g.chan_bw_mhz, dm, g.tier_nfft[t])
+            v = O.overlap_save(x, filt, g.tier_nov[t])
+            want = O.align(O.integrate(np.abs(v) ** 2, 8), int(g.shift[d, k]))
+            assert np.allclose(out[d, k], want, rtol=1e-12, atol=1e-9)
