@@ -57,6 +57,8 @@ extern "C" {
 #define CDD_ESTATE       -5   /* call not allowed in the plan's current state */
 #define CDD_ETOOBIG      -6   /* request needs more than the fixed scratch of
                                  cdd_execute_static                          */
+#define CDD_EBUSY        -7   /* pool admission refused: HBM budget or stream
+                                 slots exhausted (retry after a release)     */
 
 /* Size of the fixed device scratch array behind cdd_execute_static. */
 #define CDD_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
@@ -78,7 +80,12 @@ enum cdd_attr {
   CDD_ATTR_BLOCKS_DONE = 11,       /* execute calls since create / reset       */
   CDD_ATTR_PIPELINE_CHUNKS = 12,   /* host-buffer path: copy/compute chunks per
                                       block (settable, default 4, divides q)   */
-  CDD_ATTR_KERNEL_LAUNCHES = 13    /* kernels launched by the last execute     */
+  CDD_ATTR_KERNEL_LAUNCHES = 13,   /* kernels launched by the last execute     */
+  CDD_ATTR_BYTES_NEEDED = 14,      /* device bytes the first execute allocates
+                                      (known before it; with the host path,
+                                      staging comes on top)                    */
+  CDD_ATTR_SEQ_GAPS = 15           /* pool streams: blocks missing from the
+                                      submitted sequence numbers               */
 };
 
 enum cdd_taper { CDD_TAPER_NONE = 0, CDD_TAPER_HANN = 1, CDD_TAPER_WELCH = 2 };
@@ -104,6 +111,11 @@ int cdd_plan_set(cdd_plan plan, int attr, int64_t value);
 
 /* Read an attribute into *value. */
 int cdd_plan_get(cdd_plan plan, int attr, int64_t* value);
+
+/* Allocate the plan's device state and build its tables now (the first
+ * execute does this otherwise).  Synchronous; binds the plan to the current
+ * device. */
+int cdd_plan_commit(cdd_plan plan);
 
 /* Copy the n_chan alignment shifts r_k (integrated samples) to host memory
  * shifts[0..n_chan). */
@@ -196,6 +208,42 @@ int cdd_batch_shifts(cdd_batch batch, int64_t* shifts);
 int cdd_batch_execute(cdd_batch batch, const int8_t* d_in, float* d_out, cudaStream_t stream);
 int cdd_batch_reset(cdd_batch batch);
 int cdd_batch_destroy(cdd_batch batch);
+
+/* ------------------------------------------------------------------------
+ * Serving pool: concurrent observation streams on one GPU.  A stream is
+ * admitted when its plan's device bytes (CDD_ATTR_BYTES_NEEDED) fit the pool's
+ * remaining HBM budget and a slot is free, otherwise CDD_EBUSY; admission
+ * allocates at once, so an admitted stream cannot fail later for memory.  Each
+ * stream has its own plan (overlap tail, alignment ring and integration state
+ * stay on the device between blocks, as in Sec. 4.3) and its own CUDA stream:
+ * a block submitted while others are on the GPU is launched at once and
+ * overlaps with them.  Submissions carry a sequence number; missing numbers are
+ * counted (CDD_ATTR_SEQ_GAPS) and a repeated or older number is refused
+ * (CDD_EINVAL).  A block's latency runs from its submit call to the
+ * completion of its kernels on the GPU (stamped on the host by a stream
+ * callback).  The pool is thread-safe. */
+typedef struct cdd_pool_s* cdd_pool;
+
+enum cdd_pool_attr { CDD_POOL_BUDGET = 100, CDD_POOL_USED_BYTES = 101, CDD_POOL_STREAMS = 102 };
+
+int cdd_pool_create(cdd_pool* pool, int64_t hbm_budget_bytes, int max_streams);
+/* Admit a stream (arguments as cdd_plan_create plus segments per block and
+ * taper); *stream_id receives its slot. */
+int cdd_pool_admit(cdd_pool pool, double f_center_mhz, double bandwidth_mhz, int n_chan,
+                   double dm, int n_fft, int n_avg, int segments_per_block, int taper,
+                   int* stream_id);
+/* Plan attributes of a stream, plus CDD_ATTR_SEQ_GAPS. */
+int cdd_pool_stream_get(cdd_pool pool, int stream_id, int attr, int64_t* value);
+/* Enqueue block `seq` of a stream: d_in, d_out as for cdd_execute.  Returns at
+ * once with a ticket for cdd_pool_wait. */
+int cdd_pool_submit(cdd_pool pool, int stream_id, int64_t seq, const int8_t* d_in, float* d_out,
+                    int64_t* ticket);
+/* Wait for a ticket; *latency_ms (may be NULL) receives submit-to-done time. */
+int cdd_pool_wait(cdd_pool pool, int64_t ticket, double* latency_ms);
+/* Wait for the stream's blocks, free its plan and return its bytes to the budget. */
+int cdd_pool_release(cdd_pool pool, int stream_id);
+int cdd_pool_get(cdd_pool pool, int attr, int64_t* value);
+int cdd_pool_destroy(cdd_pool pool);
 
 /* Restart the stream: zero the overlap tails and the alignment ring and the
  * block counter.  Waits for the plan's outstanding work. */

@@ -22,13 +22,16 @@ CDD_ECUDA = -3
 CDD_EUNSUPPORTED = -4
 CDD_ESTATE = -5
 CDD_ETOOBIG = -6
+CDD_EBUSY = -7
 STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
 
 ATTR = {
     "n_fft": 0, "n_ov": 1, "hop": 2, "n_avg": 3, "n_chan": 4, "segments_per_block": 5,
     "block_samples": 6, "n_out_per_block": 7, "r_max": 8, "bytes_device": 9, "taper": 10,
-    "blocks_done": 11, "pipeline_chunks": 12, "kernel_launches": 13,
+    "blocks_done": 11, "pipeline_chunks": 12, "kernel_launches": 13, "bytes_needed": 14,
+    "seq_gaps": 15,
 }
+POOL_ATTR = {"budget": 100, "used_bytes": 101, "streams": 102}
 TAPER = {"none": 0, "hann": 1, "welch": 2}
 
 # every symbol include/cdd.h declares
@@ -36,7 +39,10 @@ EXPORTS = ("cdd_plan_create", "cdd_plan_set", "cdd_plan_get", "cdd_plan_shifts",
            "cdd_execute_voltages", "cdd_execute_host", "cdd_execute_static", "cdd_reset",
            "cdd_destroy", "cdd_strerror", "cdd_version",
            "cdd_batch_create", "cdd_batch_set", "cdd_batch_get", "cdd_batch_tier",
-           "cdd_batch_shifts", "cdd_batch_execute", "cdd_batch_reset", "cdd_batch_destroy")
+           "cdd_batch_shifts", "cdd_batch_execute", "cdd_batch_reset", "cdd_batch_destroy",
+           "cdd_plan_commit", "cdd_pool_create", "cdd_pool_admit", "cdd_pool_stream_get",
+           "cdd_pool_submit", "cdd_pool_wait", "cdd_pool_release", "cdd_pool_get",
+           "cdd_pool_destroy")
 
 
 class CddError(RuntimeError):
@@ -72,6 +78,17 @@ def _load() -> ctypes.CDLL:
     lib.cdd_batch_execute.argtypes = [vp, vp, vp, vp]
     lib.cdd_batch_reset.argtypes = [vp]
     lib.cdd_batch_destroy.argtypes = [vp]
+    lib.cdd_plan_commit.argtypes = [vp]
+    lib.cdd_pool_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int64, ctypes.c_int]
+    lib.cdd_pool_admit.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.cdd_pool_stream_get.argtypes = [vp, ctypes.c_int, ctypes.c_int, i64p]
+    lib.cdd_pool_submit.argtypes = [vp, ctypes.c_int, ctypes.c_int64, vp, vp, i64p]
+    lib.cdd_pool_wait.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]
+    lib.cdd_pool_release.argtypes = [vp, ctypes.c_int]
+    lib.cdd_pool_get.argtypes = [vp, ctypes.c_int, i64p]
+    lib.cdd_pool_destroy.argtypes = [vp]
     lib.cdd_reset.argtypes = [vp]
     lib.cdd_destroy.argtypes = [vp]
     lib.cdd_strerror.argtypes = [ctypes.c_int]
@@ -209,6 +226,65 @@ def cdd_batch_reset(batch: int) -> None:
 
 def cdd_batch_destroy(batch: int) -> None:
     _check(_lib.cdd_batch_destroy(ctypes.c_void_p(batch)), "cdd_batch_destroy")
+
+
+def cdd_plan_commit(plan: int) -> None:
+    _check(_lib.cdd_plan_commit(ctypes.c_void_p(plan)), "cdd_plan_commit")
+
+
+def cdd_pool_create(hbm_budget_bytes: int, max_streams: int) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.cdd_pool_create(ctypes.byref(h), int(hbm_budget_bytes), int(max_streams)),
+           "cdd_pool_create")
+    return h.value
+
+
+def cdd_pool_admit(pool: int, f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft, n_avg,
+                   segments_per_block, taper=0) -> int:
+    sid = ctypes.c_int(-1)
+    _check(_lib.cdd_pool_admit(ctypes.c_void_p(pool), float(f_center_mhz), float(bandwidth_mhz),
+                               int(n_chan), float(dm), int(n_fft), int(n_avg),
+                               int(segments_per_block), int(taper), ctypes.byref(sid)),
+           "cdd_pool_admit")
+    return sid.value
+
+
+def cdd_pool_stream_get(pool: int, stream_id: int, attr) -> int:
+    a = ATTR[attr] if isinstance(attr, str) else int(attr)
+    v = ctypes.c_int64()
+    _check(_lib.cdd_pool_stream_get(ctypes.c_void_p(pool), int(stream_id), a, ctypes.byref(v)),
+           "cdd_pool_stream_get")
+    return int(v.value)
+
+
+def cdd_pool_submit(pool: int, stream_id: int, seq: int, d_in: int, d_out: int) -> int:
+    t = ctypes.c_int64()
+    _check(_lib.cdd_pool_submit(ctypes.c_void_p(pool), int(stream_id), int(seq),
+                                ctypes.c_void_p(d_in), ctypes.c_void_p(d_out), ctypes.byref(t)),
+           "cdd_pool_submit")
+    return int(t.value)
+
+
+def cdd_pool_wait(pool: int, ticket: int) -> float:
+    lat = ctypes.c_double(-1.0)
+    _check(_lib.cdd_pool_wait(ctypes.c_void_p(pool), int(ticket), ctypes.byref(lat)),
+           "cdd_pool_wait")
+    return float(lat.value)
+
+
+def cdd_pool_release(pool: int, stream_id: int) -> None:
+    _check(_lib.cdd_pool_release(ctypes.c_void_p(pool), int(stream_id)), "cdd_pool_release")
+
+
+def cdd_pool_get(pool: int, attr) -> int:
+    a = POOL_ATTR[attr] if isinstance(attr, str) else int(attr)
+    v = ctypes.c_int64()
+    _check(_lib.cdd_pool_get(ctypes.c_void_p(pool), a, ctypes.byref(v)), "cdd_pool_get")
+    return int(v.value)
+
+
+def cdd_pool_destroy(pool: int) -> None:
+    _check(_lib.cdd_pool_destroy(ctypes.c_void_p(pool)), "cdd_pool_destroy")
 
 
 # ------------------------------------------------------------------ convenience

@@ -139,6 +139,19 @@ int fail_cuda(cdd_plan p, cudaError_t e) {
 
 int64_t n_out_per_block(const cdd_plan p) { return (int64_t)p->q * p->hop / p->n_avg; }
 
+// Device bytes the first execute allocates (tables, tails, ring, shifts and the
+// channel-major block copy), exactly as commit_once requests them.
+int64_t bytes_needed(const cdd_plan p) {
+  const int64_t C = p->n_chan;
+  int64_t b = C * p->n_fft * (int64_t)sizeof(float2);
+  b += (int64_t)cdd::twiddle_table_len(p->logn) * (int64_t)sizeof(float2);
+  if (p->n_ov > 0) b += 2 * C * p->n_ov * (int64_t)sizeof(char2);
+  b += C * (p->r_max + n_out_per_block(p)) * (int64_t)sizeof(float);
+  b += C * (int64_t)sizeof(int);
+  b += C * p->q * p->hop * (int64_t)sizeof(char2);
+  return b;
+}
+
 // Geometry of Sec. 2.2 / 2.3 and the channel alignment of Sec. 1.2, held by
 // the plan (with its per-channel shifts).
 int compute_geometry(cdd_plan p, int n_fft) {
@@ -330,6 +343,7 @@ const char* cdd_strerror(int code) {
     case CDD_EUNSUPPORTED: return "not supported by this build";
     case CDD_ESTATE: return "not allowed in the plan's current state";
     case CDD_ETOOBIG: return "request exceeds the fixed scratch of cdd_execute_static";
+    case CDD_EBUSY: return "admission refused: HBM budget or stream slots exhausted";
     default: return "unknown error code";
   }
 }
@@ -397,10 +411,13 @@ int cdd_plan_get(cdd_plan p, int attr, int64_t* v) {
     case CDD_ATTR_BLOCKS_DONE: *v = p->blocks; break;
     case CDD_ATTR_PIPELINE_CHUNKS: *v = p->chunks; break;
     case CDD_ATTR_KERNEL_LAUNCHES: *v = p->last_launches; break;
+    case CDD_ATTR_BYTES_NEEDED: *v = bytes_needed(p); break;
     default: return CDD_EINVAL;
   }
   return CDD_OK;
 }
+
+int cdd_plan_commit(cdd_plan p) { return prepare(p); }
 
 int cdd_plan_shifts(cdd_plan p, int64_t* shifts) {
   if (!p || !shifts) return CDD_EINVAL;
