@@ -51,9 +51,15 @@ TAPERS = ("none", "hann", "welch")
 
 def channel_lower_edges(f_center_mhz: float, bandwidth_mhz: float, n_chan: int):
     """Lower edge f_k of every channel and the channel width (Sec. 2.1: f_o is the
-    lower edge of the band; channel 0 is the lowest, upper sideband)."""
-    chan_bw = bandwidth_mhz / n_chan
-    f_lo = f_center_mhz - bandwidth_mhz / 2.0 + chan_bw * np.arange(n_chan, dtype=np.float64)
+    lower edge of the band).  Upper sideband (bandwidth > 0): channel 0 is the
+    lowest.  Lower sideband (bandwidth < 0): channel 0 is the highest, so
+    f_k = f_center + |B|/2 - (k + 1) * chan_bw."""
+    chan_bw = abs(bandwidth_mhz) / n_chan
+    k = np.arange(n_chan, dtype=np.float64)
+    if bandwidth_mhz > 0:
+        f_lo = f_center_mhz - bandwidth_mhz / 2.0 + chan_bw * k
+    else:
+        f_lo = f_center_mhz + abs(bandwidth_mhz) / 2.0 - chan_bw * (k + 1.0)
     return f_lo, chan_bw
 
 
@@ -91,6 +97,7 @@ class Geometry:
     n_avg: int                # integration length
     n_disp: float             # dispersion samples of the lowest channel
     shift: np.ndarray         # [C] int64 alignment shift r_k in integrated samples
+    sideband: int = 1         # +1 upper, -1 lower
 
 
 def plan_geometry(f_center_mhz: float, bandwidth_mhz: float, n_chan: int, dm: float,
@@ -105,10 +112,10 @@ def plan_geometry(f_center_mhz: float, bandwidth_mhz: float, n_chan: int, dm: fl
       and N >= 64 (the smallest transform the GPU path runs).
     * r_k = rint(delay of f_k relative to f_0, in integrated samples), Sec. 1.2.
     """
-    if n_chan <= 0 or n_avg <= 0 or bandwidth_mhz <= 0 or dm < 0:
-        raise ValueError("n_chan, n_avg, bandwidth must be positive and DM >= 0")
+    if n_chan <= 0 or n_avg <= 0 or bandwidth_mhz == 0 or dm < 0:
+        raise ValueError("n_chan, n_avg must be positive, bandwidth non-zero and DM >= 0")
     f_lo, chan_bw = channel_lower_edges(f_center_mhz, bandwidth_mhz, n_chan)
-    n_d = dispersion_samples(float(f_lo[0]), chan_bw, dm)
+    n_d = dispersion_samples(float(f_lo.min()), chan_bw, dm)
     n_ov = int(math.ceil(n_d))
     n_ov = -(-n_ov // n_avg) * n_avg
     if n_fft == 0:
@@ -120,10 +127,10 @@ def plan_geometry(f_center_mhz: float, bandwidth_mhz: float, n_chan: int, dm: fl
     hop = n_fft - n_ov
     if hop % n_avg:
         raise ValueError(f"hop {hop} is not a multiple of n_avg {n_avg}")
-    delay = dispersion_delay_s(f_lo, f_lo[0], dm)            # <= 0: higher channels lead
+    delay = dispersion_delay_s(f_lo, f_lo.min(), dm)         # <= 0: higher channels lead
     shift = np.rint(-delay * chan_bw * 1e6 / n_avg).astype(np.int64)
     return Geometry(n_chan, chan_bw, f_lo, float(dm), int(n_fft), int(n_ov), int(hop),
-                    int(n_avg), float(n_d), shift)
+                    int(n_avg), float(n_d), shift, 1 if bandwidth_mhz > 0 else -1)
 
 
 # --------------------------------------------------------------------------
@@ -159,12 +166,20 @@ def taper(f_l_mhz, chan_bw_mhz: float, kind: str = "none"):
 
 
 def dedispersion_filter(f_lo_mhz: float, chan_bw_mhz: float, dm: float, n_fft: int,
-                        taper_kind: str = "none") -> np.ndarray:
+                        taper_kind: str = "none", sideband: int = 1) -> np.ndarray:
     """The "chirp function" of Sec. 2.2 for one channel on an N-point grid: the
-    taper times the inverse of Eq. 3's term, conj(H) = exp(-i*Phi)."""
+    taper times the inverse of Eq. 3's term, conj(H) = exp(-i*Phi).
+
+    A lower-sideband channel carries the conjugate of the upper-sideband
+    baseband of the same sky band (frequency runs downward), so its bin j sits
+    where the upper-sideband bin -j (mod N) does -- f_l = chan_bw/2 - nu_j, with
+    the Nyquist bin its own mirror at f_l = 0 -- and the correction is the
+    conjugate: exp(+i*Phi)."""
     f_l = bin_offsets(n_fft, chan_bw_mhz)
-    h_ism = np.exp(1j * chirp_phase(f_lo_mhz, f_l, dm))
-    return np.conj(h_ism) * taper(f_l, chan_bw_mhz, taper_kind)
+    if sideband > 0:
+        return np.conj(np.exp(1j * chirp_phase(f_lo_mhz, f_l, dm))) * taper(f_l, chan_bw_mhz, taper_kind)
+    f_l = f_l[(-np.arange(n_fft)) % n_fft]
+    return np.exp(1j * chirp_phase(f_lo_mhz, f_l, dm)) * taper(f_l, chan_bw_mhz, taper_kind)
 
 
 # --------------------------------------------------------------------------
@@ -261,7 +276,7 @@ def dedisperse(vin: np.ndarray, geo: Geometry, taper_kind: str = "none",
     outs, volts = [], []
     for k in chans:
         filt = dedispersion_filter(float(geo.f_lo_mhz[k]), geo.chan_bw_mhz, geo.dm,
-                                   geo.n_fft, taper_kind)
+                                   geo.n_fft, taper_kind, geo.sideband)
         v = overlap_save(unpack(vin, k), filt, geo.n_ov)
         i_k = integrate(detect(v), geo.n_avg)
         outs.append(align(i_k, int(geo.shift[k])))
@@ -354,3 +369,20 @@ def dedisperse_batch(vin: np.ndarray, geo: BatchGeometry, channels=None, dm_inde
             v = overlap_save(x, filt, geo.tier_nov[t])
             out[di, ci] = align(integrate(detect(v), geo.n_avg), int(geo.shift[d, k]))
     return out
+
+
+# --------------------------------------------------------------------------
+# Band sum and polarisation sum (Sec. 1.2 incoherent addition; Sec. 4.3 two
+# polarisations combined after detection)
+# --------------------------------------------------------------------------
+
+def band_sum(out: np.ndarray) -> np.ndarray:
+    """Add the aligned channels: [..., C, n_out] -> [..., n_out] (Sec. 1.2: the
+    aligned sub-bands are added to give the dedispersed time series)."""
+    return np.asarray(out).sum(axis=-2)
+
+
+def dedisperse_dual(vin_a: np.ndarray, vin_b: np.ndarray, geo: Geometry, taper_kind: str = "none"):
+    """Two polarisations of one beam, each dedispersed and detected, summed
+    after detection (Sec. 4.3 combines the polarisations after detection)."""
+    return dedisperse(vin_a, geo, taper_kind) + dedisperse(vin_b, geo, taper_kind)

@@ -304,3 +304,40 @@ def test_batch_dm_trials_are_independent_single_dm_runs():
             v = O.overlap_save(x, filt, g.tier_nov[t])
             want = O.align(O.integrate(np.abs(v) ** 2, 8), int(g.shift[d, k]))
             assert np.allclose(out[d, k], want, rtol=1e-12, atol=1e-9)
+
+
+# ---------------------------------------------------------------- lower sideband, sums
+
+def test_lower_sideband_is_the_conjugate_mirror_of_upper():
+    """A lower-sideband band carries the conjugate baseband of the same sky
+    channels in reverse order; its intensities must equal the upper-sideband
+    ones channel for channel (a wrong phase sign would double the dispersion)."""
+    rng = np.random.default_rng(31)
+    n_chan = 6
+    usb = rng.integers(-50, 50, size=(80 * 40, n_chan, 2)).astype(np.int8)
+    lsb = usb[:, ::-1, :].copy()
+    lsb[..., 1] = -lsb[..., 1]                                   # conjugate
+    g_u = O.plan_geometry(325.0, 0.375, n_chan, 40.0, 128, 4)
+    g_l = O.plan_geometry(325.0, -0.375, n_chan, 40.0, 128, 4)
+    assert np.allclose(g_l.f_lo_mhz, g_u.f_lo_mhz[::-1])
+    assert np.array_equal(g_l.shift, g_u.shift[::-1]) and g_l.n_ov == g_u.n_ov
+    out_u = O.dedisperse(usb, g_u)
+    out_l = O.dedisperse(lsb, g_l)
+    assert np.allclose(out_l, out_u[::-1], rtol=1e-10, atol=1e-6)
+    # and the wrong (upper-sideband) filter on the mirrored data does not
+    bad = O.plan_geometry(325.0, 0.375, n_chan, 40.0, 128, 4)
+    wrong = O.dedisperse(lsb[:, ::-1], bad)
+    assert O.rel_rms(wrong, out_u) > 1e-2
+
+
+def test_band_sum_and_polarisation_sum():
+    rng = np.random.default_rng(32)
+    a = rng.integers(-50, 50, size=(52 * 20, 8, 2)).astype(np.int8)
+    b = rng.integers(-50, 50, size=(52 * 20, 8, 2)).astype(np.int8)
+    g = O.plan_geometry(318.0, 0.5, 8, 10.0, 64, 4)
+    oa, ob = O.dedisperse(a, g), O.dedisperse(b, g)
+    assert np.array_equal(O.dedisperse_dual(a, b, g), oa + ob)
+    assert np.allclose(O.dedisperse_dual(a, np.zeros_like(a), g), oa, rtol=0, atol=0)
+    s = O.band_sum(oa)
+    assert s.shape == (oa.shape[1],)
+    assert np.allclose(s, [oa[:, m].sum() for m in range(oa.shape[1])])
