@@ -84,8 +84,10 @@ enum cdd_attr {
   CDD_ATTR_BYTES_NEEDED = 14,      /* device bytes the first execute allocates
                                       (known before it; with the host path,
                                       staging comes on top)                    */
-  CDD_ATTR_SEQ_GAPS = 15           /* pool streams: blocks missing from the
+  CDD_ATTR_SEQ_GAPS = 15,          /* pool streams: blocks missing from the
                                       submitted sequence numbers               */
+  CDD_ATTR_POLARISATIONS = 16      /* 1 or 2 (settable): 2 keeps a second
+                                      stream state for cdd_execute_dual        */
 };
 
 enum cdd_taper { CDD_TAPER_NONE = 0, CDD_TAPER_HANN = 1, CDD_TAPER_WELCH = 2 };
@@ -134,6 +136,21 @@ int cdd_execute(cdd_plan plan, const int8_t* d_in, float* d_out, cudaStream_t st
  * (re, im).  For accuracy checks; slower than cdd_execute. */
 int cdd_execute_voltages(cdd_plan plan, const int8_t* d_in, float* d_out,
                          float* d_volt, cudaStream_t stream);
+
+/* Two polarisations of one beam (plan set to CDD_ATTR_POLARISATIONS = 2):
+ * both inputs device int8 [q*h][C][2]; each is dedispersed and detected with
+ * its own overlap tail and ring, and d_out float [C][q*h/n_avg] receives the
+ * sum of the two intensities (Sec. 4.3 combines the polarisations after
+ * detection).  CDD_ESTATE if the plan has one polarisation. */
+int cdd_execute_dual(cdd_plan plan, const int8_t* d_in_a, const int8_t* d_in_b, float* d_out,
+                     cudaStream_t stream);
+
+/* Band sum (Sec. 1.2: the aligned sub-bands are added): d_sum[p][m] =
+ * sum over k of d_out[p][k][m] for n_planes planes of [n_chan][n_out] floats
+ * (a plan's output: one plane; a batch's: one per DM trial, giving the
+ * DM-trial time series).  Device buffers; asynchronous on `stream`. */
+int cdd_band_sum(const float* d_out, int64_t n_planes, int n_chan, int64_t n_out, float* d_sum,
+                 cudaStream_t stream);
 
 /* End-to-end form with HOST buffers: h_in int8 [q*h][C][2], h_out float
  * [C][q*h/n_avg].  Copies in, dedisperses and copies out in

@@ -29,7 +29,7 @@ ATTR = {
     "n_fft": 0, "n_ov": 1, "hop": 2, "n_avg": 3, "n_chan": 4, "segments_per_block": 5,
     "block_samples": 6, "n_out_per_block": 7, "r_max": 8, "bytes_device": 9, "taper": 10,
     "blocks_done": 11, "pipeline_chunks": 12, "kernel_launches": 13, "bytes_needed": 14,
-    "seq_gaps": 15,
+    "seq_gaps": 15, "polarisations": 16,
 }
 POOL_ATTR = {"budget": 100, "used_bytes": 101, "streams": 102}
 TAPER = {"none": 0, "hann": 1, "welch": 2}
@@ -40,7 +40,7 @@ EXPORTS = ("cdd_plan_create", "cdd_plan_set", "cdd_plan_get", "cdd_plan_shifts",
            "cdd_destroy", "cdd_strerror", "cdd_version",
            "cdd_batch_create", "cdd_batch_set", "cdd_batch_get", "cdd_batch_tier",
            "cdd_batch_shifts", "cdd_batch_execute", "cdd_batch_reset", "cdd_batch_destroy",
-           "cdd_plan_commit", "cdd_pool_create", "cdd_pool_admit", "cdd_pool_stream_get",
+           "cdd_plan_commit", "cdd_execute_dual", "cdd_band_sum", "cdd_pool_create", "cdd_pool_admit", "cdd_pool_stream_get",
            "cdd_pool_submit", "cdd_pool_wait", "cdd_pool_release", "cdd_pool_get",
            "cdd_pool_destroy")
 
@@ -79,6 +79,8 @@ def _load() -> ctypes.CDLL:
     lib.cdd_batch_reset.argtypes = [vp]
     lib.cdd_batch_destroy.argtypes = [vp]
     lib.cdd_plan_commit.argtypes = [vp]
+    lib.cdd_execute_dual.argtypes = [vp, vp, vp, vp, vp]
+    lib.cdd_band_sum.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, vp, vp]
     lib.cdd_pool_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int64, ctypes.c_int]
     lib.cdd_pool_admit.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -228,6 +230,31 @@ def cdd_batch_destroy(batch: int) -> None:
     _check(_lib.cdd_batch_destroy(ctypes.c_void_p(batch)), "cdd_batch_destroy")
 
 
+def cdd_execute_dual(plan: int, d_in_a: int, d_in_b: int, d_out: int, stream: int = 0) -> None:
+    _check(_lib.cdd_execute_dual(ctypes.c_void_p(plan), ctypes.c_void_p(d_in_a),
+                                 ctypes.c_void_p(d_in_b), ctypes.c_void_p(d_out),
+                                 ctypes.c_void_p(stream)), "cdd_execute_dual")
+
+
+def cdd_band_sum(d_out: int, n_planes: int, n_chan: int, n_out: int, d_sum: int,
+                 stream: int = 0) -> None:
+    _check(_lib.cdd_band_sum(ctypes.c_void_p(d_out), int(n_planes), int(n_chan), int(n_out),
+                             ctypes.c_void_p(d_sum), ctypes.c_void_p(stream)), "cdd_band_sum")
+
+
+def band_sum(out):
+    """Torch convenience: [..., C, n_out] device float32 -> [..., n_out] (in the library)."""
+    import torch
+    if out.dtype != torch.float32 or not out.is_contiguous() or out.device.type != "cuda":
+        raise ValueError("band_sum needs a contiguous device float32 tensor")
+    c, n = out.shape[-2], out.shape[-1]
+    planes = out.numel() // (c * n)
+    res = torch.empty(out.shape[:-2] + (n,), dtype=torch.float32, device=out.device)
+    cdd_band_sum(out.data_ptr(), planes, c, n, res.data_ptr(),
+                 torch.cuda.current_stream(out.device).cuda_stream)
+    return res
+
+
 def cdd_plan_commit(plan: int) -> None:
     _check(_lib.cdd_plan_commit(ctypes.c_void_p(plan)), "cdd_plan_commit")
 
@@ -293,11 +320,13 @@ class Plan:
     """Owning wrapper of one plan; tensors in, tensors out (no computation here)."""
 
     def __init__(self, f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft=0, n_avg=1,
-                 segments_per_block=1, taper="none", pipeline_chunks=None):
+                 segments_per_block=1, taper="none", pipeline_chunks=None, polarisations=1):
         self.handle = cdd_plan_create(f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft, n_avg)
         try:
             cdd_plan_set(self.handle, "segments_per_block", segments_per_block)
             cdd_plan_set(self.handle, "taper", TAPER[taper])
+            if polarisations != 1:
+                cdd_plan_set(self.handle, "polarisations", polarisations)
             if pipeline_chunks is not None:
                 cdd_plan_set(self.handle, "pipeline_chunks", pipeline_chunks)
         except Exception:
@@ -354,6 +383,16 @@ class Plan:
         self._check_io(vin, out, device=False)
         s = torch.cuda.current_stream().cuda_stream if stream is None else stream
         cdd_execute_host(self.handle, vin.data_ptr(), out.data_ptr(), s)
+        return out
+
+    def execute_dual(self, vin_a, vin_b, out=None):
+        import torch
+        if out is None:
+            out = torch.empty((self.n_chan, self.n_out), dtype=torch.float32, device=vin_a.device)
+        self._check_io(vin_a, out, device=True)
+        self._check_io(vin_b, out, device=True)
+        cdd_execute_dual(self.handle, vin_a.data_ptr(), vin_b.data_ptr(), out.data_ptr(),
+                         torch.cuda.current_stream(vin_a.device).cuda_stream)
         return out
 
     def reset(self):

@@ -22,6 +22,8 @@ constexpr int kMaxLogN = 16;
 struct cdd_plan_s {
   // observation and geometry (fixed at create)
   double f_center = 0, bandwidth = 0, dm = 0, chan_bw = 0, f_lo0 = 0, n_disp = 0;
+  double f_base = 0;
+  int sideband = 1;
   int n_chan = 0, n_fft = 0, logn = 0, n_ov = 0, hop = 0, n_avg = 0;
   std::vector<int64_t> shift;
   int64_t r_max = 0;
@@ -42,6 +44,14 @@ struct cdd_plan_s {
   char2* d_in_cm = nullptr;  // channel-major copy of the block (corner-turn path)
   long long ring_len = 0;
   size_t bytes_device = 0;
+  // second polarisation: its own overlap tails, ring and stream position,
+  // sharing the tables (CDD_ATTR_POLARISATIONS = 2)
+  int pols = 1;
+  char2* d_tail_b[2] = {nullptr, nullptr};
+  float* d_ring_b = nullptr;
+  float* d_pol_tmp = nullptr;
+  long long g_next_b = 0;
+  int parity_b = 0;
   // stream position
   long long g_next = 0;     // stream index of the next integrated output
   int parity = 0;           // which tail buffer holds the previous block's tail
@@ -60,8 +70,8 @@ struct cdd_plan_s {
 namespace cdd {
 
 int64_t shift_of(const Geometry& g, int k) {
-  const double ref = pow(g.f_lo0, -2.0);
-  const double f_k = g.f_lo0 + g.chan_bw * k;
+  const double ref = pow(g.f_ref, -2.0);
+  const double f_k = chan_lower_edge(g, k);
   const double delay = kDispD * g.dm * (pow(f_k, -2.0) - ref);   // <= 0: f_k arrives first
   const double r = rint(-delay * g.chan_bw * 1e6 / g.n_avg);
   return (r >= 0 && r < 2e9) ? (int64_t)r : -1;
@@ -75,19 +85,22 @@ static int next_pow2_above(double x) {
 
 int geometry(Geometry* g, double f_center, double bandwidth, int n_chan, double dm, int n_fft,
              int n_avg) {
-  if (!(f_center > 0) || !(bandwidth > 0) || n_chan <= 0 || !(dm >= 0) || n_avg <= 0 ||
-      n_fft < 0 || !isfinite(dm))
+  if (!(f_center > 0) || !(bandwidth != 0) || !isfinite(bandwidth) || n_chan <= 0 ||
+      !(dm >= 0) || n_avg <= 0 || n_fft < 0 || !isfinite(dm))
     return CDD_EINVAL;
   g->f_center = f_center;
   g->bandwidth = bandwidth;
   g->dm = dm;
   g->n_chan = n_chan;
   g->n_avg = n_avg;
-  g->chan_bw = bandwidth / n_chan;
-  g->f_lo0 = f_center - bandwidth / 2.0;
-  if (!(g->f_lo0 > 0)) return CDD_EINVAL;
+  g->sideband = bandwidth > 0 ? 1 : -1;
+  g->chan_bw = fabs(bandwidth) / n_chan;
+  g->f_lo0 = f_center - fabs(bandwidth) / 2.0;
+  g->f_base = g->sideband > 0 ? g->f_lo0 : f_center + fabs(bandwidth) / 2.0;
+  g->f_ref = chan_lower_edge(*g, g->sideband > 0 ? 0 : n_chan - 1);
+  if (!(g->f_ref > 0)) return CDD_EINVAL;
   // dispersion time across the lowest (most smeared) channel, in samples
-  const double t_d = kDispD * dm * (pow(g->f_lo0, -2.0) - pow(g->f_lo0 + g->chan_bw, -2.0));
+  const double t_d = kDispD * dm * (pow(g->f_ref, -2.0) - pow(g->f_ref + g->chan_bw, -2.0));
   g->n_disp = t_d * g->chan_bw * 1e6;
   if (!(g->n_disp < 1e9)) return CDD_EINVAL;
   long long n_ov = (long long)ceil(g->n_disp);
@@ -149,6 +162,11 @@ int64_t bytes_needed(const cdd_plan p) {
   b += C * (p->r_max + n_out_per_block(p)) * (int64_t)sizeof(float);
   b += C * (int64_t)sizeof(int);
   b += C * p->q * p->hop * (int64_t)sizeof(char2);
+  if (p->pols == 2) {
+    if (p->n_ov > 0) b += 2 * C * p->n_ov * (int64_t)sizeof(char2);
+    b += C * (p->r_max + n_out_per_block(p)) * (int64_t)sizeof(float);
+    b += C * n_out_per_block(p) * (int64_t)sizeof(float);
+  }
   return b;
 }
 
@@ -160,6 +178,8 @@ int compute_geometry(cdd_plan p, int n_fft) {
   if (rc != CDD_OK) return rc;
   p->chan_bw = g.chan_bw;
   p->f_lo0 = g.f_lo0;
+  p->f_base = g.f_base;
+  p->sideband = g.sideband;
   p->n_disp = g.n_disp;
   p->n_fft = g.n_fft;
   p->logn = g.logn;
@@ -179,6 +199,10 @@ void free_device(cdd_plan p) {
   cudaFree(p->d_ring);
   cudaFree(p->d_shift);
   cudaFree(p->d_in_cm);
+  cudaFree(p->d_tail_b[0]);
+  cudaFree(p->d_tail_b[1]);
+  cudaFree(p->d_ring_b);
+  cudaFree(p->d_pol_tmp);
   for (int i = 0; i < 2; ++i) {
     cudaFree(p->d_in_stage[i]);
     cudaFree(p->d_out_stage[i]);
@@ -206,14 +230,22 @@ int dalloc(cdd_plan p, T** ptr, size_t bytes) {
 }
 
 int zero_state(cdd_plan p, cudaStream_t s) {
+  const size_t tb = (size_t)p->n_chan * p->n_ov * sizeof(char2);
+  const size_t rb = (size_t)p->n_chan * p->ring_len * sizeof(float);
   if (p->n_ov > 0) {
-    const size_t tb = (size_t)p->n_chan * p->n_ov * sizeof(char2);
     CDD_TRY(p, cudaMemsetAsync(p->d_tail[0], 0, tb, s));
     CDD_TRY(p, cudaMemsetAsync(p->d_tail[1], 0, tb, s));
   }
-  CDD_TRY(p, cudaMemsetAsync(p->d_ring, 0, (size_t)p->n_chan * p->ring_len * sizeof(float), s));
-  p->g_next = 0;
-  p->parity = 0;
+  CDD_TRY(p, cudaMemsetAsync(p->d_ring, 0, rb, s));
+  if (p->pols == 2) {
+    if (p->n_ov > 0) {
+      CDD_TRY(p, cudaMemsetAsync(p->d_tail_b[0], 0, tb, s));
+      CDD_TRY(p, cudaMemsetAsync(p->d_tail_b[1], 0, tb, s));
+    }
+    CDD_TRY(p, cudaMemsetAsync(p->d_ring_b, 0, rb, s));
+  }
+  p->g_next = p->g_next_b = 0;
+  p->parity = p->parity_b = 0;
   p->blocks = 0;
   return CDD_OK;
 }
@@ -235,14 +267,21 @@ int commit_once(cdd_plan p) {
   if ((rc = dalloc(p, &p->d_shift, (size_t)p->n_chan * sizeof(int)))) return rc;
   // channel-major copy of a block: the fused kernel then reads each segment contiguously
   if ((rc = dalloc(p, &p->d_in_cm, (size_t)p->n_chan * p->q * p->hop * sizeof(char2)))) return rc;
+  if (p->pols == 2) {
+    if (p->n_ov > 0)
+      for (int i = 0; i < 2; ++i)
+        if ((rc = dalloc(p, &p->d_tail_b[i], (size_t)p->n_chan * p->n_ov * sizeof(char2)))) return rc;
+    if ((rc = dalloc(p, &p->d_ring_b, (size_t)p->n_chan * p->ring_len * sizeof(float)))) return rc;
+    if ((rc = dalloc(p, &p->d_pol_tmp, (size_t)p->n_chan * n_out_per_block(p) * sizeof(float)))) return rc;
+  }
   std::vector<int> sh(p->shift.begin(), p->shift.end());
   CDD_TRY(p, cudaMemcpy(p->d_shift, sh.data(), sh.size() * sizeof(int), cudaMemcpyHostToDevice));
   cudaStream_t s;
   CDD_TRY(p, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   cudaError_t e = cdd::launch_twiddle_table(p->logn, p->d_tw, s);
   if (e == cudaSuccess)
-    e = cdd::launch_chirp_table(p->logn, p->d_chirp, p->n_chan, p->f_lo0, p->chan_bw, p->dm,
-                                p->taper, s);
+    e = cdd::launch_chirp_table(p->logn, p->d_chirp, p->n_chan, p->f_base, p->chan_bw, p->dm,
+                                p->taper, p->sideband, s);
   if (e == cudaSuccess && (rc = zero_state(p, s)) != CDD_OK) {
     cudaStreamDestroy(s);
     return rc;
@@ -268,8 +307,12 @@ int check_device(cdd_plan p) {
   return dev == p->device ? CDD_OK : CDD_EINVAL;
 }
 
-// One block of q segments on `s`; advances the stream position.
-int run_block(cdd_plan p, const int8_t* d_in, float* d_out, float* d_volt, int q, cudaStream_t s) {
+// One block of q segments on `s` for polarisation `pol`; advances its stream position.
+int run_block(cdd_plan p, const int8_t* d_in, float* d_out, float* d_volt, int q, cudaStream_t s,
+              int pol = 0) {
+  char2** tail = pol == 0 ? p->d_tail : p->d_tail_b;
+  int& parity = pol == 0 ? p->parity : p->parity_b;
+  long long& g_next = pol == 0 ? p->g_next : p->g_next_b;
   cdd::OlsArgs a;
   a.in = reinterpret_cast<const char2*>(d_in);
   a.in_cm = nullptr;
@@ -279,9 +322,9 @@ int run_block(cdd_plan p, const int8_t* d_in, float* d_out, float* d_volt, int q
   a.out = d_out;
   a.chirp = p->d_chirp;
   a.tw = p->d_tw;
-  a.tail_rd = p->d_tail[p->parity];
-  a.tail_wr = p->d_tail[p->parity ^ 1];
-  a.ring = p->d_ring;
+  a.tail_rd = tail[parity];
+  a.tail_wr = tail[parity ^ 1];
+  a.ring = pol == 0 ? p->d_ring : p->d_ring_b;
   a.shift = p->d_shift;
   a.volt = reinterpret_cast<float2*>(d_volt);
   a.n_chan = p->n_chan;
@@ -290,12 +333,12 @@ int run_block(cdd_plan p, const int8_t* d_in, float* d_out, float* d_volt, int q
   a.n_avg = p->n_avg;
   a.q = q;
   a.n_out = (int)((int64_t)q * p->hop / p->n_avg);
-  a.g0 = p->g_next;
+  a.g0 = g_next;
   a.ring_len = p->ring_len;
   CDD_TRY(p, cdd::launch_ols(p->logn, a, s));
-  p->g_next += a.n_out;
-  p->parity ^= 1;
-  p->blocks += 1;
+  g_next += a.n_out;
+  parity ^= 1;
+  if (pol == 0) p->blocks += 1;
   return CDD_OK;
 }
 
@@ -389,6 +432,10 @@ int cdd_plan_set(cdd_plan p, int attr, int64_t value) {
       p->chunks = (int)value;
       p->chunks_set = true;
       return CDD_OK;
+    case CDD_ATTR_POLARISATIONS:
+      if (value != 1 && value != 2) return CDD_EINVAL;
+      p->pols = (int)value;
+      return CDD_OK;
     default:
       return CDD_EINVAL;
   }
@@ -412,6 +459,7 @@ int cdd_plan_get(cdd_plan p, int attr, int64_t* v) {
     case CDD_ATTR_PIPELINE_CHUNKS: *v = p->chunks; break;
     case CDD_ATTR_KERNEL_LAUNCHES: *v = p->last_launches; break;
     case CDD_ATTR_BYTES_NEEDED: *v = bytes_needed(p); break;
+    case CDD_ATTR_POLARISATIONS: *v = p->pols; break;
     default: return CDD_EINVAL;
   }
   return CDD_OK;
@@ -437,6 +485,26 @@ int cdd_execute_voltages(cdd_plan p, const int8_t* d_in, float* d_out, float* d_
 
 int cdd_execute(cdd_plan p, const int8_t* d_in, float* d_out, cudaStream_t stream) {
   return cdd_execute_voltages(p, d_in, d_out, nullptr, stream);
+}
+
+int cdd_execute_dual(cdd_plan p, const int8_t* d_in_a, const int8_t* d_in_b, float* d_out,
+                     cudaStream_t stream) {
+  if (!p || !d_in_a || !d_in_b || !d_out) return CDD_EINVAL;
+  if (p->pols != 2) return CDD_ESTATE;
+  int rc = prepare(p);
+  if (rc) return rc;
+  if ((rc = run_block(p, d_in_a, d_out, nullptr, p->q, stream, 0))) return rc;
+  if ((rc = run_block(p, d_in_b, p->d_pol_tmp, nullptr, p->q, stream, 1))) return rc;
+  CDD_TRY(p, cdd::launch_accumulate(d_out, p->d_pol_tmp, (long long)p->n_chan * n_out_per_block(p), stream));
+  p->last_launches = 5;
+  return CDD_OK;
+}
+
+int cdd_band_sum(const float* d_out, int64_t n_planes, int n_chan, int64_t n_out, float* d_sum,
+                 cudaStream_t stream) {
+  if (!d_out || !d_sum || n_planes <= 0 || n_chan <= 0 || n_out <= 0) return CDD_EINVAL;
+  return cdd::launch_band_sum(d_out, n_planes, n_chan, n_out, d_sum, stream) == cudaSuccess
+             ? CDD_OK : CDD_ECUDA;
 }
 
 int cdd_execute_host(cdd_plan p, const int8_t* h_in, float* h_out, cudaStream_t stream) {

@@ -488,6 +488,9 @@ int cdd_batch_create(cdd_batch* out, double f_center_mhz, double bandwidth_mhz, 
     for (int d = 0; d < n_dm && rc == CDD_OK; ++d) {
       cdd::Geometry g{};
       g.f_lo0 = b->f_lo0;
+      g.sideband = 1;
+      g.f_base = b->f_lo0;
+      g.f_ref = b->f_lo0;
       g.chan_bw = b->chan_bw;
       g.dm = b->dms[d];
       g.n_avg = n_avg;

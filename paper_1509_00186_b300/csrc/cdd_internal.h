@@ -32,7 +32,14 @@ struct Geometry {
   double f_center, bandwidth, dm, chan_bw, f_lo0, n_disp;
   int n_chan, n_fft, logn, n_ov, hop, n_avg;
   int64_t r_max;
+  int sideband;      // +1 upper (channel 0 lowest), -1 lower (channel 0 highest)
+  double f_base;     // upper: f_lo0; lower: the band's top edge
+  double f_ref;      // lowest channel's lower edge: reference of smear and shifts
 };
+// Lower edge of channel k: f_base + k*chan_bw (upper) or f_base - (k+1)*chan_bw (lower).
+inline double chan_lower_edge(const Geometry& g, int k) {
+  return g.sideband > 0 ? g.f_base + g.chan_bw * k : g.f_base - g.chan_bw * (k + 1.0);
+}
 int geometry(Geometry* g, double f_center, double bandwidth, int n_chan, double dm, int n_fft,
              int n_avg);
 // Alignment shift r_k of channel k in integrated samples (-1 if out of range).
@@ -48,8 +55,9 @@ cudaError_t launch_corner_turn(const char2* in, char2* out, long long rows, int 
 // Build the chirp table (FP64 phase, reduced mod 1 turn, then rounded to
 // float): chirp[k][idx] = exp(-i Phi_k(f_l)) * w(f_l) / N in the layout the
 // fused kernel reads.
-cudaError_t launch_chirp_table(int logn, float2* chirp, int n_chan, double f_lo0_mhz,
-                               double chan_bw_mhz, double dm, int taper, cudaStream_t s);
+cudaError_t launch_chirp_table(int logn, float2* chirp, int n_chan, double f_base_mhz,
+                               double chan_bw_mhz, double dm, int taper, int sideband,
+                               cudaStream_t s);
 
 // Twiddle factors of every radix pass in the kernel's thread-major layout
 // (FP64, then rounded); twiddle_table_len entries.
@@ -59,8 +67,15 @@ int twiddle_table_len(int logn);
 bool needs_channel_major(int logn);
 
 // shift[k] = r_k for k < n_chan, computed on the device in FP64.
-cudaError_t launch_shift_table(int* shift, int n_chan, double f_lo0_mhz, double chan_bw_mhz,
-                               double dm, int n_avg, cudaStream_t s);
+cudaError_t launch_shift_table(int* shift, int n_chan, double f_base_mhz, double f_ref_mhz,
+                               double chan_bw_mhz, double dm, int n_avg, int sideband,
+                               cudaStream_t s);
+
+// sum[p][m] = sum_k out[p][k][m] (channels added in order).
+cudaError_t launch_band_sum(const float* out, long long n_planes, int n_chan, long long n_out,
+                            float* sum, cudaStream_t s);
+// acc[i] += add[i], i < n.
+cudaError_t launch_accumulate(float* acc, const float* add, long long n, cudaStream_t s);
 
 // Dynamic shared memory and block size of the fused kernel for N = 2^logn.
 int ols_threads(int logn);

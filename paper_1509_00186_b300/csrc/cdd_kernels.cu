@@ -304,8 +304,8 @@ ols_cluster_kernel(const OlsArgs a) {
 // sub-transform r holds at table index idx after its forward passes:
 // bin = r + CL * position_to_bin(pos), pos = (idx % NG) * R_last + idx / NG.
 template <int LOGS, int CL>
-__global__ void chirp_table_kernel(float2* chirp, int n_chan, double f_lo0, double chan_bw,
-                                   double dm, int taper) {
+__global__ void chirp_table_kernel(float2* chirp, int n_chan, double f_base, double chan_bw,
+                                   double dm, int taper, int sideband) {
   using PL = PassPlan<LOGS>;
   constexpr int NS = PL::N;
   constexpr int N = NS * CL;
@@ -318,8 +318,11 @@ __global__ void chirp_table_kernel(float2* chirp, int n_chan, double f_lo0, doub
     const int r = rem / NS, idx = rem % NS;
     const int pos = (idx % NG) * PL::RL + idx / NG;
     const int bin = r + CL * position_to_bin<LOGS>(pos);
-    const int sbin = bin < N / 2 ? bin : bin - N;
-    const double f_lo = f_lo0 + chan_bw * k;
+    // a lower-sideband channel is the conjugate mirror: bin j sits where the
+    // upper-sideband bin -j does (the Nyquist bin is its own mirror)
+    const int obin = sideband > 0 ? bin : (N - bin) % N;
+    const int sbin = obin < N / 2 ? obin : obin - N;
+    const double f_lo = sideband > 0 ? f_base + chan_bw * k : f_base - chan_bw * (k + 1.0);
     const double f_l = sbin * (chan_bw / N) + 0.5 * chan_bw;
     // Eq. 3 phase in turns, reduced to [-1/2, 1/2] before the sine and cosine
     const double turns = kDispD * 1e6 * dm * f_l * f_l / ((f_l + f_lo) * f_lo * f_lo);
@@ -336,7 +339,8 @@ __global__ void chirp_table_kernel(float2* chirp, int n_chan, double f_lo0, doub
       wt = 1.0 - y * y;
     }
     const double sc = wt / N;
-    chirp[e] = make_float2((float)(cs * sc), (float)(-sn * sc));   // exp(-i Phi) w / N
+    // exp(-i Phi) w / N; its conjugate for a lower-sideband channel
+    chirp[e] = make_float2((float)(cs * sc), (float)((sideband > 0 ? -sn : sn) * sc));
   }
 }
 
@@ -371,11 +375,11 @@ __global__ void twiddle_kernel(float2* tw) {
 
 // Alignment shifts r_k (Sec. 1.2) computed on the device, for callers that
 // keep no host-side copy of them.
-__global__ void shift_kernel(int* shift, int n_chan, double f_lo0, double chan_bw, double dm,
-                             int n_avg) {
-  const double ref = pow(f_lo0, -2.0);
+__global__ void shift_kernel(int* shift, int n_chan, double f_base, double f_ref, double chan_bw,
+                             double dm, int n_avg, int sideband) {
+  const double ref = pow(f_ref, -2.0);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_chan; k += gridDim.x * blockDim.x) {
-    const double f_k = f_lo0 + chan_bw * k;
+    const double f_k = sideband > 0 ? f_base + chan_bw * k : f_base - chan_bw * (k + 1.0);
     const double delay = kDispD * dm * (pow(f_k, -2.0) - ref);
     shift[k] = (int)rint(-delay * chan_bw * 1e6 / n_avg);
   }
@@ -491,11 +495,12 @@ cudaError_t launch_cluster_t(const OlsArgs& a, cudaStream_t s) {
 }
 
 template <int LOGS, int CL>
-cudaError_t launch_chirp_t(float2* chirp, int n_chan, double f_lo0, double chan_bw, double dm,
-                           int taper, cudaStream_t s) {
+cudaError_t launch_chirp_t(float2* chirp, int n_chan, double f_base, double chan_bw, double dm,
+                           int taper, int sideband, cudaStream_t s) {
   const long long total = (long long)n_chan * (CL << LOGS);
   const unsigned grid = (unsigned)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
-  chirp_table_kernel<LOGS, CL><<<grid, 256, 0, s>>>(chirp, n_chan, f_lo0, chan_bw, dm, taper);
+  chirp_table_kernel<LOGS, CL><<<grid, 256, 0, s>>>(chirp, n_chan, f_base, chan_bw, dm, taper,
+                                                     sideband);
   return cudaGetLastError();
 }
 
@@ -514,14 +519,15 @@ cudaError_t launch_ols(int logn, const OlsArgs& a, cudaStream_t s) {
   }
 }
 
-cudaError_t launch_chirp_table(int logn, float2* chirp, int n_chan, double f_lo0_mhz,
-                               double chan_bw_mhz, double dm, int taper, cudaStream_t s) {
+cudaError_t launch_chirp_table(int logn, float2* chirp, int n_chan, double f_base_mhz,
+                               double chan_bw_mhz, double dm, int taper, int sideband,
+                               cudaStream_t s) {
   switch (logn) {
-#define X(L) case L: return launch_chirp_t<L, 1>(chirp, n_chan, f_lo0_mhz, chan_bw_mhz, dm, taper, s);
+#define X(L) case L: return launch_chirp_t<L, 1>(chirp, n_chan, f_base_mhz, chan_bw_mhz, dm, taper, sideband, s);
     CDD_LOGN_CASES(X)
 #undef X
-    case 15: return launch_chirp_t<14, 2>(chirp, n_chan, f_lo0_mhz, chan_bw_mhz, dm, taper, s);
-    case 16: return launch_chirp_t<14, 4>(chirp, n_chan, f_lo0_mhz, chan_bw_mhz, dm, taper, s);
+    case 15: return launch_chirp_t<14, 2>(chirp, n_chan, f_base_mhz, chan_bw_mhz, dm, taper, sideband, s);
+    case 16: return launch_chirp_t<14, 4>(chirp, n_chan, f_base_mhz, chan_bw_mhz, dm, taper, sideband, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -546,10 +552,12 @@ cudaError_t launch_twiddle_table(int logn, float2* tw, cudaStream_t s) {
   }
 }
 
-cudaError_t launch_shift_table(int* shift, int n_chan, double f_lo0_mhz, double chan_bw_mhz,
-                               double dm, int n_avg, cudaStream_t s) {
+cudaError_t launch_shift_table(int* shift, int n_chan, double f_base_mhz, double f_ref_mhz,
+                               double chan_bw_mhz, double dm, int n_avg, int sideband,
+                               cudaStream_t s) {
   const int grid = (n_chan + 255) / 256 < 1024 ? (n_chan + 255) / 256 : 1024;
-  shift_kernel<<<grid, 256, 0, s>>>(shift, n_chan, f_lo0_mhz, chan_bw_mhz, dm, n_avg);
+  shift_kernel<<<grid, 256, 0, s>>>(shift, n_chan, f_base_mhz, f_ref_mhz, chan_bw_mhz, dm, n_avg,
+                                    sideband);
   return cudaGetLastError();
 }
 
@@ -557,6 +565,41 @@ cudaError_t launch_corner_turn(const char2* in, char2* out, long long rows, int 
                                cudaStream_t s) {
   const dim3 grid((unsigned)((rows + kTT - 1) / kTT), (unsigned)((n_chan + kTT - 1) / kTT));
   corner_turn_kernel<<<grid, 256, 0, s>>>(in, out, rows, n_chan);
+  return cudaGetLastError();
+}
+
+// sum[p][m] = sum over k of out[p][k][m], channels added in order (deterministic).
+__global__ void band_sum_kernel(const float* __restrict__ out, long long n_planes, int n_chan,
+                                long long n_out, float* __restrict__ sum) {
+  const long long total = n_planes * n_out;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long p = e / n_out, m = e % n_out;
+    const float* src = out + p * n_chan * n_out + m;
+    float acc = 0.f;
+    for (int k = 0; k < n_chan; ++k) acc += __ldg(src + (long long)k * n_out);
+    sum[e] = acc;
+  }
+}
+
+// acc[i] += add[i]
+__global__ void accumulate_kernel(float* __restrict__ acc, const float* __restrict__ add, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    acc[i] += add[i];
+}
+
+cudaError_t launch_band_sum(const float* out, long long n_planes, int n_chan, long long n_out,
+                            float* sum, cudaStream_t s) {
+  const long long total = n_planes * n_out;
+  const unsigned grid = (unsigned)((total + 255) / 256 < 148 * 16 ? (total + 255) / 256 : 148 * 16);
+  band_sum_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(out, n_planes, n_chan, n_out, sum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_accumulate(float* acc, const float* add, long long n, cudaStream_t s) {
+  const unsigned grid = (unsigned)((n + 255) / 256 < 148 * 16 ? (n + 255) / 256 : 148 * 16);
+  accumulate_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(acc, add, n);
   return cudaGetLastError();
 }
 

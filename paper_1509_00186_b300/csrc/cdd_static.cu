@@ -77,9 +77,11 @@ extern "C" int cdd_execute_static(double f_center_mhz, double bandwidth_mhz, int
 
   cudaError_t e = cdd::launch_twiddle_table(g.logn, tw, stream);
   if (e == cudaSuccess)
-    e = cdd::launch_chirp_table(g.logn, chirp, n_chan, g.f_lo0, g.chan_bw, dm, taper, stream);
+    e = cdd::launch_chirp_table(g.logn, chirp, n_chan, g.f_base, g.chan_bw, dm, taper, g.sideband,
+                                stream);
   if (e == cudaSuccess)
-    e = cdd::launch_shift_table(shift, n_chan, g.f_lo0, g.chan_bw, dm, n_avg, stream);
+    e = cdd::launch_shift_table(shift, n_chan, g.f_base, g.f_ref, g.chan_bw, dm, n_avg, g.sideband,
+                                stream);
   if (e == cudaSuccess && g.n_ov > 0)     // the stream starts with zeros; the array keeps old data
     e = cudaMemsetAsync(tail_zero, 0, (size_t)n_chan * g.n_ov * sizeof(char2), stream);
   if (e != cudaSuccess) return CDD_ECUDA;

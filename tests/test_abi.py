@@ -57,6 +57,9 @@ GEOMS = [
     (325.0, 0.4375, 7, 3.0, 256, 2),
     (325.0, 16.0, 8, 0.0, 64, 4),
     (1000.0, 1.0, 3, 1000.0, 0, 1),
+    (325.0, -32.0, 512, 50.0, 8192, 16),       # lower sideband
+    (610.0, -16.0, 256, 70.0, 0, 8),
+    (150.0, -32.0, 512, 100.0, 65536, 16),
 ]
 
 
@@ -83,7 +86,7 @@ def test_invalid_geometry_is_rejected(cdd):
     bad = [
         (325.0, 32.0, 512, 50.0, 48, 16),      # N not a power of two
         (325.0, 32.0, 512, 50.0, 64, 16),      # N <= n_ov
-        (325.0, -32.0, 512, 50.0, 0, 16),      # negative bandwidth
+        (325.0, 0.0, 512, 50.0, 0, 16),        # no bandwidth
         (325.0, 32.0, 0, 50.0, 0, 16),         # no channels
         (325.0, 32.0, 512, -5.0, 0, 16),       # negative DM
         (325.0, 32.0, 512, 50.0, 0, 0),        # no integration

@@ -136,6 +136,25 @@ def test_every_fft_length(cuda_device, logn):
     assert np.all(rel_rms_rows(out_g, out_o) <= TOL)
 
 
+@pytest.mark.parametrize("logn,taper", [(6, "none"), (10, "hann"), (13, "none"), (16, "none")])
+def test_lower_sideband(cuda_device, logn, taper):
+    """A lower-sideband band (negative bandwidth): channel 0 highest, bins
+    mirrored, conjugate correction; checked against the oracle."""
+    n = 1 << logn
+    n_chan, n_avg, chan_bw = 6, 4, 0.0625
+    dm = (n / 8) / O.dispersion_samples(317.0, chan_bw, 1.0)
+    args = (317.0 + n_chan * chan_bw / 2, -n_chan * chan_bw, n_chan, dm, n, n_avg)
+    geo = O.plan_geometry(*args)
+    assert geo.sideband == -1 and geo.shift[0] == geo.shift.max()
+    rng = np.random.default_rng(100 + logn)
+    T = 4 * geo.hop
+    vin = np.clip(np.rint(rng.normal(0, 20, (T, n_chan, 2))), -127, 127).astype(np.int8)
+    out_o, v_o = oracle_run(vin, args, T, taper=taper)
+    out_g, v_g = gpu_run(vin, args, 2, 2, taper=taper)
+    assert np.all(rel_rms_rows(v_g, v_o) <= TOL)
+    assert np.all(rel_rms_rows(out_g, out_o) <= TOL)
+
+
 @pytest.mark.parametrize("taper", ["hann", "welch"])
 def test_tapers(cuda_device, taper):
     args = (317.0 + 1.0, 2.0, 32, 10.0, 256, 4)
@@ -211,3 +230,47 @@ def test_precision_shape_full_size_sampled_channels(cuda_device):
     out_o, _ = oracle_run(vin, args, q * geo.hop, channels=chans)
     assert np.all(rel_rms_rows(out_g[chans], out_o) <= TOL)
     assert np.all(np.isfinite(out_g))
+
+
+def test_two_polarisations_summed_after_detection(cuda_device):
+    import torch
+    from paper_1509_00186_b300.cdd import Plan
+    args = (318.0, 2.0, 32, 10.0, 64, 4)
+    geo = O.plan_geometry(*args)
+    rng = np.random.default_rng(41)
+    q, blocks = 30, 3
+    T = q * geo.hop * blocks
+    a = np.clip(np.rint(rng.normal(0, 20, (T, 32, 2))), -127, 127).astype(np.int8)
+    b = np.clip(np.rint(rng.normal(0, 15, (T, 32, 2))), -127, 127).astype(np.int8)
+    want = O.dedisperse_dual(a, b, geo)
+    with Plan(*args, segments_per_block=q, polarisations=2) as p:
+        bs = p.block_samples
+        xa, xb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+        zero = torch.zeros_like(xb[:bs])
+        got = torch.cat([p.execute_dual(xa[i * bs:(i + 1) * bs], xb[i * bs:(i + 1) * bs])
+                         for i in range(blocks)], 1).cpu().numpy()
+    assert O.rel_rms(got, want) <= TOL
+    # a silent second polarisation leaves the first one's result bit for bit
+    with Plan(*args, segments_per_block=q, polarisations=2) as p2, Plan(*args, segments_per_block=q) as p1:
+        only = p2.execute_dual(xa[:bs], zero).cpu().numpy()
+        single = p1.execute(xa[:bs]).cpu().numpy()
+    assert np.array_equal(only, single)
+
+
+def test_band_sum_of_plan_and_batch_outputs(cuda_device):
+    import torch
+    from paper_1509_00186_b300.cdd import Batch, band_sum
+    vin, args, geo = tiny_input()
+    q = vin.shape[0] // geo.hop
+    out_g, _ = gpu_run(vin, args, q, 1, volt=False)
+    want = O.band_sum(O.dedisperse(vin[: q * geo.hop], geo))
+    got = band_sum(torch.from_numpy(out_g).cuda()).cpu().numpy()
+    assert O.rel_rms(got, want) <= TOL
+    # DM-trial time series of a small batch: one band sum per DM plane
+    bargs = (650.0, 6.25, 64, [5.0, 20.0], (2048, 1024, 512, 256), 4)
+    g = O.batch_geometry(*bargs)
+    x = complex_int8_voltages(5, 1984 * 2, 64, 20.0)
+    with Batch(*bargs, segments_per_block=2) as b:
+        series = band_sum(b.execute(torch.from_numpy(x).cuda())).cpu().numpy()
+    assert series.shape == (2, 1984 * 2 // 4)
+    assert O.rel_rms(series, O.band_sum(O.dedisperse_batch(x, g))) <= TOL
