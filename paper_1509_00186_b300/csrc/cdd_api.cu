@@ -315,9 +315,7 @@ int run_block(cdd_plan p, const int8_t* d_in, float* d_out, float* d_volt, int q
   long long& g_next = pol == 0 ? p->g_next : p->g_next_b;
   cdd::OlsArgs a;
   a.in = reinterpret_cast<const char2*>(d_in);
-  a.in_cm = nullptr;
   a.rows = (long long)q * p->hop;
-  CDD_TRY(p, cdd::launch_corner_turn(a.in, p->d_in_cm, a.rows, p->n_chan, s));
   a.in_cm = p->d_in_cm;
   a.out = d_out;
   a.chirp = p->d_chirp;
@@ -335,7 +333,12 @@ int run_block(cdd_plan p, const int8_t* d_in, float* d_out, float* d_volt, int q
   a.n_out = (int)((int64_t)q * p->hop / p->n_avg);
   a.g0 = g_next;
   a.ring_len = p->ring_len;
+  CDD_TRY(p, cdd::launch_corner_turn(a.in, p->d_in_cm, 0, a.rows, a.rows, p->n_chan, s));
+  a.s_begin = 0;
+  a.s_count = q;
   CDD_TRY(p, cdd::launch_ols(p->logn, a, s));
+  const int launches = 2;
+  p->last_launches = launches;
   g_next += a.n_out;
   parity ^= 1;
   if (pol == 0) p->blocks += 1;
@@ -479,7 +482,7 @@ int cdd_execute_voltages(cdd_plan p, const int8_t* d_in, float* d_out, float* d_
   int rc = prepare(p);
   if (rc) return rc;
   rc = run_block(p, d_in, d_out, d_volt, p->q, stream);
-  p->last_launches = rc ? 0 : 2;
+  if (rc) p->last_launches = 0;
   return rc;
 }
 
@@ -495,8 +498,9 @@ int cdd_execute_dual(cdd_plan p, const int8_t* d_in_a, const int8_t* d_in_b, flo
   if (rc) return rc;
   if ((rc = run_block(p, d_in_a, d_out, nullptr, p->q, stream, 0))) return rc;
   if ((rc = run_block(p, d_in_b, p->d_pol_tmp, nullptr, p->q, stream, 1))) return rc;
+  const int per_pol = p->last_launches;
   CDD_TRY(p, cdd::launch_accumulate(d_out, p->d_pol_tmp, (long long)p->n_chan * n_out_per_block(p), stream));
-  p->last_launches = 5;
+  p->last_launches = 2 * per_pol + 1;
   return CDD_OK;
 }
 
@@ -544,7 +548,7 @@ int cdd_execute_host(cdd_plan p, const int8_t* h_in, float* h_out, cudaStream_t 
   // the caller's stream continues after the last copy-out
   CDD_TRY(p, cudaStreamWaitEvent(stream, p->ev_out[(nc - 1) & 1], 0));
   CDD_TRY(p, cudaStreamSynchronize(p->st_d2h));
-  p->last_launches = 2 * nc;
+  p->last_launches *= nc;
   return CDD_OK;
 }
 

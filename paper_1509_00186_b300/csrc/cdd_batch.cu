@@ -569,7 +569,8 @@ int cdd_batch_execute(cdd_batch b, const int8_t* d_in, float* d_out, cudaStream_
   int rc = bprepare(b);
   if (rc) return rc;
   const int64_t rows = block_samples(b);
-  BTRY(b, cdd::launch_corner_turn(reinterpret_cast<const char2*>(d_in), b->d_in_cm, rows, b->n_chan, stream));
+  BTRY(b, cdd::launch_corner_turn(reinterpret_cast<const char2*>(d_in), b->d_in_cm, 0, rows, rows,
+                                  b->n_chan, stream));
   for (auto& t : b->tiers) {
     cdd::BatchArgs a;
     a.in_cm = b->d_in_cm;

@@ -22,6 +22,7 @@ struct OlsArgs {
   const int* shift;       // [C] alignment shift r_k
   float2* volt;           // [C][q*h] dedispersed voltages, or nullptr
   int n_chan, n_ov, hop, n_avg, q, n_out;
+  int s_begin, s_count;   // this launch runs segments [s_begin, s_begin + s_count) of q
   long long g0;           // stream index of this block's first integrated sample
   long long ring_len;
 };
@@ -48,9 +49,10 @@ int64_t shift_of(const Geometry& g, int k);
 // Launch the fused kernel for N = 2^logn.  Returns the CUDA error of the launch.
 cudaError_t launch_ols(int logn, const OlsArgs& a, cudaStream_t s);
 
-// out[k][row] = in[row][k]: channel-major copy of a block of int8 pairs.
-cudaError_t launch_corner_turn(const char2* in, char2* out, long long rows, int n_chan,
-                               cudaStream_t s);
+// out[k*stride + row] = in[row][k] for rows [r_begin, r_end): channel-major copy
+// of (part of) a block of int8 pairs.
+cudaError_t launch_corner_turn(const char2* in, char2* out, long long r_begin, long long r_end,
+                               long long stride, int n_chan, cudaStream_t s);
 
 // Build the chirp table (FP64 phase, reduced mod 1 turn, then rounded to
 // float): chirp[k][idx] = exp(-i Phi_k(f_l)) * w(f_l) / N in the layout the

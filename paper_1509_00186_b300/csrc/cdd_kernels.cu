@@ -49,9 +49,9 @@ ols_kernel(const OlsArgs a) {
   const int lt = threadIdx.x % T;
   float2* buf = smem + g * CF::SEG_F2;
   const int w = blockIdx.x * CF::G + g;        // n_chan * q < 2^31 (checked by the plan)
-  const bool active = w < a.n_chan * a.q;
+  const bool active = w < a.n_chan * a.s_count;
   const int k = active ? w % a.n_chan : 0;     // channel fastest: neighbouring CTAs
-  const int s = active ? w / a.n_chan : 0;     // share the input rows in L2
+  const int s = active ? a.s_begin + w / a.n_chan : 0;   // share the input rows in L2
 
   // ---- pass 0, forward: unpack and gather x[lt + T*j] of this segment
   float2* pb0 = buf + pad(lt);
@@ -186,7 +186,7 @@ ols_cluster_kernel(const OlsArgs a) {
   const int lt = threadIdx.x;
   const int w = blockIdx.x / CL;         // one segment per cluster
   const int k = w % a.n_chan;
-  const int s = w / a.n_chan;
+  const int s = a.s_begin + w / a.n_chan;
   float2* rbuf[CL];
 #pragma unroll
   for (int j = 0; j < CL; ++j) rbuf[j] = cluster.map_shared_rank(buf, j);
@@ -393,13 +393,15 @@ __global__ void shift_kernel(int* shift, int n_chan, double f_base, double f_ref
 constexpr int kTT = 64;
 __global__ void __launch_bounds__(256) corner_turn_kernel(const char2* __restrict__ in,
                                                           char2* __restrict__ out,
-                                                          long long rows, int n_chan) {
+                                                          long long r_begin, long long rows,
+                                                          long long stride, int n_chan) {
   __shared__ __align__(16) uint32_t tile[kTT][kTT / 2];    // [row][channel pair ^ swizzle]
-  const long long r0 = (long long)blockIdx.x * kTT;
+  const long long r0 = r_begin + (long long)blockIdx.x * kTT;
   const int c0 = blockIdx.y * kTT;
   const unsigned short* src = reinterpret_cast<const unsigned short*>(in);
   unsigned short* dst = reinterpret_cast<unsigned short*>(out);
-  const bool whole = r0 + kTT <= rows && c0 + kTT <= n_chan && (n_chan % 8) == 0 && (rows % 8) == 0;
+  const bool whole = r0 + kTT <= rows && c0 + kTT <= n_chan && (n_chan % 8) == 0 &&
+                     (stride % 8) == 0 && (r_begin % 8) == 0;
   auto sw = [](int r) { return ((r >> 3) & 15) << 1; };
   if (whole) {
     uint4 x[2];
@@ -440,13 +442,13 @@ __global__ void __launch_bounds__(256) corner_turn_kernel(const char2* __restric
         const int r = rb + t;
         e[t] = reinterpret_cast<const unsigned short*>(&tile[r][(ch >> 1) ^ sw(r)])[ch & 1];
       }
-      *reinterpret_cast<uint4*>(dst + (long long)(c0 + ch) * rows + r0 + rb) = y;
+      *reinterpret_cast<uint4*>(dst + (long long)(c0 + ch) * stride + r0 + rb) = y;
     }
   } else {
     for (int v = threadIdx.x; v < kTT * kTT; v += 256) {
       const int ch = v / kTT, r = v % kTT;
       if (r0 + r < rows && c0 + ch < n_chan)
-        dst[(long long)(c0 + ch) * rows + r0 + r] =
+        dst[(long long)(c0 + ch) * stride + r0 + r] =
             reinterpret_cast<const unsigned short*>(&tile[r][(ch >> 1) ^ sw(r)])[ch & 1];
     }
   }
@@ -467,7 +469,7 @@ cudaError_t launch_ols_t(const OlsArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_set[dev][cm] = true;
   }
-  const long long work = (long long)a.n_chan * a.q;
+  const long long work = (long long)a.n_chan * a.s_count;
   const unsigned grid = (unsigned)((work + CF::G - 1) / CF::G);
   if (cm) ols_kernel<LOGN, true><<<grid, CF::THREADS, CF::SMEM, s>>>(a);
   else ols_kernel<LOGN, false><<<grid, CF::THREADS, CF::SMEM, s>>>(a);
@@ -489,7 +491,7 @@ cudaError_t launch_cluster_t(const OlsArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  const unsigned grid = (unsigned)((long long)a.n_chan * a.q * CL);
+  const unsigned grid = (unsigned)((long long)a.n_chan * a.s_count * CL);
   ols_cluster_kernel<LOGS, CL><<<grid, PassPlan<LOGS>::T, SMEM, s>>>(a);
   return cudaGetLastError();
 }
@@ -561,10 +563,11 @@ cudaError_t launch_shift_table(int* shift, int n_chan, double f_base_mhz, double
   return cudaGetLastError();
 }
 
-cudaError_t launch_corner_turn(const char2* in, char2* out, long long rows, int n_chan,
-                               cudaStream_t s) {
-  const dim3 grid((unsigned)((rows + kTT - 1) / kTT), (unsigned)((n_chan + kTT - 1) / kTT));
-  corner_turn_kernel<<<grid, 256, 0, s>>>(in, out, rows, n_chan);
+cudaError_t launch_corner_turn(const char2* in, char2* out, long long r_begin, long long r_end,
+                               long long stride, int n_chan, cudaStream_t s) {
+  if (r_end <= r_begin) return cudaSuccess;
+  const dim3 grid((unsigned)((r_end - r_begin + kTT - 1) / kTT), (unsigned)((n_chan + kTT - 1) / kTT));
+  corner_turn_kernel<<<grid, 256, 0, s>>>(in, out, r_begin, r_end, stride, n_chan);
   return cudaGetLastError();
 }
 

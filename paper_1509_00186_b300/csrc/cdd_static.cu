@@ -103,6 +103,8 @@ extern "C" int cdd_execute_static(double f_center_mhz, double bandwidth_mhz, int
   a.hop = g.hop;
   a.n_avg = n_avg;
   a.q = n_seg;
+  a.s_begin = 0;
+  a.s_count = n_seg;
   a.n_out = (int)n_out;
   a.g0 = 0;
   a.ring_len = ring_len;
