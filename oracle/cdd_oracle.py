@@ -386,3 +386,89 @@ def dedisperse_dual(vin_a: np.ndarray, vin_b: np.ndarray, geo: Geometry, taper_k
     """Two polarisations of one beam, each dedispersed and detected, summed
     after detection (Sec. 4.3 combines the polarisations after detection)."""
     return dedisperse(vin_a, geo, taper_kind) + dedisperse(vin_b, geo, taper_kind)
+
+
+# --------------------------------------------------------------------------
+# Full-band mode: the paper's own design (Sec. 2.3, Sec. 3.1, Sec. 4.3)
+# --------------------------------------------------------------------------
+#
+# The voltage beam holds, for every frame t, the C complex outputs of a 2C-point
+# FFT of the real, Nyquist-sampled voltage (Sec. 2.3, Sec. 3.1).  The
+# inverse transform of each frame gives back 2C real samples; the frames in
+# series are the continuous real time series at 2B samples per second.  One
+# long real FFT over the whole band, the chirp on its N/2 bins, the inverse FFT
+# and overlap-save then dedisperse it coherently without sub-banding
+# (Sec. 2.3, Sec. 4.3), and the result is squared and integrated (Sec. 3.1).
+
+@dataclass(frozen=True)
+class FullbandGeometry:
+    f_lo_mhz: float           # lower edge of the band
+    bandwidth_mhz: float
+    n_chan: int               # C: complex outputs per frame
+    frame: int                # 2C real samples per frame
+    fs_mhz: float             # real sample rate 2B
+    dm: float
+    n_fft: int                # N (real points)
+    n_ov: int
+    hop: int
+    n_avg: int
+    n_disp: float             # dispersion samples across the whole band
+
+
+def fullband_geometry(f_center_mhz: float, bandwidth_mhz: float, n_chan: int, dm: float,
+                      n_fft: int = 0, n_avg: int = 1) -> FullbandGeometry:
+    """Sec. 2.3: N is the smallest power of two greater than twice the
+    dispersion samples across the band (real samples at 2B).  The overlap is
+    the dispersion samples rounded up to a whole number of frames and of
+    integration windows, so segments and blocks stay on frame boundaries."""
+    if n_chan <= 0 or n_avg <= 0 or bandwidth_mhz <= 0 or dm < 0:
+        raise ValueError("n_chan, n_avg, bandwidth must be positive and DM >= 0")
+    f_lo = f_center_mhz - bandwidth_mhz / 2.0
+    fs = 2.0 * bandwidth_mhz
+    n_d = float(dispersion_delay_s(f_lo, f_lo + bandwidth_mhz, dm) * fs * 1e6)
+    frame = 2 * n_chan
+    unit = max(frame, n_avg)
+    if unit % frame or unit % n_avg:
+        raise ValueError("frame and n_avg must be powers of two")
+    n_ov = -(-int(math.ceil(n_d)) // unit) * unit
+    if n_fft == 0:
+        n_fft = max(_next_pow2_above(2.0 * n_d), _next_pow2_above(n_ov), 2 * unit)
+    if n_fft & (n_fft - 1) or n_fft <= n_ov or (n_fft - n_ov) % unit:
+        raise ValueError(f"N={n_fft} does not fit overlap {n_ov}")
+    return FullbandGeometry(f_lo, bandwidth_mhz, n_chan, frame, fs, float(dm), int(n_fft),
+                            int(n_ov), int(n_fft - n_ov), int(n_avg), n_d)
+
+
+def inverse_channelise(vin: np.ndarray) -> np.ndarray:
+    """int8 [T][C][2] spectra -> real float64 [T * 2C]: the inverse real FFT of
+    every frame (bins 0..C-1 from the data, the Nyquist bin C zero; numpy's
+    inverse real FFT keeps only the real part of bin 0), frames in series."""
+    spec = vin[..., 0].astype(np.float64) + 1j * vin[..., 1].astype(np.float64)   # [T][C]
+    full = np.concatenate([spec, np.zeros((spec.shape[0], 1))], axis=1)           # + Nyquist
+    return np.fft.irfft(full, n=2 * spec.shape[1], axis=1).reshape(-1)
+
+
+def fullband_filter(geo: FullbandGeometry, taper_kind: str = "none") -> np.ndarray:
+    """The chirp function on the N/2 + 1 bins of the long real FFT (Sec. 4.3):
+    bin j sits f_l = j * fs / N above the band's lower edge f_o (Eq. 3 with f_o
+    the band edge, Sec. 2.1)."""
+    f_l = np.arange(geo.n_fft // 2 + 1) * (geo.fs_mhz / geo.n_fft)
+    h = np.exp(1j * chirp_phase(geo.f_lo_mhz, f_l, geo.dm))
+    return np.conj(h) * taper(f_l, geo.bandwidth_mhz, taper_kind)
+
+
+def dedisperse_fullband(vin: np.ndarray, geo: FullbandGeometry, return_voltages: bool = False):
+    """Inverse channelisation, then overlap-save with the long real FFT, the
+    chirp and the inverse real FFT, then squaring and integration (zero history
+    before the record).  Returns the intensity series float64 [n_seg*h/n_avg]."""
+    x = inverse_channelise(vin)
+    filt = fullband_filter(geo)
+    n_seg = x.size // geo.hop
+    xp = np.concatenate([np.zeros(geo.n_ov), x])
+    v = np.empty(n_seg * geo.hop)
+    for s in range(n_seg):
+        u = xp[s * geo.hop: s * geo.hop + geo.n_fft]
+        y = np.fft.irfft(np.fft.rfft(u) * filt, n=geo.n_fft)
+        v[s * geo.hop:(s + 1) * geo.hop] = y[geo.n_ov:]
+    out = integrate(v * v, geo.n_avg)
+    return (out, v) if return_voltages else out
