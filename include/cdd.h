@@ -227,6 +227,35 @@ int cdd_batch_reset(cdd_batch batch);
 int cdd_batch_destroy(cdd_batch batch);
 
 /* ------------------------------------------------------------------------
+ * Full-band mode: the paper's own design (Sec. 2.3, Sec. 3.1, Sec. 4.3).
+ * The input is the voltage beam as recorded: for every frame, the C complex
+ * outputs of a 2C-point FFT of the real, Nyquist-sampled voltage (bins 0..C-1;
+ * 2C a power of two, 64..16384).  Each frame is inverse transformed back to
+ * 2C real samples (bin 0 real part only, the Nyquist bin zero, scaled by
+ * 1/(2C)); the real series at 2|B| samples per second is then dedispersed as
+ * one band: N-point transforms (N a power of two up to 2^27, or 0 for the
+ * Sec. 2.3 rule: the smallest power of two above twice the dispersion samples
+ * across the band), the chirp of Eq. 3 with f_o the band's lower edge on every
+ * bin, inverse transforms, overlap-save with an overlap of the dispersion
+ * samples rounded up to whole frames and integration windows, squaring and
+ * integration over n_avg samples (a power of two).  Upper sideband only.
+ *   d_in: device int8 [frames][C][2], frames = q*h/(2C) per block
+ *         (CDD_ATTR_BLOCK_SAMPLES reports frames for this plan type);
+ *   d_out: device float [q*h/n_avg], the band's intensity series.
+ * Streams continue across calls (the last n_ov real samples lead the next
+ * block).  Segments run one after another, each over the whole GPU. */
+typedef struct cdd_fullband_s* cdd_fullband;
+
+int cdd_fullband_create(cdd_fullband* plan, double f_center_mhz, double bandwidth_mhz, int n_chan,
+                        double dm, long long n_fft, int n_avg);
+/* Only CDD_ATTR_SEGMENTS_PER_BLOCK, before the first execute. */
+int cdd_fullband_set(cdd_fullband plan, int attr, int64_t value);
+int cdd_fullband_get(cdd_fullband plan, int attr, int64_t* value);
+int cdd_fullband_execute(cdd_fullband plan, const int8_t* d_in, float* d_out, cudaStream_t stream);
+int cdd_fullband_reset(cdd_fullband plan);
+int cdd_fullband_destroy(cdd_fullband plan);
+
+/* ------------------------------------------------------------------------
  * Serving pool: concurrent observation streams on one GPU.  A stream is
  * admitted when its plan's device bytes (CDD_ATTR_BYTES_NEEDED) fit the pool's
  * remaining HBM budget and a slot is free, otherwise CDD_EBUSY; admission

@@ -42,7 +42,8 @@ EXPORTS = ("cdd_plan_create", "cdd_plan_set", "cdd_plan_get", "cdd_plan_shifts",
            "cdd_batch_shifts", "cdd_batch_execute", "cdd_batch_reset", "cdd_batch_destroy",
            "cdd_plan_commit", "cdd_execute_dual", "cdd_band_sum", "cdd_pool_create", "cdd_pool_admit", "cdd_pool_stream_get",
            "cdd_pool_submit", "cdd_pool_wait", "cdd_pool_release", "cdd_pool_get",
-           "cdd_pool_destroy")
+           "cdd_pool_destroy", "cdd_fullband_create", "cdd_fullband_set", "cdd_fullband_get",
+           "cdd_fullband_execute", "cdd_fullband_reset", "cdd_fullband_destroy")
 
 
 class CddError(RuntimeError):
@@ -79,6 +80,13 @@ def _load() -> ctypes.CDLL:
     lib.cdd_batch_reset.argtypes = [vp]
     lib.cdd_batch_destroy.argtypes = [vp]
     lib.cdd_plan_commit.argtypes = [vp]
+    lib.cdd_fullband_create.argtypes = [ctypes.POINTER(vp), ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int, ctypes.c_double, ctypes.c_longlong, ctypes.c_int]
+    lib.cdd_fullband_set.argtypes = [vp, ctypes.c_int, ctypes.c_int64]
+    lib.cdd_fullband_get.argtypes = [vp, ctypes.c_int, i64p]
+    lib.cdd_fullband_execute.argtypes = [vp, vp, vp, vp]
+    lib.cdd_fullband_reset.argtypes = [vp]
+    lib.cdd_fullband_destroy.argtypes = [vp]
     lib.cdd_execute_dual.argtypes = [vp, vp, vp, vp, vp]
     lib.cdd_band_sum.argtypes = [vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int64, vp, vp]
     lib.cdd_pool_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int64, ctypes.c_int]
@@ -253,6 +261,40 @@ def band_sum(out):
     cdd_band_sum(out.data_ptr(), planes, c, n, res.data_ptr(),
                  torch.cuda.current_stream(out.device).cuda_stream)
     return res
+
+
+def cdd_fullband_create(f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft=0, n_avg=1) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.cdd_fullband_create(ctypes.byref(h), float(f_center_mhz), float(bandwidth_mhz),
+                                    int(n_chan), float(dm), int(n_fft), int(n_avg)),
+           "cdd_fullband_create")
+    return h.value
+
+
+def cdd_fullband_set(plan: int, attr, value: int) -> None:
+    a = ATTR[attr] if isinstance(attr, str) else int(attr)
+    _check(_lib.cdd_fullband_set(ctypes.c_void_p(plan), a, int(value)), "cdd_fullband_set")
+
+
+def cdd_fullband_get(plan: int, attr) -> int:
+    a = ATTR[attr] if isinstance(attr, str) else int(attr)
+    v = ctypes.c_int64()
+    _check(_lib.cdd_fullband_get(ctypes.c_void_p(plan), a, ctypes.byref(v)), "cdd_fullband_get")
+    return int(v.value)
+
+
+def cdd_fullband_execute(plan: int, d_in: int, d_out: int, stream: int = 0) -> None:
+    _check(_lib.cdd_fullband_execute(ctypes.c_void_p(plan), ctypes.c_void_p(d_in),
+                                     ctypes.c_void_p(d_out), ctypes.c_void_p(stream)),
+           "cdd_fullband_execute")
+
+
+def cdd_fullband_reset(plan: int) -> None:
+    _check(_lib.cdd_fullband_reset(ctypes.c_void_p(plan)), "cdd_fullband_reset")
+
+
+def cdd_fullband_destroy(plan: int) -> None:
+    _check(_lib.cdd_fullband_destroy(ctypes.c_void_p(plan)), "cdd_fullband_destroy")
 
 
 def cdd_plan_commit(plan: int) -> None:
@@ -467,6 +509,64 @@ class Batch:
     def close(self):
         if self.handle:
             cdd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Fullband:
+    """Owning wrapper of a full-band plan (the paper's own design)."""
+
+    def __init__(self, f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft=0, n_avg=1,
+                 segments_per_block=1):
+        self.handle = cdd_fullband_create(f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft, n_avg)
+        try:
+            cdd_fullband_set(self.handle, "segments_per_block", segments_per_block)
+        except Exception:
+            cdd_fullband_destroy(self.handle)
+            raise
+        self.n_chan = int(n_chan)
+
+    def get(self, attr) -> int:
+        return cdd_fullband_get(self.handle, attr)
+
+    @property
+    def frames(self) -> int:
+        return self.get("block_samples")
+
+    @property
+    def n_out(self) -> int:
+        return self.get("n_out_per_block")
+
+    def execute(self, vin, out=None):
+        import torch
+        if vin.dtype != torch.int8 or tuple(vin.shape) != (self.frames, self.n_chan, 2) \
+                or not vin.is_contiguous() or vin.device.type != "cuda":
+            raise ValueError(f"input must be contiguous device int8 [{self.frames}][{self.n_chan}][2]")
+        if out is None:
+            out = torch.empty((self.n_out,), dtype=torch.float32, device=vin.device)
+        if out.dtype != torch.float32 or tuple(out.shape) != (self.n_out,) or not out.is_contiguous():
+            raise ValueError("output must be contiguous device float32 [n_out]")
+        cdd_fullband_execute(self.handle, vin.data_ptr(), out.data_ptr(),
+                             torch.cuda.current_stream(vin.device).cuda_stream)
+        return out
+
+    def reset(self):
+        cdd_fullband_reset(self.handle)
+
+    def close(self):
+        if self.handle:
+            cdd_fullband_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

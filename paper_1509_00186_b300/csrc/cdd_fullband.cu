@@ -1,0 +1,648 @@
+// cdd_fullband.cu -- the paper's full-band mode: the voltage beam's frames of
+// 2C-point spectra are inverse transformed back to the real series (Sec. 3.1),
+// and one long transform over the whole band is chirped and inverted with
+// overlap-save (Sec. 2.3, Sec. 4.3), then squared and integrated (Sec. 3.1).
+//
+// The real series is transformed as a complex one (zero imaginary part) with a
+// Hermitian chirp, so the inverse is real up to rounding and its real part is
+// kept.  N = L_out * L_mid, L_mid = min(N, 16384):
+//   outer DIF passes   radix <= 16 per pass through HBM, one thread per
+//                      butterfly, twiddles from two small tables
+//   middle kernel      each contiguous L_mid sub-transform in shared memory:
+//                      forward passes, chirp, inverse passes
+//   outer DIT passes   back through HBM; the last writes Re(y)^2
+//   integrate          sums n_avg samples of the kept part of the segment
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/cdd.h"
+#include "cdd_fft.cuh"
+#include "cdd_internal.h"
+#include "cdd_passes.cuh"
+
+namespace cdd {
+namespace {
+
+using namespace passes;
+
+constexpr int kMidLog = 14;                 // L_mid for N > 16384
+constexpr int kTwLoBits = 13;               // two-level twiddle table split
+
+// w_N^e = hi[e >> 13] * lo[e & 8191]
+__device__ __forceinline__ float2 twiddle(const float2* __restrict__ hi, const float2* __restrict__ lo,
+                                          long long e) {
+  return cmul(__ldg(&hi[e >> kTwLoBits]), __ldg(&lo[e & ((1 << kTwLoBits) - 1)]));
+}
+
+// ---- inverse channelisation: frame t of C bins -> 2C real samples --------
+// Positions of the working buffer hold the Hermitian extension of the frame's
+// spectrum in digit-reversed order (bin 0 real part only, bin C zero); the
+// inverse passes leave the series in natural order.
+template <int LOGF>
+__global__ void __launch_bounds__(Cfg<LOGF>::THREADS)
+icf_kernel(const char2* __restrict__ in, float* __restrict__ ts, const float2* __restrict__ twf,
+           long long n_frames, int n_chan) {
+  using PL = PassPlan<LOGF>;
+  using CF = Cfg<LOGF>;
+  constexpr int F = PL::N;                  // 2C
+  extern __shared__ float2 smem[];
+  const int g = threadIdx.x / PL::T;
+  const int lt = threadIdx.x % PL::T;
+  float2* buf = smem + g * CF::SEG_F2;
+  const long long t = (long long)blockIdx.x * CF::G + g;
+  const bool active = t < n_frames;
+  if (active) {
+    const unsigned short* row = reinterpret_cast<const unsigned short*>(in) + t * n_chan;
+    for (int pos = lt; pos < F; pos += PL::T) {
+      const int b = position_to_bin<LOGF>(pos);
+      float2 v = make_float2(0.f, 0.f);
+      if (b == 0) {
+        v = unpack_i8x2(__ldg(row));
+        v.y = 0.f;
+      } else if (b < F / 2) {
+        v = unpack_i8x2(__ldg(row + b));
+      } else if (b > F / 2) {
+        v = unpack_i8x2(__ldg(row + (F - b)));
+        v.y = -v.y;
+      }
+      buf[pad(pos)] = v;
+    }
+  }
+  __syncthreads();
+  static_for<0, PL::P>([&](auto I_) {
+    if (active) inv_pass<LOGF, PL::P - 1 - decltype(I_)::value>(buf, twf, lt);
+    __syncthreads();
+  });
+  if (active) {
+    float* out = ts + t * F;
+    for (int n = lt; n < F; n += PL::T) out[n] = buf[pad(n)].x * (1.0f / F);
+  }
+}
+
+// ---- outer passes through HBM --------------------------------------------
+// DIF radix-R pass of stride S over N points (sub-problems of M = R*S), in place.
+// FIRST: the input is the real series ts (imaginary part zero).
+template <int R, bool FIRST>
+__global__ void __launch_bounds__(256)
+outer_fwd_kernel(float2* __restrict__ w, const float* __restrict__ ts, long long n, long long s,
+                 const float2* __restrict__ thi, const float2* __restrict__ tlo) {
+  const long long nb = n / R;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+       b += (long long)gridDim.x * blockDim.x) {
+    const long long t = b % s;
+    const long long base = (b / s) * (s * R) + t;
+    float2 v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      v[j] = FIRST ? make_float2(__ldg(&ts[base + s * j]), 0.f) : w[base + s * j];
+    dft<R, -1>(v);
+    const long long step = n / (s * R);     // w_M^{t k} = w_N^{t k N/M}
+#pragma unroll
+    for (int k = 1; k < R; ++k) v[k] = cmul(v[k], twiddle(thi, tlo, ((t * k) % (s * R)) * step));
+#pragma unroll
+    for (int k = 0; k < R; ++k) w[base + s * k] = v[k];
+  }
+}
+
+// DIT radix-R pass of stride S, in place; LAST (stride N/R) writes Re(y)^2.
+template <int R, bool LAST>
+__global__ void __launch_bounds__(256)
+outer_inv_kernel(float2* __restrict__ w, float* __restrict__ pw, long long n, long long s,
+                 const float2* __restrict__ thi, const float2* __restrict__ tlo) {
+  const long long nb = n / R;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
+       b += (long long)gridDim.x * blockDim.x) {
+    const long long t = b % s;
+    const long long base = (b / s) * (s * R) + t;
+    const long long step = n / (s * R);
+    float2 v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = w[base + s * k];
+#pragma unroll
+    for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], twiddle(thi, tlo, ((t * k) % (s * R)) * step));
+    dft<R, 1>(v);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      if (LAST) pw[base + s * j] = v[j].x * v[j].x;
+      else w[base + s * j] = v[j];
+    }
+  }
+}
+
+// ---- middle: contiguous sub-transforms of 2^LOGS points in shared memory --
+// Sub-transform qq holds bins bin_out(qq) + L_out * (its own bins); chirp is the
+// per-bin table in the chirp pass's order.  ts != nullptr: the series is real
+// and there are no outer passes (N = 2^LOGS); pw != nullptr: write Re(y)^2.
+template <int LOGS>
+__global__ void __launch_bounds__(Cfg<LOGS>::THREADS, 1)
+middle_kernel(float2* __restrict__ w, const float* __restrict__ ts, float* __restrict__ pw,
+              const float2* __restrict__ chirp, const float2* __restrict__ tw, long long n_sub) {
+  using PL = PassPlan<LOGS>;
+  using CF = Cfg<LOGS>;
+  constexpr int NS = PL::N;
+  extern __shared__ float2 smem[];
+  const int g = threadIdx.x / PL::T;
+  const int lt = threadIdx.x % PL::T;
+  float2* buf = smem + g * CF::SEG_F2;
+  const long long qq = (long long)blockIdx.x * CF::G + g;
+  const bool active = qq < n_sub;
+  float2* wq = w + qq * NS;
+  if (active) {
+    for (int i = lt; i < NS; i += PL::T)
+      buf[pad(i)] = ts ? make_float2(__ldg(&ts[qq * NS + i]), 0.f) : wq[i];
+  }
+  __syncthreads();
+  static_for<0, PL::P - 1>([&](auto P_) {
+    constexpr int pp = decltype(P_)::value;
+    if (active) fwd_pass<LOGS, pp>(buf, tw, lt);
+    __syncthreads();
+  });
+  if (active) chirp_pass<LOGS>(buf, chirp + qq * NS, lt);
+  __syncthreads();
+  static_for<0, PL::P - 1>([&](auto I_) {
+    constexpr int pp = PL::P - 2 - decltype(I_)::value;
+    if (active) inv_pass<LOGS, pp>(buf, tw, lt);
+    __syncthreads();
+  });
+  if (active) {
+    for (int i = lt; i < NS; i += PL::T) {
+      const float2 v = buf[pad(i)];
+      if (pw) pw[qq * NS + i] = v.x * v.x;
+      else wq[i] = v;
+    }
+  }
+}
+
+// out[m] = sum of n_avg samples of pw from n_ov on (the kept part of a segment)
+__global__ void fb_integrate_kernel(const float* __restrict__ pw, float* __restrict__ out,
+                                    long long n_ov, int n_avg, long long n_out) {
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < n_out;
+       m += (long long)gridDim.x * blockDim.x) {
+    const float* p = pw + n_ov + m * n_avg;
+    float acc = 0.f;
+    for (int i = 0; i < n_avg; ++i) acc += __ldg(&p[i]);
+    out[m] = acc;
+  }
+}
+
+// ---- plan-time tables (FP64) ----------------------------------------------
+__global__ void fb_twiddle_kernel(float2* hi, float2* lo, long long n) {
+  const long long n_hi = n >> kTwLoBits;
+  const long long total = n_hi + (1 << kTwLoBits);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long m = e < n_hi ? (e << kTwLoBits) : e - n_hi;
+    double sn, cs;
+    sincospi(2.0 * (double)m / (double)n, &sn, &cs);
+    const float2 v = make_float2((float)cs, (float)(-sn));
+    if (e < n_hi) hi[e] = v;
+    else lo[e - n_hi] = v;
+  }
+}
+
+// chirp[qq * NS + idx] for the bin held there: Hermitian (bins above N/2 take
+// the conjugate of their mirror) so the inverse transform stays real.
+template <int LOGS>
+__global__ void fb_chirp_kernel(float2* chirp, long long n, int n_outer, const int* radix_out,
+                                const long long* stride_out, const long long* rprod_out,
+                                double f_lo, double fs, double dm) {
+  using PL = PassPlan<LOGS>;
+  constexpr int NS = PL::N;
+  constexpr int NG = NS / PL::RL;
+  const long long l_out = n / NS;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long qq = e / NS;
+    const int idx = (int)(e % NS);
+    long long b_out = 0;
+    for (int p = 0; p < n_outer; ++p) {
+      const long long d = (qq / (stride_out[p] / NS)) % radix_out[p];
+      b_out += d * rprod_out[p];
+    }
+    const int pos = (idx % NG) * PL::RL + idx / NG;
+    const long long bin = b_out + l_out * position_to_bin<LOGS>(pos);
+    const long long mb = bin <= n / 2 ? bin : n - bin;     // mirror for the upper half
+    const double f_l = (double)mb * (fs / (double)n);
+    const double turns = kDispD * 1e6 * dm * f_l * f_l / ((f_l + f_lo) * f_lo * f_lo);
+    const double frac = turns - rint(turns);
+    double sn, cs;
+    sincospi(2.0 * frac, &sn, &cs);
+    const double sc = 1.0 / (double)n;
+    // exp(-i Phi) / N below N/2 (and at it); the conjugate above
+    chirp[e] = make_float2((float)(cs * sc), (float)((bin <= n / 2 ? -sn : sn) * sc));
+  }
+}
+
+unsigned grid_for(long long work, int block = 256) {
+  long long g = (work + block - 1) / block;
+  if (g > 148LL * 32) g = 148LL * 32;
+  return (unsigned)(g > 0 ? g : 1);
+}
+
+template <int LOGF>
+cudaError_t launch_icf_t(const char2* in, float* ts, const float2* twf, long long n_frames, int n_chan,
+                         cudaStream_t s) {
+  using CF = Cfg<LOGF>;
+  static bool set[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 128 && !set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(icf_kernel<LOGF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CF::SMEM);
+    if (e != cudaSuccess) return e;
+    set[dev] = true;
+  }
+  icf_kernel<LOGF><<<(unsigned)((n_frames + CF::G - 1) / CF::G), CF::THREADS, CF::SMEM, s>>>(in, ts, twf, n_frames, n_chan);
+  return cudaGetLastError();
+}
+
+template <int LOGS>
+cudaError_t launch_middle_t(float2* w, const float* ts, float* pw, const float2* chirp,
+                            const float2* tw, long long n_sub, cudaStream_t s) {
+  using CF = Cfg<LOGS>;
+  static bool set[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 128 && !set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(middle_kernel<LOGS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CF::SMEM);
+    if (e != cudaSuccess) return e;
+    set[dev] = true;
+  }
+  middle_kernel<LOGS><<<(unsigned)((n_sub + CF::G - 1) / CF::G), CF::THREADS, CF::SMEM, s>>>(w, ts, pw, chirp, tw, n_sub);
+  return cudaGetLastError();
+}
+
+#define CDD_FB_CASES(X) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14)
+
+cudaError_t launch_icf(int logf, const char2* in, float* ts, const float2* twf, long long n_frames,
+                      int n_chan, cudaStream_t s) {
+  switch (logf) {
+#define X(L) case L: return launch_icf_t<L>(in, ts, twf, n_frames, n_chan, s);
+    CDD_FB_CASES(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_middle(int logs, float2* w, const float* ts, float* pw, const float2* chirp,
+                          const float2* tw, long long n_sub, cudaStream_t s) {
+  switch (logs) {
+#define X(L) case L: return launch_middle_t<L>(w, ts, pw, chirp, tw, n_sub, s);
+    CDD_FB_CASES(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_outer(bool forward, bool edge, int radix, float2* w, const float* ts, float* pw,
+                         long long n, long long stride, const float2* thi, const float2* tlo,
+                         cudaStream_t s) {
+  const unsigned grid = grid_for(n / radix);
+#define CDD_OUTER(R)                                                                           \
+  case R:                                                                                      \
+    if (forward && edge) outer_fwd_kernel<R, true><<<grid, 256, 0, s>>>(w, ts, n, stride, thi, tlo);   \
+    else if (forward) outer_fwd_kernel<R, false><<<grid, 256, 0, s>>>(w, ts, n, stride, thi, tlo);     \
+    else if (edge) outer_inv_kernel<R, true><<<grid, 256, 0, s>>>(w, pw, n, stride, thi, tlo);         \
+    else outer_inv_kernel<R, false><<<grid, 256, 0, s>>>(w, pw, n, stride, thi, tlo);                  \
+    break;
+  switch (radix) {
+    CDD_OUTER(2) CDD_OUTER(4) CDD_OUTER(8) CDD_OUTER(16)
+    default: return cudaErrorInvalidValue;
+  }
+#undef CDD_OUTER
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fb_chirp(int logs, float2* chirp, long long n, int n_outer, const int* radix,
+                            const long long* stride, const long long* rprod, double f_lo, double fs,
+                            double dm, cudaStream_t s) {
+  const unsigned grid = grid_for(n);
+  switch (logs) {
+#define X(L) case L: fb_chirp_kernel<L><<<grid, 256, 0, s>>>(chirp, n, n_outer, radix, stride, rprod, f_lo, fs, dm); break;
+    CDD_FB_CASES(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace cdd
+
+// ------------------------------------------------------------------ host side
+
+struct cdd_fullband_s {
+  double f_center = 0, bandwidth = 0, dm = 0, f_lo = 0, fs = 0, n_disp = 0;
+  int n_chan = 0, frame = 0, logf = 0, n_avg = 0;
+  long long n_fft = 0, n_ov = 0, hop = 0;
+  int logs = 0;                              // log2 L_mid
+  std::vector<int> radix_out;                // outer DIF radices, pass 0 first
+  std::vector<long long> stride_out, rprod_out;
+  int q = 1;
+  bool committed = false;
+  int device = -1;
+  int sticky = CDD_OK;
+  float* d_ts[2] = {nullptr, nullptr};       // [n_ov + q*h] real series, ping-pong
+  float2* d_w = nullptr;                     // [N] work
+  float* d_pw = nullptr;                     // [N] detected power of a segment
+  float2* d_chirp = nullptr;                 // [N]
+  float2* d_tw = nullptr;                    // twiddles of the L_mid passes
+  float2* d_twf = nullptr;                   // twiddles of the frame transform
+  float2* d_thi = nullptr;
+  float2* d_tlo = nullptr;
+  int* d_radix = nullptr;
+  long long* d_stride = nullptr;
+  long long* d_rprod = nullptr;
+  int cur = 0;
+  int64_t blocks = 0;
+  size_t bytes_device = 0;
+  int last_launches = 0;
+};
+
+namespace {
+
+int ffail(cdd_fullband f, cudaError_t e) {
+  if (e == cudaSuccess) return CDD_OK;
+  f->sticky = CDD_ECUDA;
+  return CDD_ECUDA;
+}
+
+#define FTRY(f, call)                              \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return ffail(f, e_);    \
+  } while (0)
+
+template <class T>
+int falloc(cdd_fullband f, T** p, size_t bytes) {
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    *p = nullptr;
+    return CDD_ENOMEM;
+  }
+  if (e != cudaSuccess) return ffail(f, e);
+  f->bytes_device += bytes;
+  return CDD_OK;
+}
+
+long long ts_len(const cdd_fullband f) { return f->n_ov + (long long)f->q * f->hop; }
+
+int fcommit_once(cdd_fullband f) {
+  FTRY(f, cudaGetDevice(&f->device));
+  const long long n = f->n_fft;
+  int rc;
+  for (int i = 0; i < 2; ++i)
+    if ((rc = falloc(f, &f->d_ts[i], (size_t)ts_len(f) * sizeof(float)))) return rc;
+  if ((rc = falloc(f, &f->d_w, (size_t)n * sizeof(float2)))) return rc;
+  if ((rc = falloc(f, &f->d_pw, (size_t)n * sizeof(float)))) return rc;
+  if ((rc = falloc(f, &f->d_chirp, (size_t)n * sizeof(float2)))) return rc;
+  if ((rc = falloc(f, &f->d_tw, (size_t)cdd::twiddle_table_len(f->logs) * sizeof(float2)))) return rc;
+  if ((rc = falloc(f, &f->d_twf, (size_t)cdd::twiddle_table_len(f->logf) * sizeof(float2)))) return rc;
+  const long long n_hi = n >> cdd::kTwLoBits;
+  if (!f->radix_out.empty()) {
+    if ((rc = falloc(f, &f->d_thi, (size_t)(n_hi > 0 ? n_hi : 1) * sizeof(float2)))) return rc;
+    if ((rc = falloc(f, &f->d_tlo, (size_t)(1 << cdd::kTwLoBits) * sizeof(float2)))) return rc;
+  }
+  const size_t no = f->radix_out.size() > 0 ? f->radix_out.size() : 1;
+  if ((rc = falloc(f, &f->d_radix, no * sizeof(int)))) return rc;
+  if ((rc = falloc(f, &f->d_stride, no * sizeof(long long)))) return rc;
+  if ((rc = falloc(f, &f->d_rprod, no * sizeof(long long)))) return rc;
+  if (!f->radix_out.empty()) {
+    FTRY(f, cudaMemcpy(f->d_radix, f->radix_out.data(), no * sizeof(int), cudaMemcpyHostToDevice));
+    FTRY(f, cudaMemcpy(f->d_stride, f->stride_out.data(), no * sizeof(long long), cudaMemcpyHostToDevice));
+    FTRY(f, cudaMemcpy(f->d_rprod, f->rprod_out.data(), no * sizeof(long long), cudaMemcpyHostToDevice));
+  }
+  cudaStream_t s;
+  FTRY(f, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  cudaError_t e = cdd::launch_twiddle_table(f->logs, f->d_tw, s);
+  if (e == cudaSuccess) e = cdd::launch_twiddle_table(f->logf, f->d_twf, s);
+  if (e == cudaSuccess && f->d_thi) {
+    cdd::fb_twiddle_kernel<<<cdd::grid_for(n_hi + (1 << cdd::kTwLoBits)), 256, 0, s>>>(f->d_thi, f->d_tlo, n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cdd::launch_fb_chirp(f->logs, f->d_chirp, n, (int)f->radix_out.size(), f->d_radix, f->d_stride,
+                             f->d_rprod, f->f_lo, f->fs, f->dm, s);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+    e = cudaMemsetAsync(f->d_ts[i], 0, (size_t)ts_len(f) * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess) return ffail(f, e);
+  f->committed = true;
+  return CDD_OK;
+}
+
+int fprepare(cdd_fullband f) {
+  if (!f) return CDD_EINVAL;
+  if (f->sticky) return f->sticky;
+  if (!f->committed) {
+    const int rc = fcommit_once(f);
+    if (rc != CDD_OK) {
+      f->sticky = rc;
+      return rc;
+    }
+  }
+  int dev = -1;
+  FTRY(f, cudaGetDevice(&dev));
+  return dev == f->device ? CDD_OK : CDD_EINVAL;
+}
+
+void ffree(cdd_fullband f) {
+  cudaFree(f->d_ts[0]);
+  cudaFree(f->d_ts[1]);
+  cudaFree(f->d_w);
+  cudaFree(f->d_pw);
+  cudaFree(f->d_chirp);
+  cudaFree(f->d_tw);
+  cudaFree(f->d_twf);
+  cudaFree(f->d_thi);
+  cudaFree(f->d_tlo);
+  cudaFree(f->d_radix);
+  cudaFree(f->d_stride);
+  cudaFree(f->d_rprod);
+}
+
+long long next_pow2_above_ll(double x) {
+  long long n = 1;
+  while ((double)n <= x && n < (1LL << 40)) n *= 2;
+  return n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cdd_fullband_create(cdd_fullband* out, double f_center_mhz, double bandwidth_mhz, int n_chan,
+                        double dm, long long n_fft, int n_avg) {
+  if (!out) return CDD_EINVAL;
+  *out = nullptr;
+  if (!(f_center_mhz > 0) || !(bandwidth_mhz > 0) || n_chan <= 0 || !(dm >= 0) || !isfinite(dm) ||
+      n_avg <= 0 || n_fft < 0)
+    return CDD_EINVAL;
+  const int frame = 2 * n_chan;
+  if ((frame & (frame - 1)) || (n_avg & (n_avg - 1))) return CDD_EINVAL;
+  int logf = 0;
+  while ((1 << logf) < frame) ++logf;
+  if (logf < 6 || logf > 14) return CDD_EUNSUPPORTED;
+  cdd_fullband f = new (std::nothrow) cdd_fullband_s();
+  if (!f) return CDD_ENOMEM;
+  f->f_center = f_center_mhz;
+  f->bandwidth = bandwidth_mhz;
+  f->dm = dm;
+  f->n_chan = n_chan;
+  f->frame = frame;
+  f->logf = logf;
+  f->n_avg = n_avg;
+  f->f_lo = f_center_mhz - bandwidth_mhz / 2.0;
+  f->fs = 2.0 * bandwidth_mhz;
+  int rc = CDD_OK;
+  if (!(f->f_lo > 0)) rc = CDD_EINVAL;
+  if (rc == CDD_OK) {
+    const double D = 4.148808e3;
+    f->n_disp = D * dm * (pow(f->f_lo, -2.0) - pow(f->f_lo + bandwidth_mhz, -2.0)) * f->fs * 1e6;
+    const long long unit = frame > n_avg ? frame : n_avg;
+    long long ov = (long long)ceil(f->n_disp);
+    f->n_ov = (ov + unit - 1) / unit * unit;
+    if (n_fft == 0) {
+      n_fft = next_pow2_above_ll(2.0 * f->n_disp);
+      const long long b = next_pow2_above_ll((double)f->n_ov);
+      if (b > n_fft) n_fft = b;
+      if (n_fft < 2 * unit) n_fft = 2 * unit;
+      if (n_fft < 64) n_fft = 64;
+    }
+    if (n_fft <= 0 || (n_fft & (n_fft - 1)) || n_fft <= f->n_ov || (n_fft - f->n_ov) % unit) rc = CDD_EINVAL;
+    else if (n_fft < 64 || n_fft > (1LL << 27)) rc = CDD_EUNSUPPORTED;
+  }
+  if (rc == CDD_OK) {
+    f->n_fft = n_fft;
+    f->hop = n_fft - f->n_ov;
+    int logn = 0;
+    while ((1LL << logn) < n_fft) ++logn;
+    f->logs = logn < cdd::kMidLog ? logn : cdd::kMidLog;
+    int rest = logn - f->logs;               // outer passes: radix 16, then what remains
+    long long stride = n_fft, rprod = 1;
+    while (rest > 0) {
+      const int lr = rest >= 4 ? 4 : rest;
+      stride >>= lr;
+      f->radix_out.push_back(1 << lr);
+      f->stride_out.push_back(stride);
+      f->rprod_out.push_back(rprod);
+      rprod <<= lr;
+      rest -= lr;
+    }
+  }
+  if (rc != CDD_OK) {
+    delete f;
+    return rc;
+  }
+  *out = f;
+  return CDD_OK;
+}
+
+int cdd_fullband_set(cdd_fullband f, int attr, int64_t value) {
+  if (!f) return CDD_EINVAL;
+  if (f->committed) return CDD_ESTATE;
+  if (attr != CDD_ATTR_SEGMENTS_PER_BLOCK || value < 1 || value * f->hop > ((int64_t)1 << 36))
+    return CDD_EINVAL;
+  f->q = (int)value;
+  return CDD_OK;
+}
+
+int cdd_fullband_get(cdd_fullband f, int attr, int64_t* v) {
+  if (!f || !v) return CDD_EINVAL;
+  switch (attr) {
+    case CDD_ATTR_N_FFT: *v = f->n_fft; break;
+    case CDD_ATTR_N_OV: *v = f->n_ov; break;
+    case CDD_ATTR_HOP: *v = f->hop; break;
+    case CDD_ATTR_N_AVG: *v = f->n_avg; break;
+    case CDD_ATTR_N_CHAN: *v = f->n_chan; break;
+    case CDD_ATTR_SEGMENTS_PER_BLOCK: *v = f->q; break;
+    case CDD_ATTR_BLOCK_SAMPLES: *v = (int64_t)f->q * f->hop / f->frame; break;   // frames
+    case CDD_ATTR_N_OUT_PER_BLOCK: *v = (int64_t)f->q * f->hop / f->n_avg; break;
+    case CDD_ATTR_BYTES_DEVICE: *v = (int64_t)f->bytes_device; break;
+    case CDD_ATTR_BLOCKS_DONE: *v = f->blocks; break;
+    case CDD_ATTR_KERNEL_LAUNCHES: *v = f->last_launches; break;
+    default: return CDD_EINVAL;
+  }
+  return CDD_OK;
+}
+
+int cdd_fullband_execute(cdd_fullband f, const int8_t* d_in, float* d_out, cudaStream_t s) {
+  if (!f || !d_in || !d_out) return CDD_EINVAL;
+  int rc = fprepare(f);
+  if (rc) return rc;
+  const long long n = f->n_fft, h = f->hop, nov = f->n_ov;
+  float* ts = f->d_ts[f->cur];
+  float* prev = f->d_ts[f->cur ^ 1];
+  int launches = 0;
+  // the previous block's last n_ov samples lead this block's series (Sec. 4.3)
+  if (nov > 0) {
+    FTRY(f, cudaMemcpyAsync(ts, prev + (long long)f->q * h, (size_t)nov * sizeof(float),
+                            cudaMemcpyDeviceToDevice, s));
+  }
+  const long long frames = (long long)f->q * h / f->frame;
+  FTRY(f, cdd::launch_icf(f->logf, reinterpret_cast<const char2*>(d_in), ts + nov, f->d_twf, frames,
+                          f->n_chan, s));
+  launches += 1;
+  const int no = (int)f->radix_out.size();
+  const long long n_sub = n >> f->logs;
+  for (int sg = 0; sg < f->q; ++sg) {
+    const float* seg = ts + (long long)sg * h;            // N real samples from here
+    if (no == 0) {
+      FTRY(f, cdd::launch_middle(f->logs, f->d_w, seg, f->d_pw, f->d_chirp, f->d_tw, 1, s));
+      launches += 1;
+    } else {
+      for (int p = 0; p < no; ++p)
+        FTRY(f, cdd::launch_outer(true, p == 0, f->radix_out[p], f->d_w, seg, nullptr, n,
+                                  f->stride_out[p], f->d_thi, f->d_tlo, s));
+      FTRY(f, cdd::launch_middle(f->logs, f->d_w, nullptr, nullptr, f->d_chirp, f->d_tw, n_sub, s));
+      for (int p = no - 1; p >= 0; --p)
+        FTRY(f, cdd::launch_outer(false, p == 0, f->radix_out[p], f->d_w, nullptr, f->d_pw, n,
+                                  f->stride_out[p], f->d_thi, f->d_tlo, s));
+      launches += 2 * no + 1;
+    }
+    const long long n_o = h / f->n_avg;
+    cdd::fb_integrate_kernel<<<cdd::grid_for(n_o), 256, 0, s>>>(f->d_pw, d_out + (long long)sg * n_o,
+                                                               nov, f->n_avg, n_o);
+    FTRY(f, cudaGetLastError());
+    launches += 1;
+  }
+  f->cur ^= 1;
+  f->blocks += 1;
+  f->last_launches = launches;
+  return CDD_OK;
+}
+
+int cdd_fullband_reset(cdd_fullband f) {
+  if (!f) return CDD_EINVAL;
+  if (f->sticky) return f->sticky;
+  if (f->committed) {
+    FTRY(f, cudaDeviceSynchronize());
+    for (int i = 0; i < 2; ++i)
+      FTRY(f, cudaMemset(f->d_ts[i], 0, (size_t)ts_len(f) * sizeof(float)));
+  }
+  f->cur = 0;
+  f->blocks = 0;
+  return CDD_OK;
+}
+
+int cdd_fullband_destroy(cdd_fullband f) {
+  if (!f) return CDD_OK;
+  if (f->device >= 0) {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(f->device);
+    cudaDeviceSynchronize();
+    ffree(f);
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  delete f;
+  return CDD_OK;
+}
+
+}  // extern "C"

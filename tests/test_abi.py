@@ -178,3 +178,38 @@ def test_batch_rejects_bad_requests(cdd):
                 cdd.cdd_batch_set(b, "segments_per_block", 0)
     finally:
         cdd.cdd_batch_destroy(b)
+
+
+FULLBAND = [
+    (325.0, 32.0, 512, 50.0, 0, 16),        # the 32 MHz GSB mode: N = 2^26
+    (610.0, 16.0, 256, 10.0, 0, 16),
+    (610.0, 1.0, 32, 20.0, 0, 4),
+    (325.0, 2.0, 64, 5.0, 1 << 20, 8),
+]
+
+
+@pytest.mark.parametrize("geo", FULLBAND)
+def test_fullband_geometry_matches_oracle(cdd, geo):
+    f_c, bw, C, dm, n_fft, n_avg = geo
+    g = O.fullband_geometry(f_c, bw, C, dm, n_fft, n_avg)
+    f = cdd.cdd_fullband_create(f_c, bw, C, dm, n_fft, n_avg)
+    try:
+        assert cdd.cdd_fullband_get(f, "n_fft") == g.n_fft
+        assert cdd.cdd_fullband_get(f, "n_ov") == g.n_ov
+        assert cdd.cdd_fullband_get(f, "hop") == g.hop
+        assert cdd.cdd_fullband_get(f, "block_samples") * 2 * C == g.hop
+    finally:
+        cdd.cdd_fullband_destroy(f)
+    if geo[0] == 325.0 and geo[1] == 32.0:
+        assert g.n_fft == 2 ** 26
+
+
+def test_fullband_rejects_bad_requests(cdd):
+    for args in [(325.0, 32.0, 500, 50.0, 0, 16),          # frame not a power of two
+                 (325.0, 32.0, 512, 50.0, 1 << 20, 16),    # N below the smear
+                 (325.0, -32.0, 512, 50.0, 0, 16)]:        # lower sideband
+        with pytest.raises(cdd.CddError):
+            cdd.cdd_fullband_create(*args)
+    with pytest.raises(cdd.CddError) as ei:                 # N = 2^28: beyond this build
+        cdd.cdd_fullband_create(325.0, 32.0, 512, 200.0, 0, 16)
+    assert ei.value.code == cdd.CDD_EUNSUPPORTED
