@@ -34,25 +34,22 @@ namespace {
 
 using namespace passes;
 
-template <int LOGN, bool CM>
-__global__ void __launch_bounds__(Cfg<LOGN>::THREADS, Cfg<LOGN>::MINB)
-ols_kernel(const OlsArgs a) {
+#ifndef CDD_PERSISTENT
+#define CDD_PERSISTENT 1
+#endif
+constexpr bool kUsePersistent = CDD_PERSISTENT != 0;
+
+// One overlap-save segment (channel k, segment s) by the T threads of a group:
+// unpack and gather, forward passes, chirp, inverse passes, detection,
+// integration and the aligned store.  `tw` is the whole twiddle table, in
+// global memory or (SH) staged in shared memory; `sync` is the group's barrier.
+template <int LOGN, bool CM, bool SH, class Sync>
+__device__ __forceinline__ void ols_segment(const OlsArgs& a, float2* buf, const float2* tw, int lt,
+                                            bool active, int k, int s, Sync sync) {
   using PL = PassPlan<LOGN>;
-  using CF = Cfg<LOGN>;
   constexpr int N = PL::N;
   constexpr int T = PL::T;
   constexpr int R0 = PL::R(0);
-  static_assert(PL::S(0) == T, "pass 0 stride must equal the threads per transform");
-
-  extern __shared__ float2 smem[];
-  const int g = threadIdx.x / T;
-  const int lt = threadIdx.x % T;
-  float2* buf = smem + g * CF::SEG_F2;
-  const int w = blockIdx.x * CF::G + g;        // n_chan * q < 2^31 (checked by the plan)
-  const bool active = w < a.n_chan * a.s_count;
-  const int k = active ? w % a.n_chan : 0;     // channel fastest: neighbouring CTAs
-  const int s = active ? a.s_begin + w / a.n_chan : 0;   // share the input rows in L2
-
   // ---- pass 0, forward: unpack and gather x[lt + T*j] of this segment
   float2* pb0 = buf + pad(lt);
   float2 v[R0];
@@ -87,23 +84,23 @@ ols_kernel(const OlsArgs a) {
     for (int j = 0; j < R0; ++j) v[j] = unpack_i8x2(c[j]);
     dft<R0, -1>(v);
 #pragma unroll
-    for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], __ldg(&a.tw[kk * T + lt]));
+    for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
 #pragma unroll
     for (int kk = 0; kk < R0; ++kk) pb0[poff<T>(kk)] = v[kk];
   }
-  __syncthreads();
+  sync();
 
   static_for<1, PL::P - 1>([&](auto P_) {
-    if (active) fwd_pass<LOGN, decltype(P_)::value>(buf, a.tw, lt);
-    __syncthreads();
+    if (active) fwd_pass<LOGN, decltype(P_)::value, SH>(buf, tw, lt);
+    sync();
   });
 
   if (active) chirp_pass<LOGN>(buf, a.chirp + (size_t)k * N, lt);
-  __syncthreads();
+  sync();
 
   static_for<1, PL::P - 1>([&](auto I_) {
-    if (active) inv_pass<LOGN, PL::P - 1 - decltype(I_)::value>(buf, a.tw, lt);
-    __syncthreads();
+    if (active) inv_pass<LOGN, PL::P - 1 - decltype(I_)::value, SH>(buf, tw, lt);
+    sync();
   });
 
   // ---- pass 0, inverse: natural-order voltages v[j] = z[lt + T*j]
@@ -111,7 +108,7 @@ ols_kernel(const OlsArgs a) {
 #pragma unroll
     for (int kk = 0; kk < R0; ++kk) v[kk] = pb0[poff<T>(kk)];
 #pragma unroll
-    for (int kk = 1; kk < R0; ++kk) v[kk] = cmulc(v[kk], __ldg(&a.tw[kk * T + lt]));
+    for (int kk = 1; kk < R0; ++kk) v[kk] = cmulc(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
     dft<R0, 1>(v);
     if (a.volt != nullptr) {
       const long long vbase = ((long long)k * a.q + s) * a.hop - a.n_ov;
@@ -122,7 +119,7 @@ ols_kernel(const OlsArgs a) {
       }
     }
   }
-  __syncthreads();                       // every thread has read buf: reuse it
+  sync();                       // every thread has read buf: reuse it
   float* pw = reinterpret_cast<float*>(buf);
   if (active) {
 #pragma unroll
@@ -131,7 +128,7 @@ ols_kernel(const OlsArgs a) {
       pw[n + (n >> 5)] = fmaf(v[j].x, v[j].x, v[j].y * v[j].y);   // one spare word per 32
     }
   }
-  __syncthreads();
+  sync();
 
   if (active) {
     const int n_int = a.hop / a.n_avg;
@@ -157,6 +154,61 @@ ols_kernel(const OlsArgs a) {
     }
   }
 }
+
+template <int LOGN, bool CM>
+__global__ void __launch_bounds__(Cfg<LOGN>::THREADS, Cfg<LOGN>::MINB)
+ols_kernel(const OlsArgs a) {
+  using PL = PassPlan<LOGN>;
+  using CF = Cfg<LOGN>;
+  constexpr int T = PL::T;
+  static_assert(PL::S(0) == T, "pass 0 stride must equal the threads per transform");
+  extern __shared__ float2 smem[];
+  const int g = threadIdx.x / T;
+  const int lt = threadIdx.x % T;
+  float2* buf = smem + g * CF::SEG_F2;
+  const int w = blockIdx.x * CF::G + g;        // n_chan * q < 2^31 (checked by the plan)
+  const bool active = w < a.n_chan * a.s_count;
+  const int k = active ? w % a.n_chan : 0;     // channel fastest: neighbouring CTAs
+  const int s = active ? a.s_begin + w / a.n_chan : 0;   // share the input rows in L2
+  ols_segment<LOGN, CM, false>(a, buf, a.tw, lt, active, k, s, [] { __syncthreads(); });
+}
+
+// Persistent form for N = 4096 and 8192: one CTA per SM with two groups of 256
+// threads, each looping over segments with its own named barrier, and the whole
+// twiddle table staged once in shared memory (in L1 it was evicted by the
+// streaming chirp rows).  Reads the channel-major block.
+template <int LOGN>
+struct Persist {
+  using PL = PassPlan<LOGN>;
+  static constexpr int GROUPS = 2;
+  static constexpr int THREADS = GROUPS * PL::T;
+  static constexpr size_t SMEM = (size_t(PL::TW_LEN) + size_t(GROUPS) * padded_len(PL::N)) * sizeof(float2);
+};
+
+template <int LOGN>
+__global__ void __launch_bounds__(Persist<LOGN>::THREADS, 1)
+ols_persistent_kernel(const OlsArgs a) {
+  using PL = PassPlan<LOGN>;
+  using PS = Persist<LOGN>;
+  constexpr int T = PL::T;
+  extern __shared__ float2 smem[];
+  float2* tws = smem;
+  for (int i = threadIdx.x; i < PL::TW_LEN; i += blockDim.x) tws[i] = __ldg(&a.tw[i]);
+  __syncthreads();
+  const int g = threadIdx.x / T;
+  const int lt = threadIdx.x % T;
+  float2* buf = smem + PL::TW_LEN + g * padded_len(PL::N);
+  const int bar = g + 1;                       // named barriers 1, 2 (0 is __syncthreads)
+  auto sync = [bar] { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(T) : "memory"); };
+  const int work = a.n_chan * a.s_count;
+  for (int w = blockIdx.x * PS::GROUPS + g; w < work; w += gridDim.x * PS::GROUPS) {
+    const int k = w % a.n_chan;
+    const int s = a.s_begin + w / a.n_chan;
+    ols_segment<LOGN, true, true>(a, buf, tws, lt, true, k, s, sync);
+    sync();                                    // buf is rewritten by the next segment
+  }
+}
+
 
 // ------------------------------------------------------------------ clusters
 //
@@ -468,6 +520,25 @@ cudaError_t launch_ols_t(const OlsArgs& a, cudaStream_t s) {
            : cudaFuncSetAttribute(ols_kernel<LOGN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CF::SMEM);
     if (e != cudaSuccess) return e;
     attr_set[dev][cm] = true;
+  }
+  if constexpr (LOGN == 12 || LOGN == 13) {
+    if (cm && kUsePersistent) {
+      static bool pset[128] = {};
+      if (!pset[dev]) {
+        e = cudaFuncSetAttribute(ols_persistent_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Persist<LOGN>::SMEM);
+        if (e != cudaSuccess) return e;
+        pset[dev] = true;
+      }
+      int sms = 0;
+      e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
+      const long long work = (long long)a.n_chan * a.s_count;
+      const long long need = (work + Persist<LOGN>::GROUPS - 1) / Persist<LOGN>::GROUPS;
+      const unsigned grid = (unsigned)(need < sms ? need : sms);
+      ols_persistent_kernel<LOGN><<<grid, Persist<LOGN>::THREADS, Persist<LOGN>::SMEM, s>>>(a);
+      return cudaGetLastError();
+    }
   }
   const long long work = (long long)a.n_chan * a.s_count;
   const unsigned grid = (unsigned)((work + CF::G - 1) / CF::G);

@@ -49,8 +49,16 @@ __device__ __forceinline__ float2 unpack_i8x2(uint32_t raw16) {
   return make_float2(re, im);
 }
 
-// Forward (DIF) radix pass p, in place in shared memory.
-template <int LOGN, int p>
+// A twiddle from global memory (read-only path) or from a copy in shared
+// memory; the read-only load must never see a shared-memory address.
+template <bool SH>
+__device__ __forceinline__ float2 ld_tw(const float2* p) {
+  if constexpr (SH) return *p;
+  else return __ldg(p);
+}
+
+// Forward (DIF) radix pass p, in place in shared memory; SH: tw is in shared memory.
+template <int LOGN, int p, bool SH = false>
 __device__ __forceinline__ void fwd_pass(float2* buf, const float2* __restrict__ tw, int lt) {
   using PL = PassPlan<LOGN>;
   constexpr int R = PL::R(p), S = PL::S(p), M = PL::M(p);
@@ -68,7 +76,7 @@ __device__ __forceinline__ void fwd_pass(float2* buf, const float2* __restrict__
     if constexpr (S > 1) {
       const float2* twp = tw + PL::TwOff(p) + t;
 #pragma unroll
-      for (int k = 1; k < R; ++k) v[k] = cmul(v[k], __ldg(twp + k * S));
+      for (int k = 1; k < R; ++k) v[k] = cmul(v[k], ld_tw<SH>(twp + k * S));
     }
 #pragma unroll
     for (int k = 0; k < R; ++k) pb[poff<S>(k)] = v[k];
@@ -76,7 +84,7 @@ __device__ __forceinline__ void fwd_pass(float2* buf, const float2* __restrict__
 }
 
 // Inverse (DIT) radix pass p, in place: conjugate twiddle, then butterfly.
-template <int LOGN, int p>
+template <int LOGN, int p, bool SH = false>
 __device__ __forceinline__ void inv_pass(float2* buf, const float2* __restrict__ tw, int lt) {
   using PL = PassPlan<LOGN>;
   constexpr int R = PL::R(p), S = PL::S(p), M = PL::M(p);
@@ -93,7 +101,7 @@ __device__ __forceinline__ void inv_pass(float2* buf, const float2* __restrict__
     if constexpr (S > 1) {
       const float2* twp = tw + PL::TwOff(p) + t;
 #pragma unroll
-      for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], __ldg(twp + k * S));
+      for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], ld_tw<SH>(twp + k * S));
     }
     dft<R, 1>(v);
 #pragma unroll
