@@ -34,7 +34,8 @@ sys.path.insert(0, ROOT)
 METRIC = "dedispersed Msamples/s, ×real-time, % HBM roofline; block p99 latency"
 WORKLOAD = "gsb"
 SAMPLE_CHANNELS = 192            # CPU baseline: channels of the full block (~10-20 s)
-KERNEL_SOURCES = ("paper_1509_00186_b300/csrc/cdd_kernels.cu", "paper_1509_00186_b300/csrc/cdd_fft.cuh")
+KERNEL_SOURCES = ("paper_1509_00186_b300/csrc/cdd_kernels.cu", "paper_1509_00186_b300/csrc/cdd_fft.cuh",
+                  "paper_1509_00186_b300/csrc/cdd_passes.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ols_kernel_gsb_traffic.json")
 
 
@@ -249,7 +250,7 @@ def run_gpu(args, world, rank, local):
 
     w, q = workload_info(args.channels)
     plan = Plan(w.f_center_mhz, w.bandwidth_mhz, w.n_chan, w.dm, w.n_fft, w.n_avg,
-                segments_per_block=q, pipeline_chunks=4)
+                segments_per_block=q, pipeline_chunks=4, stage_timing=True)
     hop = plan.get("hop")
     assert hop * q == plan.block_samples and q == w.n_samp // hop
     rows, n_out, C = plan.block_samples, plan.n_out, w.n_chan
@@ -263,6 +264,7 @@ def run_gpu(args, world, rank, local):
         plan.execute(vin, out)
     launches_per_step = plan.get("kernel_launches")
     torch.cuda.synchronize(dev)
+    stage0 = {k: plan.get(k) for k in ("timed_blocks", "corner_turn_ns", "ols_ns")}
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     clocks = ClockSampler(local) if rank == 0 else None
     if clocks:
@@ -277,6 +279,9 @@ def run_gpu(args, world, rank, local):
     barrier(world)
     clock_info = clocks.stop() if clocks else None
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    # per-stage device time, from the events the library records on the launching stream
+    stage = {k: plan.get(k) - v for k, v in stage0.items()}
+    assert stage["timed_blocks"] == args.steps, stage
     total_ms = ev[0].elapsed_time(ev[-1])
     total_ms_max = max_over_ranks(total_ms, world, dev)
     samples_rank = float(C) * rows * args.steps
@@ -310,7 +315,8 @@ def run_gpu(args, world, rank, local):
     # ---- roofline of the fused kernel (one launch per step)
     peaks = measured_peaks()
     n_fft = w.n_fft
-    kernel_ms = statistics.mean(step_ms)
+    kernel_ms = stage["ols_ns"] / args.steps / 1e6          # fused kernel, mean per launch
+    corner_ms = stage["corner_turn_ns"] / args.steps / 1e6
     segs = C * q
     flops = segs * (10.0 * n_fft * math.log2(n_fft) + 9.0 * n_fft)     # fwd+inv FFT, chirp, detect
     comp_bytes = C * rows * 2 + C * plan.get("n_ov") * 2 + C * n_out * 4
@@ -344,11 +350,16 @@ def run_gpu(args, world, rank, local):
                      "traffic": traffic,
                      "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x "
                                     f"{peaks['sm_max_mhz']:.0f} MHz ({peaks['_source']} max clock)",
-                     "kernel": f"ols_kernel<{int(math.log2(n_fft))}>",
+                     "kernel": (f"ols_persistent_kernel<{int(math.log2(n_fft))}>"
+                                if n_fft in (4096, 8192) else f"ols_kernel<{int(math.log2(n_fft))}>"),
+                     "kernel_ms": kernel_ms,
                      "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
                      "flops_per_launch": flops, "algorithmic_bytes_per_launch": comp_bytes},
         "e2e": {"value": e2e_value, "unit": "Msamples/s",
                 "h2d_bytes_per_step": int(hin.numel()), "d2h_bytes_per_step": int(hout.numel() * 4)},
+        "stages": {"corner_turn": {"ms": corner_ms, "gbs": 4.0 * C * rows / (corner_ms * 1e-3) / 1e9,
+                                   "hbm_frac": 4.0 * C * rows / (corner_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+                   "ols": {"ms": kernel_ms}},
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clock_info,
         "paper_gflops": flops / (kernel_ms * 1e-3) / 1e9,

@@ -86,8 +86,19 @@ enum cdd_attr {
                                       staging comes on top)                    */
   CDD_ATTR_SEQ_GAPS = 15,          /* pool streams: blocks missing from the
                                       submitted sequence numbers               */
-  CDD_ATTR_POLARISATIONS = 16      /* 1 or 2 (settable): 2 keeps a second
+  CDD_ATTR_POLARISATIONS = 16,     /* 1 or 2 (settable): 2 keeps a second
                                       stream state for cdd_execute_dual        */
+  CDD_ATTR_STAGE_TIMING = 17,      /* 0 or 1 (settable): 1 brackets the corner
+                                      turn and the fused segment kernel of
+                                      every block with CUDA events on the
+                                      launching stream                         */
+  CDD_ATTR_TIMED_BLOCKS = 18,      /* blocks timed so far (stage timing on)    */
+  CDD_ATTR_CORNER_TURN_NS = 19,    /* summed device time of the corner turns
+                                      of the timed blocks, nanoseconds         */
+  CDD_ATTR_OLS_NS = 20             /* summed device time of the fused segment
+                                      kernels of the timed blocks, ns.  Reading
+                                      18..20 waits for the timed blocks still
+                                      in flight; the sums never reset.         */
 };
 
 enum cdd_taper { CDD_TAPER_NONE = 0, CDD_TAPER_HANN = 1, CDD_TAPER_WELCH = 2 };

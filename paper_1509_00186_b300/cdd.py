@@ -29,7 +29,8 @@ ATTR = {
     "n_fft": 0, "n_ov": 1, "hop": 2, "n_avg": 3, "n_chan": 4, "segments_per_block": 5,
     "block_samples": 6, "n_out_per_block": 7, "r_max": 8, "bytes_device": 9, "taper": 10,
     "blocks_done": 11, "pipeline_chunks": 12, "kernel_launches": 13, "bytes_needed": 14,
-    "seq_gaps": 15, "polarisations": 16,
+    "seq_gaps": 15, "polarisations": 16, "stage_timing": 17, "timed_blocks": 18,
+    "corner_turn_ns": 19, "ols_ns": 20,
 }
 POOL_ATTR = {"budget": 100, "used_bytes": 101, "streams": 102}
 TAPER = {"none": 0, "hann": 1, "welch": 2}
@@ -362,11 +363,14 @@ class Plan:
     """Owning wrapper of one plan; tensors in, tensors out (no computation here)."""
 
     def __init__(self, f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft=0, n_avg=1,
-                 segments_per_block=1, taper="none", pipeline_chunks=None, polarisations=1):
+                 segments_per_block=1, taper="none", pipeline_chunks=None, polarisations=1,
+                 stage_timing=False):
         self.handle = cdd_plan_create(f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft, n_avg)
         try:
             cdd_plan_set(self.handle, "segments_per_block", segments_per_block)
             cdd_plan_set(self.handle, "taper", TAPER[taper])
+            if stage_timing:
+                cdd_plan_set(self.handle, "stage_timing", 1)
             if polarisations != 1:
                 cdd_plan_set(self.handle, "polarisations", polarisations)
             if pipeline_chunks is not None:

@@ -19,6 +19,8 @@ constexpr int kMaxLogN = 16;
 
 }  // namespace
 
+constexpr int kTimingSlots = 256;   // stage-timing event triples per plan
+
 struct cdd_plan_s {
   // observation and geometry (fixed at create)
   double f_center = 0, bandwidth = 0, dm = 0, chan_bw = 0, f_lo0 = 0, n_disp = 0;
@@ -65,6 +67,12 @@ struct cdd_plan_s {
   cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
               ev_out[2] = {nullptr, nullptr};
   bool host_ready = false;
+  // stage timing (CDD_ATTR_STAGE_TIMING): kTimingSlots triples of events
+  // {before corner turn, between, after fused kernel}, reused round robin
+  bool timing = false;
+  std::vector<cudaEvent_t> t_ev;
+  std::vector<char> t_pending;
+  int64_t t_next = 0, t_blocks = 0, t_ct_ns = 0, t_ols_ns = 0;
 };
 
 namespace cdd {
@@ -211,6 +219,8 @@ void free_device(cdd_plan p) {
     if (p->ev_out[i]) cudaEventDestroy(p->ev_out[i]);
   }
   if (p->ev_start) cudaEventDestroy(p->ev_start);
+  for (cudaEvent_t e : p->t_ev)
+    if (e) cudaEventDestroy(e);
   if (p->st_h2d) cudaStreamDestroy(p->st_h2d);
   if (p->st_comp) cudaStreamDestroy(p->st_comp);
   if (p->st_d2h) cudaStreamDestroy(p->st_d2h);
@@ -274,6 +284,11 @@ int commit_once(cdd_plan p) {
     if ((rc = dalloc(p, &p->d_ring_b, (size_t)p->n_chan * p->ring_len * sizeof(float)))) return rc;
     if ((rc = dalloc(p, &p->d_pol_tmp, (size_t)p->n_chan * n_out_per_block(p) * sizeof(float)))) return rc;
   }
+  if (p->timing) {
+    p->t_ev.assign(3 * kTimingSlots, nullptr);
+    p->t_pending.assign(kTimingSlots, 0);
+    for (cudaEvent_t& e : p->t_ev) CDD_TRY(p, cudaEventCreate(&e));
+  }
   std::vector<int> sh(p->shift.begin(), p->shift.end());
   CDD_TRY(p, cudaMemcpy(p->d_shift, sh.data(), sh.size() * sizeof(int), cudaMemcpyHostToDevice));
   cudaStream_t s;
@@ -307,6 +322,29 @@ int check_device(cdd_plan p) {
   return dev == p->device ? CDD_OK : CDD_EINVAL;
 }
 
+// Fold a finished timing slot into the sums (waits for its last event).
+int harvest_slot(cdd_plan p, int slot) {
+  cudaEvent_t* e = &p->t_ev[3 * slot];
+  CDD_TRY(p, cudaEventSynchronize(e[2]));
+  float ct = 0.f, ols = 0.f;
+  CDD_TRY(p, cudaEventElapsedTime(&ct, e[0], e[1]));
+  CDD_TRY(p, cudaEventElapsedTime(&ols, e[1], e[2]));
+  p->t_ct_ns += llround((double)ct * 1e6);
+  p->t_ols_ns += llround((double)ols * 1e6);
+  p->t_blocks += 1;
+  p->t_pending[slot] = 0;
+  return CDD_OK;
+}
+
+int harvest_all(cdd_plan p) {
+  for (int i = 0; i < (int)p->t_pending.size(); ++i)
+    if (p->t_pending[i]) {
+      const int rc = harvest_slot(p, i);
+      if (rc) return rc;
+    }
+  return CDD_OK;
+}
+
 // One block of q segments on `s` for polarisation `pol`; advances its stream position.
 int run_block(cdd_plan p, const int8_t* d_in, float* d_out, float* d_volt, int q, cudaStream_t s,
               int pol = 0) {
@@ -333,10 +371,23 @@ int run_block(cdd_plan p, const int8_t* d_in, float* d_out, float* d_volt, int q
   a.n_out = (int)((int64_t)q * p->hop / p->n_avg);
   a.g0 = g_next;
   a.ring_len = p->ring_len;
+  cudaEvent_t* te = nullptr;
+  if (p->timing) {
+    const int slot = (int)(p->t_next++ % kTimingSlots);
+    if (p->t_pending[slot]) {
+      const int rc = harvest_slot(p, slot);
+      if (rc) return rc;
+    }
+    te = &p->t_ev[3 * slot];
+    p->t_pending[slot] = 1;
+    CDD_TRY(p, cudaEventRecord(te[0], s));
+  }
   CDD_TRY(p, cdd::launch_corner_turn(a.in, p->d_in_cm, 0, a.rows, a.rows, p->n_chan, s));
+  if (te) CDD_TRY(p, cudaEventRecord(te[1], s));
   a.s_begin = 0;
   a.s_count = q;
   CDD_TRY(p, cdd::launch_ols(p->logn, a, s));
+  if (te) CDD_TRY(p, cudaEventRecord(te[2], s));
   const int launches = 2;
   p->last_launches = launches;
   g_next += a.n_out;
@@ -439,6 +490,10 @@ int cdd_plan_set(cdd_plan p, int attr, int64_t value) {
       if (value != 1 && value != 2) return CDD_EINVAL;
       p->pols = (int)value;
       return CDD_OK;
+    case CDD_ATTR_STAGE_TIMING:
+      if (value != 0 && value != 1) return CDD_EINVAL;
+      p->timing = value == 1;
+      return CDD_OK;
     default:
       return CDD_EINVAL;
   }
@@ -463,6 +518,19 @@ int cdd_plan_get(cdd_plan p, int attr, int64_t* v) {
     case CDD_ATTR_KERNEL_LAUNCHES: *v = p->last_launches; break;
     case CDD_ATTR_BYTES_NEEDED: *v = bytes_needed(p); break;
     case CDD_ATTR_POLARISATIONS: *v = p->pols; break;
+    case CDD_ATTR_STAGE_TIMING: *v = p->timing ? 1 : 0; break;
+    case CDD_ATTR_TIMED_BLOCKS:
+    case CDD_ATTR_CORNER_TURN_NS:
+    case CDD_ATTR_OLS_NS: {
+      if (p->timing && p->committed) {
+        if (p->sticky) return p->sticky;
+        const int rc = harvest_all(p);
+        if (rc) return rc;
+      }
+      *v = attr == CDD_ATTR_TIMED_BLOCKS ? p->t_blocks
+         : attr == CDD_ATTR_CORNER_TURN_NS ? p->t_ct_ns : p->t_ols_ns;
+      break;
+    }
     default: return CDD_EINVAL;
   }
   return CDD_OK;

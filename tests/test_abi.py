@@ -123,6 +123,22 @@ def test_setters(cdd):
     cdd.cdd_destroy(0)     # NULL is accepted
 
 
+def test_stage_timing_attributes_before_commit(cdd):
+    p = cdd.cdd_plan_create(325.0, 32.0, 512, 50.0, 8192, 16)
+    try:
+        assert cdd.cdd_plan_get(p, "stage_timing") == 0
+        with pytest.raises(cdd.CddError):
+            cdd.cdd_plan_set(p, "stage_timing", 2)
+        cdd.cdd_plan_set(p, "stage_timing", 1)
+        assert cdd.cdd_plan_get(p, "stage_timing") == 1
+        for a in ("timed_blocks", "corner_turn_ns", "ols_ns"):      # nothing timed yet, no GPU call
+            assert cdd.cdd_plan_get(p, a) == 0
+        with pytest.raises(cdd.CddError):                           # read-only
+            cdd.cdd_plan_set(p, "ols_ns", 5)
+    finally:
+        cdd.cdd_destroy(p)
+
+
 def test_static_entry_rejects_before_touching_the_gpu(cdd):
     """cdd_execute_static checks geometry and its fixed scratch size first."""
     with pytest.raises(cdd.CddError) as ei:       # 2048 x 16384 chirp table = 256 MiB

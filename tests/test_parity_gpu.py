@@ -116,6 +116,27 @@ def test_host_buffer_path_equals_device_path(tiny):
     assert O.rel_rms(host, out_o) <= TOL
 
 
+def test_stage_timing_changes_no_bits(tiny):
+    """Events around the two stages are recorded on the launching stream; the
+    output is the same bits with and without them, and every block is timed."""
+    import torch
+    from paper_1509_00186_b300.cdd import Plan
+    vin, args, geo, q, _, _ = tiny
+    plain, _ = gpu_run(vin, args, 100, 3, volt=False)
+    plan = Plan(*args, segments_per_block=100, stage_timing=True)
+    try:
+        bs = plan.block_samples
+        x = torch.from_numpy(np.ascontiguousarray(vin[: 3 * bs])).cuda()
+        outs = [plan.execute(x[b * bs:(b + 1) * bs]) for b in range(3)]
+        timed = torch.cat(outs, 1).cpu().numpy()
+        assert plan.get("timed_blocks") == 3
+        ct, ols = plan.get("corner_turn_ns"), plan.get("ols_ns")
+        assert 0 < ct < 1e9 and 0 < ols < 1e9
+    finally:
+        plan.close()
+    assert np.array_equal(timed, plain)
+
+
 @pytest.mark.parametrize("logn", list(range(6, 17)))
 def test_every_fft_length(cuda_device, logn):
     """Each supported N on a ragged channel count (the last CTA is partly idle
