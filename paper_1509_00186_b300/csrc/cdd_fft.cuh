@@ -73,6 +73,55 @@ __device__ __forceinline__ float2 rot(float2 b) {
   }
 }
 
+// The same angles in double, for compile-time constants derived from them.
+__host__ __device__ constexpr double cos32d(int k) {
+  constexpr double c[9] = {1.0,
+                           0.98078528040323044913,
+                           0.92387953251128675613,
+                           0.83146961230254523708,
+                           0.70710678118654752440,
+                           0.55557023301960222474,
+                           0.38268343236508977173,
+                           0.19509032201612826785,
+                           0.0};
+  int m = ((k % 32) + 32) % 32;
+  return m <= 8 ? c[m] : m <= 16 ? -c[16 - m] : m <= 24 ? -c[m - 16] : c[32 - m];
+}
+
+// Radix-2 butterfly (a, b) -> (a + w b, a - w b), w = exp(DIR * 2*pi*i * J / LEN).
+// For a non-trivial w = c + i s the product is factored through the larger of
+// |c| and |s|: w b = c (b + i (s/c) b) or w b = s ((c/s) b + i b), so that the
+// butterfly is two fused multiply-adds for the inner factor and four for
+// a +- c u (six instructions instead of four for the product and four adds).
+// The ratio is at most 1 in magnitude, so no intermediate grows.
+template <int LEN, int DIR, int J>
+__device__ __forceinline__ void bfly(float2& a, float2& b) {
+  constexpr int m = J * (32 / LEN);       // angle in units of 2*pi/32
+  if constexpr (m == 0 || m == 8) {
+    const float2 w = rot<LEN, DIR, J>(b);
+    b = csub(a, w);
+    a = cadd(a, w);
+  } else {
+    constexpr double cd = cos32d(m);
+    constexpr double sd = DIR > 0 ? cos32d(m - 8) : -cos32d(m - 8);
+    constexpr bool by_c = (cd < 0 ? -cd : cd) >= (sd < 0 ? -sd : sd);
+    // b' = b * (w / f): by_c: f = c, b' = (b.x - r b.y, b.y + r b.x), r = s/c;
+    //                   else: f = s, b' = (r b.x - b.y, b.x + r b.y), r = c/s.
+    constexpr float f = (float)(by_c ? cd : sd);
+    constexpr float r = (float)(by_c ? sd / cd : cd / sd);
+    float ux, uy;
+    if constexpr (by_c) {
+      ux = fmaf(-r, b.y, b.x);
+      uy = fmaf(r, b.x, b.y);
+    } else {
+      ux = fmaf(r, b.x, -b.y);
+      uy = fmaf(r, b.y, b.x);
+    }
+    b = make_float2(fmaf(-f, ux, a.x), fmaf(-f, uy, a.y));
+    a = make_float2(fmaf(f, ux, a.x), fmaf(f, uy, a.y));
+  }
+}
+
 template <int R>
 __host__ __device__ constexpr int bitrev(int i) {
   int r = 0;
@@ -99,10 +148,7 @@ __device__ __forceinline__ void dft(float2 (&v)[R]) {
       static_for<0, len / 2>([&](auto J) {
         constexpr int i = decltype(G)::value * len;
         constexpr int j = decltype(J)::value;
-        const float2 a = t[i + j];
-        const float2 b = rot<len, DIR, j>(t[i + j + len / 2]);
-        t[i + j] = cadd(a, b);
-        t[i + j + len / 2] = csub(a, b);
+        bfly<len, DIR, j>(t[i + j], t[i + j + len / 2]);
       });
     });
   });
