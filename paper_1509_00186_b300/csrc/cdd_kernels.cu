@@ -43,8 +43,69 @@ constexpr bool kUsePersistent = CDD_PERSISTENT != 0;
 // unpack and gather, forward passes, chirp, inverse passes, detection,
 // integration and the aligned store.  `tw` is the whole twiddle table, in
 // global memory or (SH) staged in shared memory; `sync` is the group's barrier.
+// Window sums over groups of NA neighbouring lanes by recursive halving: at
+// each step a lane keeps one half of its V values, adds its partner's copy of
+// that half and sends the other half.  Afterwards lane l holds, in u[i]
+// (i < R0/NA), the sum over its lane group of the values it started with at
+// index j = (R0/NA) * (l mod NA) + i.
+template <int R0, int NA, int V = R0>
+__device__ __forceinline__ void lane_window_sums(float (&u)[R0], int lane) {
+  if constexpr (NA > 1) {
+    constexpr int o = NA / 2, H = V / 2;
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      const float keep = hi ? u[i + H] : u[i];
+      const float send = hi ? u[i] : u[i + H];
+      u[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+    lane_window_sums<R0, NA / 2, H>(u, lane);
+  }
+}
+
+// Detect and integrate the R0 samples n = lt + T*j (j < R0) a thread holds
+// after the last inverse pass: windows of NA samples are NA neighbouring lanes
+// (T is a multiple of 32 and windows start at multiples of NA), so a window's
+// sum is formed in registers.  emit(m, sum) receives output m of the segment,
+// the window starting at n_ov + m*NA.
+template <int R0, int T, int NA, class Emit>
+__device__ __forceinline__ void lane_windows(const float2 (&v)[R0], int lt, int n_ov, Emit& emit) {
+  static_assert(T % 32 == 0 && NA <= 32 && NA <= R0, "window must be lanes of one warp");
+  float u[R0];
+#pragma unroll
+  for (int j = 0; j < R0; ++j) u[j] = fmaf(v[j].x, v[j].x, v[j].y * v[j].y);
+  const int lane = lt & 31;
+  lane_window_sums<R0, NA>(u, lane);
+  constexpr int V = R0 / NA;
+  const int first = lt - (lane & (NA - 1));      // first lane's sample of the window
+#pragma unroll
+  for (int i = 0; i < V; ++i) {
+    const int j = V * (lane & (NA - 1)) + i;
+    const int n0 = first + T * j;
+    if (n0 >= n_ov) emit((n0 - n_ov) / NA, u[i]);
+  }
+}
+
+template <int R0, int T, class Emit>
+__device__ __forceinline__ void integrate_in_lanes(const float2 (&v)[R0], int lt, int n_ov, int na,
+                                                   Emit& emit) {
+  switch (na) {
+    case 1: lane_windows<R0, T, 1>(v, lt, n_ov, emit); break;
+    case 2: lane_windows<R0, T, 2>(v, lt, n_ov, emit); break;
+    case 4: lane_windows<R0, T, 4>(v, lt, n_ov, emit); break;
+    case 8: lane_windows<R0, T, 8>(v, lt, n_ov, emit); break;
+    case 16:
+      if constexpr (R0 >= 16) lane_windows<R0, T, 16>(v, lt, n_ov, emit);
+      break;
+    case 32:
+      if constexpr (R0 >= 32) lane_windows<R0, T, 32>(v, lt, n_ov, emit);
+      break;
+    default: break;
+  }
+}
+
 template <int LOGN, bool CM, bool SH, class Sync>
-__device__ __forceinline__ void ols_segment(const OlsArgs& a, float2* buf, const float2* tw, int lt,
+__device__ __forceinline__ bool ols_segment(const OlsArgs& a, float2* buf, const float2* tw, int lt,
                                             bool active, int k, int s, Sync sync) {
   using PL = PassPlan<LOGN>;
   constexpr int N = PL::N;
@@ -90,13 +151,25 @@ __device__ __forceinline__ void ols_segment(const OlsArgs& a, float2* buf, const
   }
   sync();
 
+  // When the last two radices are equal, the last forward pass before the
+  // chirp pass, the chirp pass and the first inverse pass after it touch each
+  // sub-problem of R_{P-2} * R_{P-1} points with the same R_{P-1} consecutive
+  // threads (a part of one warp), so those hand-offs need only a warp barrier.
+  constexpr bool kWarpMid = PL::P >= 3 && PL::R(PL::P - 2) == PL::RL && PL::RL <= 32;
+  auto mid_sync = [&] {
+    if constexpr (kWarpMid) __syncwarp();
+    else sync();
+  };
   static_for<1, PL::P - 1>([&](auto P_) {
-    if (active) fwd_pass<LOGN, decltype(P_)::value, SH>(buf, tw, lt);
-    sync();
+    constexpr int p = decltype(P_)::value;
+    if (active) fwd_pass<LOGN, p, SH>(buf, tw, lt);
+    if constexpr (p == PL::P - 2) mid_sync();
+    else sync();
   });
 
   if (active) chirp_pass<LOGN>(buf, a.chirp + (size_t)k * N, lt);
-  sync();
+  if constexpr (PL::P >= 3) mid_sync();
+  else sync();
 
   static_for<1, PL::P - 1>([&](auto I_) {
     if (active) inv_pass<LOGN, PL::P - 1 - decltype(I_)::value, SH>(buf, tw, lt);
@@ -120,30 +193,47 @@ __device__ __forceinline__ void ols_segment(const OlsArgs& a, float2* buf, const
     }
   }
   sync();                       // every thread has read buf: reuse it
+  // Integration in registers when each window is n_avg neighbouring lanes of
+  // one warp (n_avg a power of two, at most 32 and at most R0); otherwise the
+  // detected samples go through shared memory.  N = 16384 (one 512-thread CTA
+  // per SM, 128 registers) keeps the shared-memory form: the register form
+  // spills there and measured slower.
+  const int na = a.n_avg;
+  bool in_lanes = false;
+  if constexpr (T % 32 == 0 && LOGN <= 13) in_lanes = na <= R0 && na <= 32 && (na & (na - 1)) == 0;
   float* pw = reinterpret_cast<float*>(buf);
-  if (active) {
+  if (!in_lanes) {
+    if (active) {
 #pragma unroll
-    for (int j = 0; j < R0; ++j) {
-      const int n = lt + T * j;
-      pw[n + (n >> 5)] = fmaf(v[j].x, v[j].x, v[j].y * v[j].y);   // one spare word per 32
+      for (int j = 0; j < R0; ++j) {
+        const int n = lt + T * j;
+        pw[n + (n >> 5)] = fmaf(v[j].x, v[j].x, v[j].y * v[j].y);   // one spare word per 32
+      }
     }
+    sync();
   }
-  sync();
 
   if (active) {
-    const int n_int = a.hop / a.n_avg;
+    const int n_int = a.hop / na;
     const int r = __ldg(&a.shift[k]);
     const long long gseg = a.g0 + (long long)s * n_int;
     float* outk = a.out + (size_t)k * a.n_out;
     float* ringk = a.ring + (size_t)k * a.ring_len;
-    for (int m = lt; m < n_int; m += T) {
-      const int n0 = a.n_ov + m * a.n_avg;
-      float acc = 0.f;
-      for (int i = 0; i < a.n_avg; ++i) acc += pw[(n0 + i) + ((n0 + i) >> 5)];
+    auto emit = [&](int m, float acc) {
       const long long gi = gseg + m;              // stream index of this output
       const long long dst = gi + r - a.g0;        // its aligned index in this block
       if (dst < a.n_out) outk[dst] = acc;
       else ringk[gi % a.ring_len] = acc;
+    };
+    if (in_lanes) {
+      if constexpr (T % 32 == 0 && LOGN <= 13) integrate_in_lanes<R0, T>(v, lt, a.n_ov, na, emit);
+    } else {
+      for (int m = lt; m < n_int; m += T) {
+        const int n0 = a.n_ov + m * na;
+        float acc = 0.f;
+        for (int i = 0; i < na; ++i) acc += pw[(n0 + i) + ((n0 + i) >> 5)];
+        emit(m, acc);
+      }
     }
     if (s == 0) {                                 // block prefix: earlier blocks' samples
       const int lim = r < a.n_out ? r : a.n_out;
@@ -153,6 +243,7 @@ __device__ __forceinline__ void ols_segment(const OlsArgs& a, float2* buf, const
       }
     }
   }
+  return !in_lanes;               // buf (the power samples) read since the last barrier
 }
 
 template <int LOGN, bool CM>
@@ -185,6 +276,33 @@ struct Persist {
   static constexpr size_t SMEM = (size_t(PL::TW_LEN) + size_t(GROUPS) * padded_len(PL::N)) * sizeof(float2);
 };
 
+#ifndef CDD_PREFETCH
+#define CDD_PREFETCH 1
+#endif
+
+// Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Ask L2 for the channel-major input rows and the chirp row of work item w,
+// restricted to the 16-byte blocks that lie wholly inside the rows the
+// segment reads (so every prefetched byte is one the kernel will load).
+template <int LOGN>
+__device__ __forceinline__ void prefetch_work(const OlsArgs& a, int w) {
+  constexpr int N = 1 << LOGN;
+  const int k = w % a.n_chan;
+  const long long s = a.s_begin + w / a.n_chan;
+  long long r0 = s * a.hop - a.n_ov;
+  const long long r1 = r0 + N;                  // <= (s + 1) * hop <= rows
+  if (r0 < 0) r0 = 0;
+  const char* row = reinterpret_cast<const char*>(a.in_cm + (long long)k * a.rows);
+  const uintptr_t lo = (reinterpret_cast<uintptr_t>(row + 2 * r0) + 15) & ~uintptr_t(15);
+  const uintptr_t hi = reinterpret_cast<uintptr_t>(row + 2 * r1) & ~uintptr_t(15);
+  if (hi > lo) prefetch_l2(reinterpret_cast<const void*>(lo), (uint32_t)(hi - lo));
+  prefetch_l2(a.chirp + (size_t)k * N, (uint32_t)(N * sizeof(float2)));
+}
+
 template <int LOGN>
 __global__ void __launch_bounds__(Persist<LOGN>::THREADS, 1)
 ols_persistent_kernel(const OlsArgs a) {
@@ -201,11 +319,13 @@ ols_persistent_kernel(const OlsArgs a) {
   const int bar = g + 1;                       // named barriers 1, 2 (0 is __syncthreads)
   auto sync = [bar] { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(T) : "memory"); };
   const int work = a.n_chan * a.s_count;
-  for (int w = blockIdx.x * PS::GROUPS + g; w < work; w += gridDim.x * PS::GROUPS) {
+  const int stride = gridDim.x * PS::GROUPS;
+  for (int w = blockIdx.x * PS::GROUPS + g; w < work; w += stride) {
+    if (CDD_PREFETCH && lt == 0 && w + stride < work) prefetch_work<LOGN>(a, w + stride);
     const int k = w % a.n_chan;
     const int s = a.s_begin + w / a.n_chan;
-    ols_segment<LOGN, true, true>(a, buf, tws, lt, true, k, s, sync);
-    sync();                                    // buf is rewritten by the next segment
+    if (ols_segment<LOGN, true, true>(a, buf, tws, lt, true, k, s, sync))
+      sync();                                  // buf is rewritten by the next segment
   }
 }
 
