@@ -1,6 +1,7 @@
 """Throughput benchmark of the coherent-dedispersion path on one or more GPUs.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cdd|reference]
+    python bench.py --path lsb_hann|dual|precision|band_sum|batch|fullband|serving
 
 A step dedisperses one block of the 32 MHz / 512-channel / DM 50 / N 8192 / x16
 workload (GMRT GSB real-time shape): 76 overlap-save segments per channel, i.e.
@@ -375,6 +376,300 @@ def run_gpu(args, world, rank, local):
     return 0
 
 
+# ---------------------------------------------------------------- other rows
+#
+# `--path P` measures one more row of the path on one GPU and prints its own
+# JSON line (rank 0; other ranks exit).  Each line carries the roofline of its
+# dominant kernel or of the whole step (said in "roofline.kernel") and the FP64
+# oracle timed on a bounded sample of the same workload.
+
+def _timed(fn, steps, warmup, dev):
+    """W warm-up calls, then K calls bracketed by CUDA events on the current
+    stream, with nvidia-smi clock samples during the timed region."""
+    import torch
+    for _ in range(max(warmup, 3)):
+        fn()
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    clocks = ClockSampler(dev.index or 0)
+    time.sleep(0.3)
+    torch.cuda.synchronize(dev)
+    ev[0].record(stream)
+    for i in range(steps):
+        fn()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    clock_info = clocks.stop()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    return ev[0].elapsed_time(ev[-1]), step_ms, clock_info
+
+
+def _fp32_peak(dev, peaks):
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12, \
+        f"{sms} SMs x 128 FP32 lanes x 2 flop x {peaks['sm_max_mhz']:.0f} MHz ({peaks['_source']} max clock)"
+
+
+def _cpu_time(fn):
+    t0 = time.perf_counter()
+    fn()
+    return time.perf_counter() - t0
+
+
+def _line(path, args, metric, value, unit, ms, steps_ms, config, roofline, cpu, clocks, launches,
+          dtype="f32", higher=True, **extra):
+    line = {"path": path, "metric": metric, "value": value, "unit": unit, "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": higher, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic: seeded complex int8 N(0,20) noise", "config": config,
+            "latency_ms": {"p50": statistics.median(steps_ms),
+                           "p99": float(sorted(steps_ms)[min(len(steps_ms) - 1, int(0.99 * len(steps_ms)))])},
+            "roofline": roofline, "gpu_launches": launches, "clocks": clocks}
+    line.update(extra)
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    return line
+
+
+def _alu_roofline(kernel, flops, kernel_ms, dev, peaks):
+    peak, src = _fp32_peak(dev, peaks)
+    ach = flops / (kernel_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None, "peak_source": src, "kernel": kernel, "kernel_ms": kernel_ms,
+            "flops_per_launch": flops}
+
+
+def _hbm_roofline(kernel, nbytes, kernel_ms, peaks):
+    ach = nbytes / (kernel_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": None,
+            "peak_source": f"hbm_gbs ({peaks['_source']})", "kernel": kernel, "kernel_ms": kernel_ms,
+            "algorithmic_bytes_per_launch": nbytes}
+
+
+def _ols_flops(n_fft, segments):
+    return segments * (10.0 * n_fft * math.log2(n_fft) + 9.0 * n_fft)
+
+
+def row_plan_variant(args, dev, peaks, path):
+    """lsb_hann: the GSB block as a lower-sideband band with the Hann taper.
+    dual: the GSB block for two polarisations summed after detection.
+    precision: 150 MHz / DM 100 / N 65536 (a cluster of four CTAs per segment)."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from synth import WORKLOADS, complex_int8_voltages
+    from paper_1509_00186_b300.cdd import Plan
+    w = WORKLOADS["precision" if path == "precision" else "gsb"]
+    bw = -w.bandwidth_mhz if path == "lsb_hann" else w.bandwidth_mhz
+    taper = "hann" if path == "lsb_hann" else "none"
+    geo = O.plan_geometry(w.f_center_mhz, bw, w.n_chan, w.dm, w.n_fft, w.n_avg)
+    q = w.n_samp // geo.hop
+    pols = 2 if path == "dual" else 1
+    plan = Plan(w.f_center_mhz, bw, w.n_chan, w.dm, w.n_fft, w.n_avg, segments_per_block=q,
+                taper=taper, polarisations=pols, stage_timing=True)
+    rows, C, n_out = plan.block_samples, w.n_chan, plan.n_out
+    va = complex_int8_voltages(w.seed, rows, C, w.sigma)
+    vb = complex_int8_voltages(w.seed + 100, rows, C, w.sigma) if pols == 2 else None
+    xa = torch.from_numpy(va).to(dev)
+    xb = torch.from_numpy(vb).to(dev) if pols == 2 else None
+    out = torch.empty((C, n_out), dtype=torch.float32, device=dev)
+    fn = (lambda: plan.execute_dual(xa, xb, out)) if pols == 2 else (lambda: plan.execute(xa, out))
+    for _ in range(max(args.warmup, 3)):
+        fn()
+    torch.cuda.synchronize(dev)
+    st0 = {k: plan.get(k) for k in ("timed_blocks", "ols_ns", "corner_turn_ns")}
+    total, steps_ms, clocks = _timed(fn, args.steps, 0, dev)
+    st = {k: plan.get(k) - v for k, v in st0.items()}
+    launches = plan.get("kernel_launches")
+    plan.close()
+    kernel_ms = st["ols_ns"] / st["timed_blocks"] / 1e6
+    samples = float(C) * rows * pols
+    value = samples * args.steps / (total * 1e-3) / 1e6
+    logn = int(math.log2(geo.n_fft))
+    kname = {"precision": "ols_cluster_kernel<14,4>"}.get(path, f"ols_persistent_kernel<{logn}>")
+    roof = _alu_roofline(kname, _ols_flops(geo.n_fft, C * q), kernel_ms, dev, peaks)
+    roof["corner_turn_ms"] = st["corner_turn_ns"] / st["timed_blocks"] / 1e6
+    cpu = None
+    if not args.no_cpu_baseline:
+        n_cpu = {"precision": 16, "dual": 48}.get(path, 96)
+        dt = _cpu_time(lambda: [O.dedisperse(v, geo, taper, channels=range(n_cpu))
+                                for v in ((va, vb) if pols == 2 else (va,))])
+        cpu = {"value": n_cpu * q * geo.hop * pols / dt / 1e6, "unit": "Msamples/s", "cores": 1,
+               "kind": "oracle", "seconds": dt,
+               "sample": f"{n_cpu} of {C} channels x {q * geo.hop} samples x {pols} polarisation(s)"}
+    wl = f"{w.f_center_mhz:g}MHz-{abs(bw):g}MHz-{'LSB' if bw < 0 else 'USB'}-{C}ch-DM{w.dm:g}-N{geo.n_fft}-x{w.n_avg}"
+    config = {"workload": f"{path}:{wl}", "taper": taper, "polarisations": pols,
+              "segments_per_block": q, "block_samples_per_channel": rows}
+    rt = C * w.chan_bw_mhz * 1e6 * pols
+    return _line(path, args, "dedispersed Msamples/s", value, "Msamples/s", total / args.steps,
+                 steps_ms, config, roof, cpu, clocks, launches * args.steps,
+                 x_realtime=value * 1e6 / rt)
+
+
+def row_band_sum(args, dev, peaks):
+    """Band sum of aligned intensities [planes][C][n_out] -> [planes][n_out] on
+    the batched form's output shape: 64 DM-trial planes of 2048 channels x
+    23808 outputs (12.5 GB, far larger than L2), giving the DM-trial time
+    series.  HBM bound."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from paper_1509_00186_b300.cdd import band_sum
+    planes, C, n_out = 64, 2048, 23808
+    g = torch.Generator(device=dev)
+    g.manual_seed(11)
+    out = torch.rand((planes, C, n_out), dtype=torch.float32, device=dev, generator=g)
+    res = torch.empty((planes, n_out), dtype=torch.float32, device=dev)
+    from paper_1509_00186_b300 import cdd as _c
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    fn = lambda: _c.cdd_band_sum(out.data_ptr(), planes, C, n_out, res.data_ptr(), stream)
+    total, steps_ms, clocks = _timed(fn, args.steps, args.warmup, dev)
+    ms = total / args.steps
+    nbytes = planes * C * n_out * 4 + planes * n_out * 4
+    value = planes * C * n_out / (ms * 1e-3) / 1e6
+    roof = _hbm_roofline("band_sum_kernel<4>", nbytes, ms, peaks)
+    cpu = None
+    if not args.no_cpu_baseline:
+        host = out[0].cpu().numpy()
+        dt = _cpu_time(lambda: O.band_sum(host))
+        cpu = {"value": host.size / dt / 1e6, "unit": "Mintensities/s", "cores": 1, "kind": "oracle",
+               "seconds": dt, "sample": f"one plane ({C} x {n_out}) of the {planes}, numpy"}
+    # the library's band sum against a float64 sum of the same plane
+    check = float(np.abs(res[0].cpu().numpy() - out[0].double().sum(0).cpu().numpy()).max()
+                  / out[0].double().sum(0).abs().max().item())
+    config = {"workload": f"band_sum:{planes}x{C}x{n_out}-float32 (DM-trial planes)",
+              "bytes_in": planes * C * n_out * 4, "l2": "input 12.5 GB, larger than L2"}
+    return _line("band_sum", args, "band-summed intensities per second", value, "Mintensities/s", ms,
+                 steps_ms, config, roof, cpu, clocks, args.steps, max_rel_err_plane0=check)
+
+
+def row_batch(args, dev, peaks):
+    """Batched form: 650 MHz / 200 MHz / 2048 channels / 64 DM trials 20.0..51.5,
+    tiers N = 16384, 8192, 4096, 2048 (lowest frequencies first), x16, a block
+    of 24 longest hops (3.9 s)."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from synth import complex_int8_voltages
+    from paper_1509_00186_b300.cdd import Batch
+    dms = [20.0 + 0.5 * i for i in range(64)]
+    tiers = (16384, 8192, 4096, 2048)
+    C, n_avg = 2048, 16
+    b = Batch(650.0, 200.0, C, dms, tiers, n_avg, segments_per_block=24)
+    bs, n_out = b.block_samples, b.n_out
+    vin = complex_int8_voltages(4, bs, C, 20.0)
+    x = torch.from_numpy(vin).to(dev)
+    out = torch.empty((len(dms), C, n_out), dtype=torch.float32, device=dev)
+    total, steps_ms, clocks = _timed(lambda: b.execute(x, out), args.steps, args.warmup, dev)
+    launches = b.get("kernel_launches")
+    flops = 0.0
+    for t in range(len(tiers)):
+        n, nov, _, ct = b.tier(t)
+        segs = ct * (bs // (n - nov))
+        flops += segs * (5.0 * n * math.log2(n) + len(dms) * (5.0 * n * math.log2(n) + 9.0 * n))
+    b.close()
+    ms = total / args.steps
+    value = C * bs / (ms * 1e-3) / 1e6
+    roof = _alu_roofline("whole step (forward spectra + per-DM chirp/inverse/detect/integrate)",
+                         flops, ms, dev, peaks)
+    roof["output_bytes_per_step"] = out.numel() * 4
+    cpu = None
+    if not args.no_cpu_baseline:
+        geo = O.batch_geometry(650.0, 200.0, C, dms, tiers, n_avg)
+        chans = [0, 512, 1024, 1536]
+        dt = _cpu_time(lambda: O.dedisperse_batch(vin, geo, channels=chans))
+        cpu = {"value": len(chans) * bs / dt / 1e6, "unit": "Msamples/s", "cores": 1, "kind": "oracle",
+               "seconds": dt, "sample": f"channels {chans} (one per tier) x {bs} samples x {len(dms)} DMs"}
+    config = {"workload": f"batch:650MHz-200MHz-{C}ch-{len(dms)}DM-N16384/8192/4096/2048-x{n_avg}",
+              "block_samples_per_channel": bs, "dm_trials": len(dms)}
+    return _line("batch", args, "input Msamples/s through all DM trials", value, "Msamples/s", ms,
+                 steps_ms, config, roof, cpu, clocks, launches * args.steps,
+                 x_realtime=value * 1e6 / (200.0e6))
+
+
+def row_fullband(args, dev, peaks):
+    """Full-band mode (the paper's design): 325 MHz / 32 MHz / 512-channel
+    frames / DM 50: N = 2^26 real points over the whole band, one segment per
+    block (h real samples, 0.65 s)."""
+    import numpy as np
+    import torch
+    import oracle as O
+    from synth import complex_int8_voltages
+    from paper_1509_00186_b300.cdd import Fullband
+    a = (325.0, 32.0, 512, 50.0, 0, 16)
+    f = Fullband(*a, segments_per_block=1)
+    n, nov, h = f.get("n_fft"), f.get("n_ov"), f.get("hop")
+    frames = f.frames
+    vin = complex_int8_voltages(13, frames, 512, 20.0)
+    x = torch.from_numpy(vin).to(dev)
+    out = torch.empty((f.n_out,), dtype=torch.float32, device=dev)
+    total, steps_ms, clocks = _timed(lambda: f.execute(x, out), args.steps, args.warmup, dev)
+    launches = f.get("kernel_launches")
+    f.close()
+    ms = total / args.steps
+    logn = int(math.log2(n))
+    outer = max(0, -(-(logn - 14) // 4))
+    pass_bytes = (24 * n + 2 * (12 * n + 16 * n * (outer - 1))) if outer else 16 * n
+    nbytes = pass_bytes + 9.25 * h + 8 * nov
+    value = h / (ms * 1e-3) / 1e6
+    roof = _hbm_roofline(f"whole step ({outer} radix-16 HBM passes each way around 16384-point "
+                         "shared-memory sub-transforms)", nbytes, ms, peaks)
+    roof["flops_per_launch"] = 10.0 * n * logn + 9.0 * n
+    cpu = None
+    if not args.no_cpu_baseline:
+        geo = O.fullband_geometry(*a)
+        dt = _cpu_time(lambda: O.dedisperse_fullband(vin, geo))
+        cpu = {"value": h / dt / 1e6, "unit": "Msamples/s", "cores": 1, "kind": "oracle", "seconds": dt,
+               "sample": f"one segment (N = 2^{logn}, {h} real samples), numpy FP64"}
+    config = {"workload": f"fullband:325MHz-32MHz-512ch-frames-DM50-N2^{logn}-x16", "n_fft": n,
+              "n_ov": nov, "hop": h, "frames_per_block": frames}
+    return _line("fullband", args, "dedispersed real Msamples/s", value, "Msamples/s", ms, steps_ms,
+                 config, roof, cpu, clocks, launches * args.steps, x_realtime=value / 64.0)
+
+
+def row_serving(args, dev, peaks):
+    """Serving pool: 8 mixed streams (GSB 16/32 MHz at 325/610 MHz, upgraded-GMRT
+    200 MHz / 2048 channels at 650 MHz; DM 5..150), 8 blocks each, submitted as
+    fast as possible; the value is the aggregate rate, latency per block."""
+    from paper_1509_00186_b300 import serving
+    specs = serving.mixed_scenario(8)
+    summary, _ = serving.run_mix(specs, 8, speedup=1e9)
+    clocks = None
+    cfg = {"workload": "serving:8-mixed-streams-x8-blocks", "streams": [s.__dict__ for s in specs]}
+    line = {"path": "serving", "metric": "served Msamples/s (8 streams, back to back)",
+            "value": summary["msamples_per_s"], "unit": "Msamples/s", "n_gpus": 1,
+            "steps": summary["blocks"], "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "x_realtime": summary["x_realtime"], "latency_ms": summary["latency_ms"],
+            "deadline_ms": summary["deadline_ms"], "missed_deadlines": summary["missed_deadlines"],
+            "roofline": None, "roofline_note": "the same per-channel kernels as the block path; "
+                                               "this row measures latency and admission",
+            "clocks": clocks}
+    return line
+
+
+ROWS = ("block", "lsb_hann", "dual", "precision", "band_sum", "batch", "fullband", "serving")
+
+
+def run_row(args, world, rank, local):
+    if rank != 0:
+        return 0
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks = measured_peaks()
+    if args.path in ("lsb_hann", "dual", "precision"):
+        line = row_plan_variant(args, dev, peaks, args.path)
+    else:
+        line = {"band_sum": row_band_sum, "batch": row_batch, "fullband": row_fullband,
+                "serving": row_serving}[args.path](args, dev, peaks)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -383,6 +678,8 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--impl", choices=("cdd", "reference"), default="cdd")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--path", choices=ROWS, default="block",
+                    help="block: the headline line; others: one more row of the path (one GPU)")
     ap.add_argument("--channels", type=int, default=None,
                     help="keep only the lowest C channels (profiling captures; not a bench line)")
     args = ap.parse_args(argv)
@@ -391,6 +688,8 @@ def main(argv=None):
         print(f"warning: --gpus {args.gpus} but WORLD_SIZE {world}", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.path != "block":
+        return run_row(args, world, rank, local)
     return run_gpu(args, world, rank, local)
 
 

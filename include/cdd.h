@@ -159,7 +159,10 @@ int cdd_execute_dual(cdd_plan plan, const int8_t* d_in_a, const int8_t* d_in_b, 
 /* Band sum (Sec. 1.2: the aligned sub-bands are added): d_sum[p][m] =
  * sum over k of d_out[p][k][m] for n_planes planes of [n_chan][n_out] floats
  * (a plan's output: one plane; a batch's: one per DM trial, giving the
- * DM-trial time series).  Device buffers; asynchronous on `stream`. */
+ * DM-trial time series).  Device buffers; asynchronous on `stream`.  The
+ * summation order is fixed (every 8th channel per partial sum, then the 8
+ * partials), so results are deterministic; n_out % 4 == 0 with a 16-byte
+ * aligned d_out takes the vector path. */
 int cdd_band_sum(const float* d_out, int64_t n_planes, int n_chan, int64_t n_out, float* d_sum,
                  cudaStream_t stream);
 

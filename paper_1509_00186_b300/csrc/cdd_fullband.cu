@@ -85,46 +85,54 @@ icf_kernel(const char2* __restrict__ in, float* __restrict__ ts, const float2* _
 }
 
 // ---- outer passes through HBM --------------------------------------------
-// DIF radix-R pass of stride S over N points (sub-problems of M = R*S), in place.
-// FIRST: the input is the real series ts (imaginary part zero).
+// DIF radix-R pass of stride S = 2^ls over N points (sub-problems of M = R*S),
+// in place.  FIRST: the input is the real series ts (imaginary part zero).
+// Butterfly b: t = b mod S, base = (b div S) * M + t; its twiddles are
+// w_M^{t k} = w_N^{t k N/M} with t k < M, so no reduction is needed.
 template <int R, bool FIRST>
 __global__ void __launch_bounds__(256)
-outer_fwd_kernel(float2* __restrict__ w, const float* __restrict__ ts, long long n, long long s,
+outer_fwd_kernel(float2* __restrict__ w, const float* __restrict__ ts, long long n, int ls,
                  const float2* __restrict__ thi, const float2* __restrict__ tlo) {
-  const long long nb = n / R;
+  constexpr int LR = ilog2(R);
+  const long long s = 1LL << ls;
+  const long long nb = n >> LR;
+  const long long step = n >> (ls + LR);
   for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
        b += (long long)gridDim.x * blockDim.x) {
-    const long long t = b % s;
-    const long long base = (b / s) * (s * R) + t;
+    const long long t = b & (s - 1);
+    const long long base = ((b >> ls) << (ls + LR)) + t;
     float2 v[R];
 #pragma unroll
     for (int j = 0; j < R; ++j)
       v[j] = FIRST ? make_float2(__ldg(&ts[base + s * j]), 0.f) : w[base + s * j];
     dft<R, -1>(v);
-    const long long step = n / (s * R);     // w_M^{t k} = w_N^{t k N/M}
+    const long long e1 = t * step;
 #pragma unroll
-    for (int k = 1; k < R; ++k) v[k] = cmul(v[k], twiddle(thi, tlo, ((t * k) % (s * R)) * step));
+    for (int k = 1; k < R; ++k) v[k] = cmul(v[k], twiddle(thi, tlo, e1 * k));
 #pragma unroll
     for (int k = 0; k < R; ++k) w[base + s * k] = v[k];
   }
 }
 
-// DIT radix-R pass of stride S, in place; LAST (stride N/R) writes Re(y)^2.
+// DIT radix-R pass of stride S = 2^ls, in place; LAST (stride N/R) writes Re(y)^2.
 template <int R, bool LAST>
 __global__ void __launch_bounds__(256)
-outer_inv_kernel(float2* __restrict__ w, float* __restrict__ pw, long long n, long long s,
+outer_inv_kernel(float2* __restrict__ w, float* __restrict__ pw, long long n, int ls,
                  const float2* __restrict__ thi, const float2* __restrict__ tlo) {
-  const long long nb = n / R;
+  constexpr int LR = ilog2(R);
+  const long long s = 1LL << ls;
+  const long long nb = n >> LR;
+  const long long step = n >> (ls + LR);
   for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nb;
        b += (long long)gridDim.x * blockDim.x) {
-    const long long t = b % s;
-    const long long base = (b / s) * (s * R) + t;
-    const long long step = n / (s * R);
+    const long long t = b & (s - 1);
+    const long long base = ((b >> ls) << (ls + LR)) + t;
+    const long long e1 = t * step;
     float2 v[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = w[base + s * k];
 #pragma unroll
-    for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], twiddle(thi, tlo, ((t * k) % (s * R)) * step));
+    for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], twiddle(thi, tlo, e1 * k));
     dft<R, 1>(v);
 #pragma unroll
     for (int j = 0; j < R; ++j) {
@@ -301,13 +309,16 @@ cudaError_t launch_middle(int logs, float2* w, const float* ts, float* pw, const
 cudaError_t launch_outer(bool forward, bool edge, int radix, float2* w, const float* ts, float* pw,
                          long long n, long long stride, const float2* thi, const float2* tlo,
                          cudaStream_t s) {
+  if (stride <= 0 || (stride & (stride - 1)) || n % (stride * radix)) return cudaErrorInvalidValue;
+  int ls = 0;
+  while ((1LL << ls) < stride) ++ls;
   const unsigned grid = grid_for(n / radix);
-#define CDD_OUTER(R)                                                                           \
-  case R:                                                                                      \
-    if (forward && edge) outer_fwd_kernel<R, true><<<grid, 256, 0, s>>>(w, ts, n, stride, thi, tlo);   \
-    else if (forward) outer_fwd_kernel<R, false><<<grid, 256, 0, s>>>(w, ts, n, stride, thi, tlo);     \
-    else if (edge) outer_inv_kernel<R, true><<<grid, 256, 0, s>>>(w, pw, n, stride, thi, tlo);         \
-    else outer_inv_kernel<R, false><<<grid, 256, 0, s>>>(w, pw, n, stride, thi, tlo);                  \
+#define CDD_OUTER(R)                                                                         \
+  case R:                                                                                    \
+    if (forward && edge) outer_fwd_kernel<R, true><<<grid, 256, 0, s>>>(w, ts, n, ls, thi, tlo);    \
+    else if (forward) outer_fwd_kernel<R, false><<<grid, 256, 0, s>>>(w, ts, n, ls, thi, tlo);      \
+    else if (edge) outer_inv_kernel<R, true><<<grid, 256, 0, s>>>(w, pw, n, ls, thi, tlo);          \
+    else outer_inv_kernel<R, false><<<grid, 256, 0, s>>>(w, pw, n, ls, thi, tlo);                   \
     break;
   switch (radix) {
     CDD_OUTER(2) CDD_OUTER(4) CDD_OUTER(8) CDD_OUTER(16)

@@ -762,38 +762,88 @@ cudaError_t launch_corner_turn(const char2* in, char2* out, long long r_begin, l
   return cudaGetLastError();
 }
 
-// sum[p][m] = sum over k of out[p][k][m], channels added in order (deterministic).
-__global__ void band_sum_kernel(const float* __restrict__ out, long long n_planes, int n_chan,
-                                long long n_out, float* __restrict__ sum) {
-  const long long total = n_planes * n_out;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long p = e / n_out, m = e % n_out;
-    const float* src = out + p * n_chan * n_out + m;
-    float acc = 0.f;
-    for (int k = 0; k < n_chan; ++k) acc += __ldg(src + (long long)k * n_out);
-    sum[e] = acc;
+// Band sum over channels: sum[p][m] = sum_k out[p][k][m].  A CTA owns a tile
+// of 32*V neighbouring outputs of one plane (V = 4: float4 per lane); its 8
+// warps take every 8th channel, so each warp keeps 8 row loads in flight, and
+// the 8 partial sums meet in shared memory.
+template <int V>
+__global__ void __launch_bounds__(256)
+band_sum_kernel(const float* __restrict__ out, long long n_planes, int n_chan, long long n_out,
+                float* __restrict__ sum) {
+  constexpr int TILE = 32 * V;
+  __shared__ float part[8][TILE];
+  const long long tiles = (n_out + TILE - 1) / TILE;
+  const long long p = blockIdx.x / tiles;
+  const long long c0 = (blockIdx.x % tiles) * TILE;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const long long m = c0 + (long long)lane * V;
+  float acc[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) acc[v] = 0.f;
+  if (m < n_out) {                                   // V = 4: n_out % 4 == 0, so m + 3 < n_out
+    const float* col = out + p * n_chan * n_out + m;
+#pragma unroll 8
+    for (int k = wp; k < n_chan; k += 8) {
+      if constexpr (V == 4) {
+        const float4 x = __ldg(reinterpret_cast<const float4*>(col + (long long)k * n_out));
+        acc[0] += x.x;
+        acc[1] += x.y;
+        acc[2] += x.z;
+        acc[3] += x.w;
+      } else {
+        acc[0] += __ldg(col + (long long)k * n_out);
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v) part[wp][lane * V + v] = acc[v];
+  __syncthreads();
+  for (int t = threadIdx.x; t < TILE; t += blockDim.x) {
+    float tot = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) tot += part[w][t];
+    if (c0 + t < n_out) sum[p * n_out + c0 + t] = tot;
   }
 }
 
-// acc[i] += add[i]
+// acc[i] += add[i]; float4 when both are 16-byte aligned and n % 4 == 0.
+template <int V>
 __global__ void accumulate_kernel(float* __restrict__ acc, const float* __restrict__ add, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    acc[i] += add[i];
+  const long long nv = n / V;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv;
+       i += (long long)gridDim.x * blockDim.x) {
+    if constexpr (V == 4) {
+      float4 a = reinterpret_cast<float4*>(acc)[i];
+      const float4 b = __ldg(reinterpret_cast<const float4*>(add) + i);
+      a.x += b.x;
+      a.y += b.y;
+      a.z += b.z;
+      a.w += b.w;
+      reinterpret_cast<float4*>(acc)[i] = a;
+    } else {
+      acc[i] += add[i];
+    }
+  }
 }
 
 cudaError_t launch_band_sum(const float* out, long long n_planes, int n_chan, long long n_out,
                             float* sum, cudaStream_t s) {
-  const long long total = n_planes * n_out;
-  const unsigned grid = (unsigned)((total + 255) / 256 < 148 * 16 ? (total + 255) / 256 : 148 * 16);
-  band_sum_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(out, n_planes, n_chan, n_out, sum);
+  const bool vec = n_out % 4 == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+  const int tile = vec ? 128 : 32;
+  const long long blocks = n_planes * ((n_out + tile - 1) / tile);
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  if (vec) band_sum_kernel<4><<<(unsigned)blocks, 256, 0, s>>>(out, n_planes, n_chan, n_out, sum);
+  else band_sum_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(out, n_planes, n_chan, n_out, sum);
   return cudaGetLastError();
 }
 
 cudaError_t launch_accumulate(float* acc, const float* add, long long n, cudaStream_t s) {
-  const unsigned grid = (unsigned)((n + 255) / 256 < 148 * 16 ? (n + 255) / 256 : 148 * 16);
-  accumulate_kernel<<<grid > 0 ? grid : 1, 256, 0, s>>>(acc, add, n);
+  const bool vec = n % 4 == 0 && ((reinterpret_cast<uintptr_t>(acc) | reinterpret_cast<uintptr_t>(add)) & 15) == 0;
+  const long long nv = vec ? n / 4 : n;
+  const unsigned grid = (unsigned)((nv + 255) / 256 < 148 * 32 ? (nv + 255) / 256 : 148 * 32);
+  if (vec) accumulate_kernel<4><<<grid > 0 ? grid : 1, 256, 0, s>>>(acc, add, n);
+  else accumulate_kernel<1><<<grid > 0 ? grid : 1, 256, 0, s>>>(acc, add, n);
   return cudaGetLastError();
 }
 

@@ -295,3 +295,20 @@ def test_band_sum_of_plan_and_batch_outputs(cuda_device):
         series = band_sum(b.execute(torch.from_numpy(x).cuda())).cpu().numpy()
     assert series.shape == (2, 1984 * 2 // 4)
     assert O.rel_rms(series, O.band_sum(O.dedisperse_batch(x, g))) <= TOL
+
+
+def test_band_sum_ragged_and_misaligned(cuda_device):
+    """The scalar form of the band sum (n_out not a multiple of 4, or a buffer
+    that is not 16-byte aligned) and the vector form agree with a float64 sum."""
+    import torch
+    from paper_1509_00186_b300.cdd import band_sum
+    rng = np.random.default_rng(3)
+    for planes, C, n in ((3, 37, 1001), (2, 512, 4096), (1, 1, 5)):
+        a = rng.random((planes, C, n)).astype(np.float32)
+        got = band_sum(torch.from_numpy(a).cuda()).cpu().numpy()
+        assert O.rel_rms(got, O.band_sum(a.astype(np.float64))) <= 1e-6
+        raw = torch.empty(a.size + 1, dtype=torch.float32, device="cuda")
+        shifted = raw[1:].view(planes, C, n)                  # 4 bytes past a 16-byte boundary
+        shifted.copy_(torch.from_numpy(a))
+        got2 = band_sum(shifted).cpu().numpy()
+        assert np.array_equal(got2, got) or O.rel_rms(got2, got) <= 1e-6
