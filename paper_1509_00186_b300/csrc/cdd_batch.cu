@@ -56,11 +56,14 @@ __device__ __forceinline__ float2 dm_chirp(float2 t1, float2 dm) {
   return make_float2(cs, -sn);
 }
 
-template <int LOGN>
-__global__ void __launch_bounds__(Cfg<LOGN>::THREADS, Cfg<LOGN>::MINB)
-batch_kernel(const BatchArgs a) {
+// One (channel, segment) work item w of a tier: the forward transform, the
+// spectrum to its scratch row, then every DM trial.  SH: tw is in shared
+// memory.  sync() is the group's barrier.  Returns true when buf (the power
+// samples) was read after the last barrier.
+template <int LOGN, bool SH, class Sync>
+__device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, const float2* tw, int lt,
+                                              bool active, int w, Sync sync) {
   using PL = PassPlan<LOGN>;
-  using CF = Cfg<LOGN>;
   constexpr int N = PL::N;
   constexpr int T = PL::T;
   constexpr int R0 = PL::R(0);
@@ -68,13 +71,14 @@ batch_kernel(const BatchArgs a) {
   constexpr int NG = N / RL;
   constexpr int PERC = NG / T;
   static_assert(RL <= 16, "stride-1 groups must not cross a padding word");
+  // The last forward pass, the spectrum/chirp groups and the first inverse
+  // pass stay within a warp when the last two radices are equal.
+  constexpr bool kWarpMid = PL::P >= 3 && PL::R(PL::P - 2) == RL && RL <= 32;
+  auto mid_sync = [&] {
+    if constexpr (kWarpMid) __syncwarp();
+    else sync();
+  };
 
-  extern __shared__ float2 smem[];
-  const int g = threadIdx.x / T;
-  const int lt = threadIdx.x % T;
-  float2* buf = smem + g * CF::SEG_F2;
-  const int w = blockIdx.x * CF::G + g;
-  const bool active = w < a.n_tchan * a.q;
   const int kt = active ? w % a.n_tchan : 0;     // channel within the tier, fastest
   const int s = active ? w / a.n_tchan : 0;
   const int k = a.chan0 + kt;
@@ -104,17 +108,22 @@ batch_kernel(const BatchArgs a) {
     for (int j = 0; j < R0; ++j) v[j] = unpack_i8x2(c[j]);
     dft<R0, -1>(v);
 #pragma unroll
-    for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], __ldg(&a.tw[kk * T + lt]));
+    for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
 #pragma unroll
     for (int kk = 0; kk < R0; ++kk) pb0[poff<T>(kk)] = v[kk];
   }
-  __syncthreads();
+  sync();
   static_for<1, PL::P - 1>([&](auto P_) {
-    if (active) fwd_pass<LOGN, decltype(P_)::value>(buf, a.tw, lt);
-    __syncthreads();
+    constexpr int p = decltype(P_)::value;
+    if (active) fwd_pass<LOGN, p, SH>(buf, tw, lt);
+    if constexpr (p == PL::P - 2) mid_sync();
+    else sync();
   });
+  if constexpr (PL::P < 3) sync();
 
-  // ---- last forward radix: the spectrum, scaled by 1/N, to this segment's scratch row
+  // ---- last forward radix: the spectrum, scaled by 1/N, to this segment's
+  // scratch row.  A thread later chirps and writes back exactly the groups it
+  // reads here, so no barrier separates the two.
   float2* xk = a.xs + (size_t)w * N;
   if (active) {
 #pragma unroll 1
@@ -132,11 +141,14 @@ batch_kernel(const BatchArgs a) {
   }
 
   const float2* t1k = a.t1 + (size_t)kt * N;
-  const int n_int = a.hop / a.n_avg;
+  const int na = a.n_avg;
+  const int n_int = a.hop / na;
+  bool in_lanes = false;
+  if constexpr (T % 32 == 0 && LOGN <= 13) in_lanes = na <= R0 && na <= 32 && (na & (na - 1)) == 0;
   float* pw = reinterpret_cast<float*>(buf);
 #pragma unroll 1
   for (int d = 0; d < a.n_dm; ++d) {
-    __syncthreads();                          // buf is free again
+    if (!in_lanes && d > 0) sync();           // the previous DM's power samples are read
     // ---- chirp of DM d and first inverse radix (each thread re-reads its own rows)
     if (active) {
       const float2 dm = a.dms[d];
@@ -153,47 +165,106 @@ batch_kernel(const BatchArgs a) {
         for (int j = 0; j < RL; ++j) pb[j] = x[j];
       }
     }
-    __syncthreads();
+    if constexpr (PL::P >= 3) mid_sync();
+    else sync();
     static_for<1, PL::P - 1>([&](auto I_) {
-      if (active) inv_pass<LOGN, PL::P - 1 - decltype(I_)::value>(buf, a.tw, lt);
-      __syncthreads();
+      if (active) inv_pass<LOGN, PL::P - 1 - decltype(I_)::value, SH>(buf, tw, lt);
+      sync();
     });
     // ---- pass 0, inverse, detection
     if (active) {
 #pragma unroll
       for (int kk = 0; kk < R0; ++kk) v[kk] = pb0[poff<T>(kk)];
 #pragma unroll
-      for (int kk = 1; kk < R0; ++kk) v[kk] = cmulc(v[kk], __ldg(&a.tw[kk * T + lt]));
+      for (int kk = 1; kk < R0; ++kk) v[kk] = cmulc(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
       dft<R0, 1>(v);
     }
-    __syncthreads();
-    if (active) {
+    sync();                                   // every thread has read buf
+    if (!in_lanes) {
+      if (active) {
 #pragma unroll
-      for (int j = 0; j < R0; ++j) {
-        const int n = lt + T * j;
-        pw[n + (n >> 5)] = fmaf(v[j].x, v[j].x, v[j].y * v[j].y);
+        for (int j = 0; j < R0; ++j) {
+          const int n = lt + T * j;
+          pw[n + (n >> 5)] = fmaf(v[j].x, v[j].x, v[j].y * v[j].y);
+        }
       }
+      sync();
     }
-    __syncthreads();
     // ---- integrate, discard the overlap, align into DM d's plane
     if (active) {
       const size_t row = (size_t)d * a.n_chan + k;
       const int r = __ldg(&a.shift[row]);
       float* outk = a.out + row * a.n_out;
       float* rw = a.ring_wr + row * a.r_max;
-      for (int m = lt; m < n_int; m += T) {
-        const int n0 = a.n_ov + m * a.n_avg;
-        float acc = 0.f;
-        for (int i = 0; i < a.n_avg; ++i) acc += pw[(n0 + i) + ((n0 + i) >> 5)];
+      auto emit = [&](int m, float acc) {
         const int dst = s * n_int + m + r;     // aligned index within this block
         if (dst < a.n_out) outk[dst] = acc;
         else rw[dst - a.n_out] = acc;          // the next block's first r outputs
+      };
+      if (in_lanes) {
+        if constexpr (T % 32 == 0 && LOGN <= 13) integrate_in_lanes<R0, T>(v, lt, a.n_ov, na, emit);
+      } else {
+        for (int m = lt; m < n_int; m += T) {
+          const int n0 = a.n_ov + m * na;
+          float acc = 0.f;
+          for (int i = 0; i < na; ++i) acc += pw[(n0 + i) + ((n0 + i) >> 5)];
+          emit(m, acc);
+        }
       }
       if (s == 0) {
         const float* rr = a.ring_rd + row * a.r_max;
         for (int m = lt; m < r; m += T) outk[m] = rr[m];
       }
     }
+  }
+  return !in_lanes;
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(Cfg<LOGN>::THREADS, Cfg<LOGN>::MINB)
+batch_kernel(const BatchArgs a) {
+  using PL = PassPlan<LOGN>;
+  using CF = Cfg<LOGN>;
+  extern __shared__ float2 smem[];
+  const int g = threadIdx.x / PL::T;
+  const int lt = threadIdx.x % PL::T;
+  float2* buf = smem + g * CF::SEG_F2;
+  const int w = blockIdx.x * CF::G + g;
+  const bool active = w < a.n_tchan * a.q;
+  batch_segment<LOGN, false>(a, buf, a.tw, lt, active, w, [] { __syncthreads(); });
+}
+
+// Persistent form for N = 4096 and 8192: one CTA per SM, two groups of 256
+// threads looping over work items with their own named barriers, the twiddle
+// table staged once in shared memory (each work item runs one forward and
+// n_dm inverse transforms with it).
+template <int LOGN>
+struct BatchPersist {
+  using PL = PassPlan<LOGN>;
+  static constexpr int GROUPS = 2;
+  static constexpr int THREADS = GROUPS * PL::T;
+  static constexpr size_t SMEM = (size_t(PL::TW_LEN) + size_t(GROUPS) * padded_len(PL::N)) * sizeof(float2);
+};
+
+template <int LOGN>
+__global__ void __launch_bounds__(BatchPersist<LOGN>::THREADS, 1)
+batch_persistent_kernel(const BatchArgs a) {
+  using PL = PassPlan<LOGN>;
+  using BP = BatchPersist<LOGN>;
+  constexpr int T = PL::T;
+  extern __shared__ float2 smem[];
+  float2* tws = smem;
+  for (int i = threadIdx.x; i < PL::TW_LEN; i += blockDim.x) tws[i] = __ldg(&a.tw[i]);
+  __syncthreads();
+  const int g = threadIdx.x / T;
+  const int lt = threadIdx.x % T;
+  float2* buf = smem + PL::TW_LEN + g * padded_len(PL::N);
+  const int bar = g + 1;                       // named barriers 1, 2 (0 is __syncthreads)
+  auto sync = [bar] { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(T) : "memory"); };
+  const int work = a.n_tchan * a.q;
+  for (int w = blockIdx.x * BP::GROUPS + g; w < work; w += gridDim.x * BP::GROUPS) {
+    if (batch_segment<LOGN, true>(a, buf, tws, lt, true, w, sync))
+      sync();                                  // buf is rewritten by the next work item
   }
 }
 
@@ -234,6 +305,23 @@ cudaError_t launch_batch_t(const BatchArgs& a, cudaStream_t s) {
     attr_set[dev] = true;
   }
   const long long work = (long long)a.n_tchan * a.q;
+  if constexpr (LOGN == 12 || LOGN == 13) {
+    using BP = BatchPersist<LOGN>;
+    static bool pset[128] = {};
+    if (!pset[dev]) {
+      e = cudaFuncSetAttribute(batch_persistent_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)BP::SMEM);
+      if (e != cudaSuccess) return e;
+      pset[dev] = true;
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long need = (work + BP::GROUPS - 1) / BP::GROUPS;
+    const unsigned grid = (unsigned)(need < sms ? need : sms);
+    batch_persistent_kernel<LOGN><<<grid, BP::THREADS, BP::SMEM, s>>>(a);
+    return cudaGetLastError();
+  }
   batch_kernel<LOGN><<<(unsigned)((work + CF::G - 1) / CF::G), CF::THREADS, CF::SMEM, s>>>(a);
   return cudaGetLastError();
 }

@@ -43,67 +43,6 @@ constexpr bool kUsePersistent = CDD_PERSISTENT != 0;
 // unpack and gather, forward passes, chirp, inverse passes, detection,
 // integration and the aligned store.  `tw` is the whole twiddle table, in
 // global memory or (SH) staged in shared memory; `sync` is the group's barrier.
-// Window sums over groups of NA neighbouring lanes by recursive halving: at
-// each step a lane keeps one half of its V values, adds its partner's copy of
-// that half and sends the other half.  Afterwards lane l holds, in u[i]
-// (i < R0/NA), the sum over its lane group of the values it started with at
-// index j = (R0/NA) * (l mod NA) + i.
-template <int R0, int NA, int V = R0>
-__device__ __forceinline__ void lane_window_sums(float (&u)[R0], int lane) {
-  if constexpr (NA > 1) {
-    constexpr int o = NA / 2, H = V / 2;
-    const bool hi = (lane & o) != 0;
-#pragma unroll
-    for (int i = 0; i < H; ++i) {
-      const float keep = hi ? u[i + H] : u[i];
-      const float send = hi ? u[i] : u[i + H];
-      u[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-    }
-    lane_window_sums<R0, NA / 2, H>(u, lane);
-  }
-}
-
-// Detect and integrate the R0 samples n = lt + T*j (j < R0) a thread holds
-// after the last inverse pass: windows of NA samples are NA neighbouring lanes
-// (T is a multiple of 32 and windows start at multiples of NA), so a window's
-// sum is formed in registers.  emit(m, sum) receives output m of the segment,
-// the window starting at n_ov + m*NA.
-template <int R0, int T, int NA, class Emit>
-__device__ __forceinline__ void lane_windows(const float2 (&v)[R0], int lt, int n_ov, Emit& emit) {
-  static_assert(T % 32 == 0 && NA <= 32 && NA <= R0, "window must be lanes of one warp");
-  float u[R0];
-#pragma unroll
-  for (int j = 0; j < R0; ++j) u[j] = fmaf(v[j].x, v[j].x, v[j].y * v[j].y);
-  const int lane = lt & 31;
-  lane_window_sums<R0, NA>(u, lane);
-  constexpr int V = R0 / NA;
-  const int first = lt - (lane & (NA - 1));      // first lane's sample of the window
-#pragma unroll
-  for (int i = 0; i < V; ++i) {
-    const int j = V * (lane & (NA - 1)) + i;
-    const int n0 = first + T * j;
-    if (n0 >= n_ov) emit((n0 - n_ov) / NA, u[i]);
-  }
-}
-
-template <int R0, int T, class Emit>
-__device__ __forceinline__ void integrate_in_lanes(const float2 (&v)[R0], int lt, int n_ov, int na,
-                                                   Emit& emit) {
-  switch (na) {
-    case 1: lane_windows<R0, T, 1>(v, lt, n_ov, emit); break;
-    case 2: lane_windows<R0, T, 2>(v, lt, n_ov, emit); break;
-    case 4: lane_windows<R0, T, 4>(v, lt, n_ov, emit); break;
-    case 8: lane_windows<R0, T, 8>(v, lt, n_ov, emit); break;
-    case 16:
-      if constexpr (R0 >= 16) lane_windows<R0, T, 16>(v, lt, n_ov, emit);
-      break;
-    case 32:
-      if constexpr (R0 >= 32) lane_windows<R0, T, 32>(v, lt, n_ov, emit);
-      break;
-    default: break;
-  }
-}
-
 template <int LOGN, bool CM, bool SH, class Sync>
 __device__ __forceinline__ bool ols_segment(const OlsArgs& a, float2* buf, const float2* tw, int lt,
                                             bool active, int k, int s, Sync sync) {
