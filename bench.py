@@ -599,7 +599,7 @@ def row_fullband(args, dev, peaks):
     import oracle as O
     from synth import complex_int8_voltages
     from paper_1509_00186_b300.cdd import Fullband
-    a = (325.0, 32.0, 512, 50.0, 0, 16)
+    a = (325.0, 32.0, 512, 50.0 if args.dm is None else args.dm, 0, 16)
     f = Fullband(*a, segments_per_block=1)
     n, nov, h = f.get("n_fft"), f.get("n_ov"), f.get("hop")
     frames = f.frames
@@ -624,7 +624,7 @@ def row_fullband(args, dev, peaks):
         dt = _cpu_time(lambda: O.dedisperse_fullband(vin, geo))
         cpu = {"value": h / dt / 1e6, "unit": "Msamples/s", "cores": 1, "kind": "oracle", "seconds": dt,
                "sample": f"one segment (N = 2^{logn}, {h} real samples), numpy FP64"}
-    config = {"workload": f"fullband:325MHz-32MHz-512ch-frames-DM50-N2^{logn}-x16", "n_fft": n,
+    config = {"workload": f"fullband:325MHz-32MHz-512ch-frames-DM{a[3]:g}-N2^{logn}-x16", "n_fft": n,
               "n_ov": nov, "hop": h, "frames_per_block": frames}
     return _line("fullband", args, "dedispersed real Msamples/s", value, "Msamples/s", ms, steps_ms,
                  config, roof, cpu, clocks, launches * args.steps, x_realtime=value / 64.0)
@@ -680,6 +680,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", choices=ROWS, default="block",
                     help="block: the headline line; others: one more row of the path (one GPU)")
+    ap.add_argument("--dm", type=float, default=None,
+                    help="--path fullband: another DM (sets N; smaller cases for profiling captures)")
     ap.add_argument("--channels", type=int, default=None,
                     help="keep only the lowest C channels (profiling captures; not a bench line)")
     args = ap.parse_args(argv)

@@ -214,6 +214,19 @@ __host__ __device__ inline int position_to_bin(int pos) {
   return bin;
 }
 
+// Inverse of position_to_bin: the working-buffer position that holds bin b.
+template <int LOGN>
+__host__ __device__ inline int bin_to_position(int bin) {
+  using PL = PassPlan<LOGN>;
+  int pos = 0;
+#pragma unroll
+  for (int p = 0; p < PL::P; ++p) {
+    const int d = (bin / PL::Rprod(p)) % PL::R(p);
+    pos += d * PL::S(p);
+  }
+  return pos;
+}
+
 // Padded shared-memory index: one spare float2 after every 16, so that the
 // stride-1 groups of the middle pass hit distinct banks.
 __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }

@@ -40,9 +40,12 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ hi, const f
 }
 
 // ---- inverse channelisation: frame t of C bins -> 2C real samples --------
-// Positions of the working buffer hold the Hermitian extension of the frame's
-// spectrum in digit-reversed order (bin 0 real part only, bin C zero); the
-// inverse passes leave the series in natural order.
+// x[n] = (1/F) sum_b Y[b] e^{+2 pi i b n / F} over the Hermitian extension Y
+// of the frame (bin 0 real part only, bin C zero), F = 2C.  Since x is real,
+// x[n] = Re(DFT(conj Y))[n] / F: the forward passes run on conj Y gathered in
+// natural bin order straight from the frame (neighbouring lanes read
+// neighbouring bytes), and sample n is read back from the position that holds
+// bin n, so the stores are coalesced too.
 template <int LOGF>
 __global__ void __launch_bounds__(Cfg<LOGF>::THREADS)
 icf_kernel(const char2* __restrict__ in, float* __restrict__ ts, const float2* __restrict__ twf,
@@ -50,37 +53,146 @@ icf_kernel(const char2* __restrict__ in, float* __restrict__ ts, const float2* _
   using PL = PassPlan<LOGF>;
   using CF = Cfg<LOGF>;
   constexpr int F = PL::N;                  // 2C
+  constexpr int C = F / 2;
+  constexpr int T = PL::T;
+  constexpr int R0 = PL::R(0);
+  constexpr int RL = PL::RL;
+  static_assert(RL <= 16, "stride-1 groups must not cross a padding word");
   extern __shared__ float2 smem[];
-  const int g = threadIdx.x / PL::T;
-  const int lt = threadIdx.x % PL::T;
+  const int g = threadIdx.x / T;
+  const int lt = threadIdx.x % T;
   float2* buf = smem + g * CF::SEG_F2;
   const long long t = (long long)blockIdx.x * CF::G + g;
   const bool active = t < n_frames;
   if (active) {
     const unsigned short* row = reinterpret_cast<const unsigned short*>(in) + t * n_chan;
-    for (int pos = lt; pos < F; pos += PL::T) {
-      const int b = position_to_bin<LOGF>(pos);
-      float2 v = make_float2(0.f, 0.f);
-      if (b == 0) {
-        v = unpack_i8x2(__ldg(row));
-        v.y = 0.f;
-      } else if (b < F / 2) {
-        v = unpack_i8x2(__ldg(row + b));
-      } else if (b > F / 2) {
-        v = unpack_i8x2(__ldg(row + (F - b)));
-        v.y = -v.y;
+    float2 v[R0];
+#pragma unroll
+    for (int j = 0; j < R0; ++j) {
+      const int b = lt + T * j;
+      if (b < C) {                            // conj X[b]; bin 0 keeps its real part only
+        v[j] = unpack_i8x2(__ldg(row + b));
+        v[j].y = b == 0 ? 0.f : -v[j].y;
+      } else if (b > C) {                     // conj of conj X[F - b]
+        v[j] = unpack_i8x2(__ldg(row + (F - b)));
+      } else {
+        v[j] = make_float2(0.f, 0.f);         // the Nyquist bin is not recorded
       }
-      buf[pad(pos)] = v;
+    }
+    dft<R0, -1>(v);
+#pragma unroll
+    for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], __ldg(&twf[kk * T + lt]));
+    float2* pb0 = buf + pad(lt);
+#pragma unroll
+    for (int kk = 0; kk < R0; ++kk) pb0[poff<T>(kk)] = v[kk];
+  }
+  __syncthreads();
+  static_for<1, PL::P - 1>([&](auto P_) {
+    if (active) fwd_pass<LOGF, decltype(P_)::value>(buf, twf, lt);
+    __syncthreads();
+  });
+  if constexpr (PL::P >= 2) {                 // the last radix on stride-1 groups
+    if (active) {
+      for (int q = lt; q < F / RL; q += T) {
+        float2* pb = buf + pad(q * RL);
+        float2 x[RL];
+#pragma unroll
+        for (int j = 0; j < RL; ++j) x[j] = pb[j];
+        dft<RL, -1>(x);
+#pragma unroll
+        for (int j = 0; j < RL; ++j) pb[j] = x[j];
+      }
+    }
+    __syncthreads();
+  }
+  if (active) {
+    float* out = ts + t * F;
+    for (int n = lt; n < F; n += T) out[n] = buf[pad(bin_to_position<LOGF>(n))].x * (1.0f / F);
+  }
+}
+
+// Frames of C = 2^LOGC bins (F = 2C real samples), the same result through a
+// C-point complex transform: with X[C] = 0 and bin 0 real,
+//   E[k] = X[k] + conj X[C-k],  O[k] = (X[k] - conj X[C-k]) e^{+2 pi i k/F},
+//   z[n] = x[2n] + i x[2n+1] = (1/F) sum_k (E[k] + i O[k]) e^{+2 pi i k n/C}
+// (split the F-point sum into even and odd samples; Hermitian symmetry gives
+// X[k+C] = conj X[C-k]).  As above, the forward passes run on conj(E + iO)
+// in natural order and z[n] = conj(Y[n]) / F is read back from the position
+// holding bin n; each z[n] is one float2 store of two neighbouring samples.
+template <int LOGC>
+__global__ void __launch_bounds__(Cfg<LOGC>::THREADS, Cfg<LOGC>::MINB)
+icf_half_kernel(const char2* __restrict__ in, float* __restrict__ ts, const float2* __restrict__ twc,
+                const float2* __restrict__ wk, long long n_frames) {
+  using PL = PassPlan<LOGC>;
+  using CF = Cfg<LOGC>;
+  constexpr int C = PL::N;
+  constexpr int F = 2 * C;
+  constexpr int T = PL::T;
+  constexpr int R0 = PL::R(0);
+  constexpr int RL = PL::RL;
+  static_assert(RL <= 16, "stride-1 groups must not cross a padding word");
+  extern __shared__ float2 smem[];
+  const int g = threadIdx.x / T;
+  const int lt = threadIdx.x % T;
+  float2* buf = smem + g * CF::SEG_F2;
+  const long long t = (long long)blockIdx.x * CF::G + g;
+  const bool active = t < n_frames;
+  if (active) {
+    const unsigned short* row = reinterpret_cast<const unsigned short*>(in) + t * C;
+    float2 v[R0];
+#pragma unroll
+    for (int j = 0; j < R0; ++j) {
+      const int k = lt + T * j;
+      float2 xk = unpack_i8x2(__ldg(row + k));
+      float2 xp = unpack_i8x2(__ldg(row + (k == 0 ? 0 : C - k)));   // X[C - k]
+      if (k == 0) {                          // bin 0 real part only; X[C] is not recorded
+        xk.y = 0.f;
+        xp = make_float2(0.f, 0.f);
+      }
+      const float2 e = make_float2(xk.x + xp.x, xk.y - xp.y);
+      const float2 o = cmul(make_float2(xk.x - xp.x, xk.y + xp.y), __ldg(&wk[k]));
+      v[j] = make_float2(e.x - o.y, -(e.y + o.x));                   // conj(E + i O)
+    }
+    dft<R0, -1>(v);
+#pragma unroll
+    for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], __ldg(&twc[kk * T + lt]));
+    float2* pb0 = buf + pad(lt);
+#pragma unroll
+    for (int kk = 0; kk < R0; ++kk) pb0[poff<T>(kk)] = v[kk];
+  }
+  __syncthreads();
+  static_for<1, PL::P - 1>([&](auto P_) {
+    if (active) fwd_pass<LOGC, decltype(P_)::value>(buf, twc, lt);
+    __syncthreads();
+  });
+  if (active) {                              // the last radix on stride-1 groups
+    for (int q = lt; q < C / RL; q += T) {
+      float2* pb = buf + pad(q * RL);
+      float2 x[RL];
+#pragma unroll
+      for (int j = 0; j < RL; ++j) x[j] = pb[j];
+      dft<RL, -1>(x);
+#pragma unroll
+      for (int j = 0; j < RL; ++j) pb[j] = x[j];
     }
   }
   __syncthreads();
-  static_for<0, PL::P>([&](auto I_) {
-    if (active) inv_pass<LOGF, PL::P - 1 - decltype(I_)::value>(buf, twf, lt);
-    __syncthreads();
-  });
   if (active) {
-    float* out = ts + t * F;
-    for (int n = lt; n < F; n += PL::T) out[n] = buf[pad(n)].x * (1.0f / F);
+    float2* out2 = reinterpret_cast<float2*>(ts + t * F);
+#pragma unroll 4
+    for (int n = lt; n < C; n += T) {
+      const float2 y = buf[pad(bin_to_position<LOGC>(n))];
+      out2[n] = make_float2(y.x * (1.0f / F), -y.y * (1.0f / F));
+    }
+  }
+}
+
+// wk[k] = e^{+2 pi i k / (2C)}, k < C (FP64, rounded once)
+__global__ void fb_wk_kernel(float2* wk, int c) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < c; k += gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincospi((double)k / (double)c, &sn, &cs);
+    wk[k] = make_float2((float)cs, (float)sn);
   }
 }
 
@@ -114,12 +226,19 @@ outer_fwd_kernel(float2* __restrict__ w, const float* __restrict__ ts, long long
   }
 }
 
-// DIT radix-R pass of stride S = 2^ls, in place; LAST (stride N/R) writes Re(y)^2.
-template <int R, bool LAST>
+// DIT radix-R pass of stride S = 2^ls, in place.  LAST (stride N/R, so a
+// thread's butterfly is samples b + S*j): NA = 0 writes Re(y)^2 to pw; NA > 0
+// also detects and sums windows of NA samples across neighbouring lanes
+// (consecutive b are consecutive samples; NA <= R, a power of two) and writes
+// the window sums of the kept part straight to out (window m starts at
+// n_ov + m*NA).
+template <int R, bool LAST, int NA = 0>
 __global__ void __launch_bounds__(256)
 outer_inv_kernel(float2* __restrict__ w, float* __restrict__ pw, long long n, int ls,
-                 const float2* __restrict__ thi, const float2* __restrict__ tlo) {
+                 const float2* __restrict__ thi, const float2* __restrict__ tlo,
+                 float* __restrict__ out, long long n_ov) {
   constexpr int LR = ilog2(R);
+  static_assert(NA == 0 || (LAST && NA <= R && (NA & (NA - 1)) == 0), "lane windows");
   const long long s = 1LL << ls;
   const long long nb = n >> LR;
   const long long step = n >> (ls + LR);
@@ -134,10 +253,25 @@ outer_inv_kernel(float2* __restrict__ w, float* __restrict__ pw, long long n, in
 #pragma unroll
     for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], twiddle(thi, tlo, e1 * k));
     dft<R, 1>(v);
+    if constexpr (NA > 0) {
+      float u[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) {
-      if (LAST) pw[base + s * j] = v[j].x * v[j].x;
-      else w[base + s * j] = v[j];
+      for (int j = 0; j < R; ++j) u[j] = v[j].x * v[j].x;
+      const int lane = threadIdx.x & 31;
+      lane_window_sums<R, NA>(u, lane);
+      constexpr int V = R / NA;
+      const long long first = base - (lane & (NA - 1));
+#pragma unroll
+      for (int i = 0; i < V; ++i) {
+        const long long n0 = first + s * (V * (lane & (NA - 1)) + i);
+        if (n0 >= n_ov) out[(n0 - n_ov) / NA] = u[i];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        if (LAST) pw[base + s * j] = v[j].x * v[j].x;
+        else w[base + s * j] = v[j];
+      }
     }
   }
 }
@@ -268,6 +402,24 @@ cudaError_t launch_icf_t(const char2* in, float* ts, const float2* twf, long lon
   return cudaGetLastError();
 }
 
+template <int LOGC>
+cudaError_t launch_icf_half_t(const char2* in, float* ts, const float2* twc, const float2* wk,
+                              long long n_frames, cudaStream_t s) {
+  using CF = Cfg<LOGC>;
+  static bool set[128] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 128 && !set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(icf_half_kernel<LOGC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)CF::SMEM);
+    if (e != cudaSuccess) return e;
+    set[dev] = true;
+  }
+  icf_half_kernel<LOGC><<<(unsigned)((n_frames + CF::G - 1) / CF::G), CF::THREADS, CF::SMEM, s>>>(
+      in, ts, twc, wk, n_frames);
+  return cudaGetLastError();
+}
+
 template <int LOGS>
 cudaError_t launch_middle_t(float2* w, const float* ts, float* pw, const float2* chirp,
                             const float2* tw, long long n_sub, cudaStream_t s) {
@@ -286,15 +438,21 @@ cudaError_t launch_middle_t(float2* w, const float* ts, float* pw, const float2*
 
 #define CDD_FB_CASES(X) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14)
 
-cudaError_t launch_icf(int logf, const char2* in, float* ts, const float2* twf, long long n_frames,
-                      int n_chan, cudaStream_t s) {
+// Frames of 2C >= 128 samples take the half-length form (twf: the C-point
+// table, wk: e^{+2 pi i k/2C}); 64-sample frames the direct form (twf: the
+// 64-point table).
+cudaError_t launch_icf(int logf, const char2* in, float* ts, const float2* twf, const float2* wk,
+                       long long n_frames, int n_chan, cudaStream_t s) {
   switch (logf) {
-#define X(L) case L: return launch_icf_t<L>(in, ts, twf, n_frames, n_chan, s);
-    CDD_FB_CASES(X)
+    case 6: return launch_icf_t<6>(in, ts, twf, n_frames, n_chan, s);
+#define X(L) case L + 1: return launch_icf_half_t<L>(in, ts, twf, wk, n_frames, s);
+    X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13)
 #undef X
     default: return cudaErrorInvalidValue;
   }
 }
+
+int icf_table_logn(int logf) { return logf > 6 ? logf - 1 : logf; }
 
 cudaError_t launch_middle(int logs, float2* w, const float* ts, float* pw, const float2* chirp,
                           const float2* tw, long long n_sub, cudaStream_t s) {
@@ -308,17 +466,28 @@ cudaError_t launch_middle(int logs, float2* w, const float* ts, float* pw, const
 
 cudaError_t launch_outer(bool forward, bool edge, int radix, float2* w, const float* ts, float* pw,
                          long long n, long long stride, const float2* thi, const float2* tlo,
-                         cudaStream_t s) {
+                         cudaStream_t s, float* out = nullptr, long long n_ov = 0, int na = 0) {
   if (stride <= 0 || (stride & (stride - 1)) || n % (stride * radix)) return cudaErrorInvalidValue;
   int ls = 0;
   while ((1LL << ls) < stride) ++ls;
   const unsigned grid = grid_for(n / radix);
-#define CDD_OUTER(R)                                                                         \
-  case R:                                                                                    \
-    if (forward && edge) outer_fwd_kernel<R, true><<<grid, 256, 0, s>>>(w, ts, n, ls, thi, tlo);    \
-    else if (forward) outer_fwd_kernel<R, false><<<grid, 256, 0, s>>>(w, ts, n, ls, thi, tlo);      \
-    else if (edge) outer_inv_kernel<R, true><<<grid, 256, 0, s>>>(w, pw, n, ls, thi, tlo);          \
-    else outer_inv_kernel<R, false><<<grid, 256, 0, s>>>(w, pw, n, ls, thi, tlo);                   \
+  if (!forward && edge && na > 0) {           // last pass with the integration fused
+    if (radix != 16 || (n / radix) % 32) return cudaErrorInvalidValue;
+    switch (na) {
+#define CDD_OUTER_NA(A) \
+      case A: outer_inv_kernel<16, true, A><<<grid, 256, 0, s>>>(w, pw, n, ls, thi, tlo, out, n_ov); break;
+      CDD_OUTER_NA(1) CDD_OUTER_NA(2) CDD_OUTER_NA(4) CDD_OUTER_NA(8) CDD_OUTER_NA(16)
+#undef CDD_OUTER_NA
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
+#define CDD_OUTER(R)                                                                                  \
+  case R:                                                                                             \
+    if (forward && edge) outer_fwd_kernel<R, true><<<grid, 256, 0, s>>>(w, ts, n, ls, thi, tlo);             \
+    else if (forward) outer_fwd_kernel<R, false><<<grid, 256, 0, s>>>(w, ts, n, ls, thi, tlo);               \
+    else if (edge) outer_inv_kernel<R, true><<<grid, 256, 0, s>>>(w, pw, n, ls, thi, tlo, nullptr, 0);       \
+    else outer_inv_kernel<R, false><<<grid, 256, 0, s>>>(w, pw, n, ls, thi, tlo, nullptr, 0);                \
     break;
   switch (radix) {
     CDD_OUTER(2) CDD_OUTER(4) CDD_OUTER(8) CDD_OUTER(16)
@@ -363,6 +532,7 @@ struct cdd_fullband_s {
   float2* d_chirp = nullptr;                 // [N]
   float2* d_tw = nullptr;                    // twiddles of the L_mid passes
   float2* d_twf = nullptr;                   // twiddles of the frame transform
+  float2* d_wk = nullptr;                    // e^{+2 pi i k/2C}, k < C (half-length frame form)
   float2* d_thi = nullptr;
   float2* d_tlo = nullptr;
   int* d_radix = nullptr;
@@ -413,7 +583,9 @@ int fcommit_once(cdd_fullband f) {
   if ((rc = falloc(f, &f->d_pw, (size_t)n * sizeof(float)))) return rc;
   if ((rc = falloc(f, &f->d_chirp, (size_t)n * sizeof(float2)))) return rc;
   if ((rc = falloc(f, &f->d_tw, (size_t)cdd::twiddle_table_len(f->logs) * sizeof(float2)))) return rc;
-  if ((rc = falloc(f, &f->d_twf, (size_t)cdd::twiddle_table_len(f->logf) * sizeof(float2)))) return rc;
+  if ((rc = falloc(f, &f->d_twf, (size_t)cdd::twiddle_table_len(cdd::icf_table_logn(f->logf)) * sizeof(float2))))
+    return rc;
+  if ((rc = falloc(f, &f->d_wk, (size_t)f->n_chan * sizeof(float2)))) return rc;
   const long long n_hi = n >> cdd::kTwLoBits;
   if (!f->radix_out.empty()) {
     if ((rc = falloc(f, &f->d_thi, (size_t)(n_hi > 0 ? n_hi : 1) * sizeof(float2)))) return rc;
@@ -431,7 +603,11 @@ int fcommit_once(cdd_fullband f) {
   cudaStream_t s;
   FTRY(f, cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   cudaError_t e = cdd::launch_twiddle_table(f->logs, f->d_tw, s);
-  if (e == cudaSuccess) e = cdd::launch_twiddle_table(f->logf, f->d_twf, s);
+  if (e == cudaSuccess) e = cdd::launch_twiddle_table(cdd::icf_table_logn(f->logf), f->d_twf, s);
+  if (e == cudaSuccess) {
+    cdd::fb_wk_kernel<<<cdd::grid_for(f->n_chan), 256, 0, s>>>(f->d_wk, f->n_chan);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess && f->d_thi) {
     cdd::fb_twiddle_kernel<<<cdd::grid_for(n_hi + (1 << cdd::kTwLoBits)), 256, 0, s>>>(f->d_thi, f->d_tlo, n);
     e = cudaGetLastError();
@@ -471,6 +647,7 @@ void ffree(cdd_fullband f) {
   cudaFree(f->d_chirp);
   cudaFree(f->d_tw);
   cudaFree(f->d_twf);
+  cudaFree(f->d_wk);
   cudaFree(f->d_thi);
   cudaFree(f->d_tlo);
   cudaFree(f->d_radix);
@@ -597,7 +774,7 @@ int cdd_fullband_execute(cdd_fullband f, const int8_t* d_in, float* d_out, cudaS
                             cudaMemcpyDeviceToDevice, s));
   }
   const long long frames = (long long)f->q * h / f->frame;
-  FTRY(f, cdd::launch_icf(f->logf, reinterpret_cast<const char2*>(d_in), ts + nov, f->d_twf, frames,
+  FTRY(f, cdd::launch_icf(f->logf, reinterpret_cast<const char2*>(d_in), ts + nov, f->d_twf, f->d_wk, frames,
                           f->n_chan, s));
   launches += 1;
   const int no = (int)f->radix_out.size();
@@ -612,10 +789,15 @@ int cdd_fullband_execute(cdd_fullband f, const int8_t* d_in, float* d_out, cudaS
         FTRY(f, cdd::launch_outer(true, p == 0, f->radix_out[p], f->d_w, seg, nullptr, n,
                                   f->stride_out[p], f->d_thi, f->d_tlo, s));
       FTRY(f, cdd::launch_middle(f->logs, f->d_w, nullptr, nullptr, f->d_chirp, f->d_tw, n_sub, s));
+      // the last pass also integrates across lanes when its radix is 16 and
+      // n_avg <= 16; otherwise it writes Re(y)^2 for the integration kernel
+      const bool fused = f->radix_out[0] == 16 && f->n_avg <= 16;
       for (int p = no - 1; p >= 0; --p)
         FTRY(f, cdd::launch_outer(false, p == 0, f->radix_out[p], f->d_w, nullptr, f->d_pw, n,
-                                  f->stride_out[p], f->d_thi, f->d_tlo, s));
+                                  f->stride_out[p], f->d_thi, f->d_tlo, s,
+                                  d_out + (long long)sg * (h / f->n_avg), nov, fused ? f->n_avg : 0));
       launches += 2 * no + 1;
+      if (fused) continue;
     }
     const long long n_o = h / f->n_avg;
     cdd::fb_integrate_kernel<<<cdd::grid_for(n_o), 256, 0, s>>>(f->d_pw, d_out + (long long)sg * n_o,
