@@ -39,6 +39,20 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ hi, const f
   return cmul(__ldg(&hi[e >> kTwLoBits]), __ldg(&lo[e & ((1 << kTwLoBits) - 1)]));
 }
 
+// w[k] = w_N^{k e1} for 0 < k < R: the powers of two from the tables, the
+// rest as products (at most three deep), so a radix-16 butterfly makes 8
+// table loads instead of 30.
+template <int R>
+__device__ __forceinline__ void twiddle_powers(const float2* __restrict__ hi, const float2* __restrict__ lo,
+                                               long long e1, float2 (&w)[R]) {
+  static_for<1, R>([&](auto K_) {
+    constexpr int k = decltype(K_)::value;
+    constexpr int top = 1 << ilog2(k);             // highest power of two <= k
+    if constexpr (top == k) w[k] = twiddle(hi, lo, e1 * k);
+    else w[k] = cmul(w[k - top], w[top]);
+  });
+}
+
 // ---- inverse channelisation: frame t of C bins -> 2C real samples --------
 // x[n] = (1/F) sum_b Y[b] e^{+2 pi i b n / F} over the Hermitian extension Y
 // of the frame (bin 0 real part only, bin C zero), F = 2C.  Since x is real,
@@ -202,7 +216,7 @@ __global__ void fb_wk_kernel(float2* wk, int c) {
 // Butterfly b: t = b mod S, base = (b div S) * M + t; its twiddles are
 // w_M^{t k} = w_N^{t k N/M} with t k < M, so no reduction is needed.
 template <int R, bool FIRST>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 outer_fwd_kernel(float2* __restrict__ w, const float* __restrict__ ts, long long n, int ls,
                  const float2* __restrict__ thi, const float2* __restrict__ tlo) {
   constexpr int LR = ilog2(R);
@@ -218,9 +232,10 @@ outer_fwd_kernel(float2* __restrict__ w, const float* __restrict__ ts, long long
     for (int j = 0; j < R; ++j)
       v[j] = FIRST ? make_float2(__ldg(&ts[base + s * j]), 0.f) : w[base + s * j];
     dft<R, -1>(v);
-    const long long e1 = t * step;
+    float2 tw[R];
+    twiddle_powers<R>(thi, tlo, t * step, tw);
 #pragma unroll
-    for (int k = 1; k < R; ++k) v[k] = cmul(v[k], twiddle(thi, tlo, e1 * k));
+    for (int k = 1; k < R; ++k) v[k] = cmul(v[k], tw[k]);
 #pragma unroll
     for (int k = 0; k < R; ++k) w[base + s * k] = v[k];
   }
@@ -233,7 +248,7 @@ outer_fwd_kernel(float2* __restrict__ w, const float* __restrict__ ts, long long
 // the window sums of the kept part straight to out (window m starts at
 // n_ov + m*NA).
 template <int R, bool LAST, int NA = 0>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 outer_inv_kernel(float2* __restrict__ w, float* __restrict__ pw, long long n, int ls,
                  const float2* __restrict__ thi, const float2* __restrict__ tlo,
                  float* __restrict__ out, long long n_ov) {
@@ -250,8 +265,10 @@ outer_inv_kernel(float2* __restrict__ w, float* __restrict__ pw, long long n, in
     float2 v[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = w[base + s * k];
+    float2 tw[R];
+    twiddle_powers<R>(thi, tlo, e1, tw);
 #pragma unroll
-    for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], twiddle(thi, tlo, e1 * k));
+    for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], tw[k]);
     dft<R, 1>(v);
     if constexpr (NA > 0) {
       float u[R];
@@ -294,9 +311,14 @@ middle_kernel(float2* __restrict__ w, const float* __restrict__ ts, float* __res
   const long long qq = (long long)blockIdx.x * CF::G + g;
   const bool active = qq < n_sub;
   float2* wq = w + qq * NS;
-  if (active) {
-    for (int i = lt; i < NS; i += PL::T)
-      buf[pad(i)] = ts ? make_float2(__ldg(&ts[qq * NS + i]), 0.f) : wq[i];
+  if (active) {                             // every load in flight before the first store
+    constexpr int PER = NS / PL::T;
+    float2 r[PER];
+#pragma unroll
+    for (int i = 0; i < PER; ++i)
+      r[i] = ts ? make_float2(__ldg(&ts[qq * NS + lt + i * PL::T]), 0.f) : wq[lt + i * PL::T];
+#pragma unroll
+    for (int i = 0; i < PER; ++i) buf[pad(lt + i * PL::T)] = r[i];
   }
   __syncthreads();
   static_for<0, PL::P - 1>([&](auto P_) {

@@ -219,11 +219,6 @@ struct Persist {
 #define CDD_PREFETCH 1
 #endif
 
-// Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 // Ask L2 for the channel-major input rows and the chirp row of work item w,
 // restricted to the 16-byte blocks that lie wholly inside the rows the
 // segment reads (so every prefetched byte is one the kernel will load).

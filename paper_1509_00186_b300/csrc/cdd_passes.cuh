@@ -50,6 +50,12 @@ __device__ __forceinline__ float2 unpack_i8x2(uint32_t raw16) {
   return make_float2(re, im);
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16; the
+// range must lie inside one allocation).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // A twiddle from global memory (read-only path) or from a copy in shared
 // memory; the read-only load must never see a shared-memory address.
 template <bool SH>
