@@ -306,7 +306,7 @@ ols_cluster_kernel(const OlsArgs a) {
     const unsigned short* tail = reinterpret_cast<const unsigned short*>(a.tail_rd) + (long long)k * a.n_ov;
     unsigned short* tail_out = reinterpret_cast<unsigned short*>(a.tail_wr) + (long long)k * a.n_ov;
     const bool last = (s == a.q - 1) && a.n_ov > 0;
-#pragma unroll 1
+#pragma unroll 2
     for (int i = 0; i < PERX; ++i) {
       const int t = rank * NB + lt + i * T;
       unsigned short c[CL];
@@ -365,36 +365,71 @@ ols_cluster_kernel(const OlsArgs a) {
   }
   cluster.sync();                        // no CTA reads another's buffer after this
 
-  // ---- detect into this CTA's buffer: (j, tt) -> j*NB + tt, one spare word per 32
-  float* pw = reinterpret_cast<float*>(buf);
-#pragma unroll
-  for (int i = 0; i < PERX; ++i) {
-#pragma unroll
-    for (int j = 0; j < CL; ++j) {
-      const int nl = j * NB + lt + i * T;
-      pw[nl + (nl >> 5)] = fmaf(z[i][j].x, z[i][j].x, z[i][j].y * z[i][j].y);
-    }
-  }
-  __syncthreads();
-
-  // ---- integrate, discard, align: n in [NS*j + rank*NB, NS*j + (rank+1)*NB)
   const int n_int = a.hop / a.n_avg;
   const int r = __ldg(&a.shift[k]);
   const long long gseg = a.g0 + (long long)s * n_int;
   float* outk = a.out + (size_t)k * a.n_out;
   float* ringk = a.ring + (size_t)k * a.ring_len;
-  const int per_j = NB / a.n_avg;
-  for (int e = lt; e < CL * per_j; e += T) {
-    const int j = e / per_j, mm = e % per_j;
-    const int n0 = NS * j + rank * NB + mm * a.n_avg;
-    if (n0 < a.n_ov) continue;                          // the overlap is discarded
-    const int nl0 = j * NB + mm * a.n_avg;
-    float acc = 0.f;
-    for (int i = 0; i < a.n_avg; ++i) acc += pw[(nl0 + i) + ((nl0 + i) >> 5)];
+  auto emit = [&](int n0, float acc) {      // the window starting at sample n0 >= n_ov
     const long long gi = gseg + (n0 - a.n_ov) / a.n_avg;
     const long long dst = gi + r - a.g0;
     if (dst < a.n_out) outk[dst] = acc;
     else ringk[gi % a.ring_len] = acc;
+  };
+  const int na = a.n_avg;
+  constexpr int U = PERX * CL;
+  if (U == 32 && na <= 32 && (na & (na - 1)) == 0) {
+    // ---- detect and integrate across lanes: a thread holds samples
+    // n = NS*j + rank*NB + lt + i*T, so a window is na neighbouring lanes
+    float u[U];
+#pragma unroll
+    for (int i = 0; i < PERX; ++i)
+#pragma unroll
+      for (int j = 0; j < CL; ++j) u[i * CL + j] = fmaf(z[i][j].x, z[i][j].x, z[i][j].y * z[i][j].y);
+    const int lane = lt & 31;
+    auto windows = [&](auto NA_) {
+      constexpr int NA = decltype(NA_)::value;
+      constexpr int V = U / NA;
+      lane_window_sums<U, NA>(u, lane);
+      const int lo = lane & (NA - 1);
+#pragma unroll
+      for (int q = 0; q < V; ++q) {
+        const int jj = V * lo + q;                    // flattened (i, j) of this sum
+        const int n0 = NS * (jj % CL) + rank * NB + (lt - lo) + (jj / CL) * T;
+        if (n0 >= a.n_ov) emit(n0, u[q]);
+      }
+    };
+    switch (na) {
+      case 1: windows(std::integral_constant<int, 1>{}); break;
+      case 2: windows(std::integral_constant<int, 2>{}); break;
+      case 4: windows(std::integral_constant<int, 4>{}); break;
+      case 8: windows(std::integral_constant<int, 8>{}); break;
+      case 16: windows(std::integral_constant<int, 16>{}); break;
+      default: windows(std::integral_constant<int, 32>{}); break;
+    }
+  } else {
+    // ---- detect into this CTA's buffer: (j, tt) -> j*NB + tt, one spare word per 32
+    float* pw = reinterpret_cast<float*>(buf);
+#pragma unroll
+    for (int i = 0; i < PERX; ++i) {
+#pragma unroll
+      for (int j = 0; j < CL; ++j) {
+        const int nl = j * NB + lt + i * T;
+        pw[nl + (nl >> 5)] = fmaf(z[i][j].x, z[i][j].x, z[i][j].y * z[i][j].y);
+      }
+    }
+    __syncthreads();
+    // ---- integrate, discard, align: n in [NS*j + rank*NB, NS*j + (rank+1)*NB)
+    const int per_j = NB / na;
+    for (int e = lt; e < CL * per_j; e += T) {
+      const int j = e / per_j, mm = e % per_j;
+      const int n0 = NS * j + rank * NB + mm * na;
+      if (n0 < a.n_ov) continue;                          // the overlap is discarded
+      const int nl0 = j * NB + mm * na;
+      float acc = 0.f;
+      for (int i = 0; i < na; ++i) acc += pw[(nl0 + i) + ((nl0 + i) >> 5)];
+      emit(n0, acc);
+    }
   }
   if (s == 0 && rank == 0) {
     const int lim = r < a.n_out ? r : a.n_out;
