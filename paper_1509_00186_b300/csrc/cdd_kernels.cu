@@ -290,14 +290,23 @@ ols_cluster_kernel(const OlsArgs a) {
   extern __shared__ float2 smem[];
   float2* buf = smem;
   const int lt = threadIdx.x;
-  const int w = blockIdx.x / CL;         // one segment per cluster
-  const int k = w % a.n_chan;
-  const int s = a.s_begin + w / a.n_chan;
   float2* rbuf[CL];
 #pragma unroll
   for (int j = 0; j < CL; ++j) rbuf[j] = cluster.map_shared_rank(buf, j);
   const float2* twx = a.tw + PL::TW_LEN;
+  const int na = a.n_avg;
+  constexpr int U = PERX * CL;
+  const bool in_lanes = U == 32 && na <= 32 && (na & (na - 1)) == 0;
   cluster.sync();                        // every CTA of the cluster has started: DSMEM is live
+  // One segment per cluster: the body below.  Pairs (N = 32768) run as
+  // persistent clusters that loop over segments, each CTA asking L2 for its
+  // quarter of the next segment's input rows and chirp row while it works;
+  // clusters of four (N = 65536) run one segment each (measured faster).
+  const int n_clusters = (int)(gridDim.x / CL);
+  const int work = a.n_chan * a.s_count;
+  auto segment = [&](const int w) {
+  const int k = w % a.n_chan;
+  const int s = a.s_begin + w / a.n_chan;
 
   // ---- cross pass, forward: x[t + NS*j] -> DFT_CL -> w_N^{t*kk} -> CTA kk, index t
   {
@@ -376,9 +385,7 @@ ols_cluster_kernel(const OlsArgs a) {
     if (dst < a.n_out) outk[dst] = acc;
     else ringk[gi % a.ring_len] = acc;
   };
-  const int na = a.n_avg;
-  constexpr int U = PERX * CL;
-  if (U == 32 && na <= 32 && (na & (na - 1)) == 0) {
+  if (in_lanes) {
     // ---- detect and integrate across lanes: a thread holds samples
     // n = NS*j + rank*NB + lt + i*T, so a window is na neighbouring lanes
     float u[U];
@@ -437,6 +444,33 @@ ols_cluster_kernel(const OlsArgs a) {
       const long long src = a.g0 + m - r;
       outk[m] = src >= 0 ? ringk[src % a.ring_len] : 0.f;
     }
+  }
+  // The next forward cross pass writes into every CTA's buffer: with the
+  // shared-memory integration the buffers are still being read here.
+  if (!in_lanes) cluster.sync();
+  };
+  if constexpr (CL == 2) {
+    for (int w = (int)(blockIdx.x / CL); w < work; w += n_clusters) {
+      if (lt == 0 && w + n_clusters < work) {
+        const int wn = w + n_clusters;
+        const int kn = wn % a.n_chan;
+        const long long r0 = (long long)(a.s_begin + wn / a.n_chan) * a.hop - a.n_ov;
+        const char* row = reinterpret_cast<const char*>(a.in_cm + (long long)kn * a.rows);
+#pragma unroll
+        for (int j = 0; j < CL; ++j) {      // rows r0 + NS*j + [rank*NB, (rank+1)*NB), inside [0, rows)
+          long long b0 = r0 + (long long)NS * j + (long long)rank * NB;
+          const long long b1 = b0 + NB;
+          if (b0 < 0) b0 = 0;
+          const uintptr_t lo = (reinterpret_cast<uintptr_t>(row + 2 * b0) + 15) & ~uintptr_t(15);
+          const uintptr_t hi = reinterpret_cast<uintptr_t>(row + 2 * b1) & ~uintptr_t(15);
+          if (b1 > 0 && hi > lo) prefetch_l2(reinterpret_cast<const void*>(lo), (uint32_t)(hi - lo));
+        }
+        prefetch_l2(a.chirp + (size_t)kn * N + (size_t)rank * NS, (uint32_t)(NS * sizeof(float2)));
+      }
+      segment(w);
+    }
+  } else {
+    segment((int)(blockIdx.x / CL));
   }
 }
 
@@ -651,8 +685,27 @@ cudaError_t launch_cluster_t(const OlsArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  const unsigned grid = (unsigned)((long long)a.n_chan * a.s_count * CL);
-  ols_cluster_kernel<LOGS, CL><<<grid, PassPlan<LOGS>::T, SMEM, s>>>(a);
+  // the kernel loops over segments: as many clusters as can be resident at once
+  const long long work = (long long)a.n_chan * a.s_count;
+  static int max_clusters[128] = {};
+  if (max_clusters[dev] == 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL * 148);
+    cfg.blockDim = dim3(PassPlan<LOGS>::T);
+    cfg.dynamicSmemBytes = SMEM;
+    int m = 0;
+    if (cudaOccupancyMaxActiveClusters(&m, (void*)ols_cluster_kernel<LOGS, CL>, &cfg) != cudaSuccess) {
+      cudaGetLastError();                   // no answer: one cluster per segment
+      m = 1 << 30;
+    }
+    max_clusters[dev] = m > 0 ? m : 1;
+  }
+  // Persistent clusters measured faster for pairs (N = 32768) and slower for
+  // clusters of four (N = 65536), which then run one segment each.
+  const long long cap = CL == 2 ? max_clusters[dev] : work;
+  const long long clusters = work < cap ? work : cap;
+  if (clusters <= 0) return cudaSuccess;
+  ols_cluster_kernel<LOGS, CL><<<(unsigned)(clusters * CL), PassPlan<LOGS>::T, SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
