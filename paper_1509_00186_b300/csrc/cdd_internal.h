@@ -73,7 +73,7 @@ cudaError_t launch_shift_table(int* shift, int n_chan, double f_base_mhz, double
                                double chan_bw_mhz, double dm, int n_avg, int sideband,
                                cudaStream_t s);
 
-// sum[p][m] = sum_k out[p][k][m] (channels added in order).
+// sum[p][m] = sum_k out[p][k][m] (a fixed summation order: deterministic).
 cudaError_t launch_band_sum(const float* out, long long n_planes, int n_chan, long long n_out,
                             float* sum, cudaStream_t s);
 // acc[i] += add[i], i < n.

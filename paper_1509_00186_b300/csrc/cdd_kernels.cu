@@ -576,7 +576,8 @@ __global__ void __launch_bounds__(256) corner_turn_kernel(const char2* __restric
   const unsigned short* src = reinterpret_cast<const unsigned short*>(in);
   unsigned short* dst = reinterpret_cast<unsigned short*>(out);
   const bool whole = r0 + kTT <= rows && c0 + kTT <= n_chan && (n_chan % 8) == 0 &&
-                     (stride % 8) == 0 && (r_begin % 8) == 0;
+                     (stride % 8) == 0 && (r_begin % 8) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
   auto sw = [](int r) { return ((r >> 3) & 15) << 1; };
   if (whole) {
     uint4 x[2];

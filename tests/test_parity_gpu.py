@@ -312,3 +312,23 @@ def test_band_sum_ragged_and_misaligned(cuda_device):
         shifted.copy_(torch.from_numpy(a))
         got2 = band_sum(shifted).cpu().numpy()
         assert np.array_equal(got2, got) or O.rel_rms(got2, got) <= 1e-6
+
+
+def test_unaligned_input_pointer(cuda_device):
+    """A caller's block that does not start on a 16-byte boundary (here 2
+    bytes past one) takes the corner turn's element-wise path and gives the
+    same bits as an aligned copy."""
+    import torch
+    from paper_1509_00186_b300.cdd import Plan
+    args = (313.0, 8.0, 128, 50.0, 8192, 16)
+    geo = O.plan_geometry(*args)
+    vin = complex_int8_voltages(22, 4 * geo.hop, 128, 20.0)
+    with Plan(*args, segments_per_block=4) as p:
+        a = p.execute(torch.from_numpy(vin).cuda()).cpu().numpy()
+    raw = torch.empty(vin.size + 2, dtype=torch.int8, device="cuda")
+    shifted = raw[2:].view(vin.shape)
+    assert shifted.data_ptr() % 16 == 2
+    shifted.copy_(torch.from_numpy(vin))
+    with Plan(*args, segments_per_block=4) as p:
+        b = p.execute(shifted).cpu().numpy()
+    assert np.array_equal(a, b)
