@@ -309,6 +309,25 @@ int cdd_pool_destroy(cdd_pool pool);
  * block counter.  Waits for the plan's outstanding work. */
 int cdd_reset(cdd_plan plan);
 
+/* Stream checkpoint (no counterpart in the paper; a real-time pipeline
+ * restarts a stream without losing its overlap and alignment state).  The
+ * state a stream carries between blocks is the last n_ov input samples of
+ * each channel (the overlap tail), the integrated samples whose aligned
+ * positions fall in later blocks (the last r_max entries of the alignment
+ * ring) and the stream position; for a two-polarisation plan, both.
+ *   cdd_plan_state_bytes: size of the blob (header + state), host side only.
+ *   cdd_plan_export_state: waits for `stream` (the plan's work must be on it),
+ *     then copies the state into host memory `state` of `bytes` >= the size.
+ *     A plan that has not run exports the state of a fresh stream.
+ *   cdd_plan_import_state: replaces the plan's stream state with a blob from
+ *     a plan of the same geometry (frequencies, bandwidth, channels, DM, N,
+ *     n_avg, segments per block, taper, polarisations), else CDD_EINVAL with
+ *     nothing changed; commits the plan if needed and waits for `stream`.
+ * Blocks run after an import continue the exported stream bit for bit. */
+int cdd_plan_state_bytes(cdd_plan plan, int64_t* bytes);
+int cdd_plan_export_state(cdd_plan plan, void* state, int64_t bytes, cudaStream_t stream);
+int cdd_plan_import_state(cdd_plan plan, const void* state, int64_t bytes, cudaStream_t stream);
+
 /* Free the plan and everything it owns (NULL is accepted). */
 int cdd_destroy(cdd_plan plan);
 

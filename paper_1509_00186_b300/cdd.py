@@ -44,7 +44,8 @@ EXPORTS = ("cdd_plan_create", "cdd_plan_set", "cdd_plan_get", "cdd_plan_shifts",
            "cdd_plan_commit", "cdd_execute_dual", "cdd_band_sum", "cdd_pool_create", "cdd_pool_admit", "cdd_pool_stream_get",
            "cdd_pool_submit", "cdd_pool_wait", "cdd_pool_release", "cdd_pool_get",
            "cdd_pool_destroy", "cdd_fullband_create", "cdd_fullband_set", "cdd_fullband_get",
-           "cdd_fullband_execute", "cdd_fullband_reset", "cdd_fullband_destroy")
+           "cdd_fullband_execute", "cdd_fullband_reset", "cdd_fullband_destroy",
+           "cdd_plan_state_bytes", "cdd_plan_export_state", "cdd_plan_import_state")
 
 
 class CddError(RuntimeError):
@@ -64,6 +65,9 @@ def _load() -> ctypes.CDLL:
     lib.cdd_plan_set.argtypes = [vp, ctypes.c_int, ctypes.c_int64]
     lib.cdd_plan_get.argtypes = [vp, ctypes.c_int, i64p]
     lib.cdd_plan_shifts.argtypes = [vp, i64p]
+    lib.cdd_plan_state_bytes.argtypes = [vp, i64p]
+    lib.cdd_plan_export_state.argtypes = [vp, vp, ctypes.c_int64, vp]
+    lib.cdd_plan_import_state.argtypes = [vp, vp, ctypes.c_int64, vp]
     lib.cdd_execute.argtypes = [vp, vp, vp, vp]
     lib.cdd_execute_voltages.argtypes = [vp, vp, vp, vp, vp]
     lib.cdd_execute_host.argtypes = [vp, vp, vp, vp]
@@ -153,6 +157,26 @@ def cdd_plan_shifts(plan: int, n_chan: int):
     buf = (ctypes.c_int64 * n_chan)()
     _check(_lib.cdd_plan_shifts(ctypes.c_void_p(plan), buf), "cdd_plan_shifts")
     return list(buf)
+
+
+def cdd_plan_state_bytes(plan: int) -> int:
+    v = ctypes.c_int64()
+    _check(_lib.cdd_plan_state_bytes(ctypes.c_void_p(plan), ctypes.byref(v)), "cdd_plan_state_bytes")
+    return v.value
+
+
+def cdd_plan_export_state(plan: int, stream: int = 0) -> bytes:
+    n = cdd_plan_state_bytes(plan)
+    buf = ctypes.create_string_buffer(n)
+    _check(_lib.cdd_plan_export_state(ctypes.c_void_p(plan), buf, n, ctypes.c_void_p(stream)),
+           "cdd_plan_export_state")
+    return buf.raw
+
+
+def cdd_plan_import_state(plan: int, state: bytes, stream: int = 0) -> None:
+    buf = ctypes.create_string_buffer(bytes(state), len(state))
+    _check(_lib.cdd_plan_import_state(ctypes.c_void_p(plan), buf, len(state), ctypes.c_void_p(stream)),
+           "cdd_plan_import_state")
 
 
 def cdd_execute(plan: int, d_in: int, d_out: int, stream: int = 0) -> None:
@@ -393,6 +417,18 @@ class Plan:
 
     def shifts(self):
         return cdd_plan_shifts(self.handle, self.n_chan)
+
+    def export_state(self) -> bytes:
+        """The stream's state after the blocks enqueued so far (waits for them)."""
+        import torch
+        return cdd_plan_export_state(self.handle, torch.cuda.current_stream().cuda_stream
+                                     if torch.cuda.is_available() else 0)
+
+    def import_state(self, state: bytes) -> None:
+        """Continue the stream that `state` was exported from."""
+        import torch
+        cdd_plan_import_state(self.handle, state, torch.cuda.current_stream().cuda_stream
+                              if torch.cuda.is_available() else 0)
 
     def _check_io(self, vin, out, device):
         import torch

@@ -620,6 +620,148 @@ int cdd_execute_host(cdd_plan p, const int8_t* h_in, float* h_out, cudaStream_t 
   return CDD_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+struct StateHeader {
+  uint32_t magic, version;
+  int32_t n_chan, n_fft, n_ov, hop, n_avg, q, pols, taper;
+  int64_t ring_len, r_max, g_next, g_next_b, blocks;
+  double f_center, bandwidth, dm;
+};
+constexpr uint32_t kStateMagic = 0x43444453u;     // "SDDC"
+constexpr uint32_t kStateVersion = 1;
+
+int64_t state_bytes(const cdd_plan p) {
+  const int64_t per_pol = (int64_t)p->n_chan * p->n_ov * (int64_t)sizeof(char2) +
+                          (int64_t)p->n_chan * p->r_max * (int64_t)sizeof(float);
+  return (int64_t)sizeof(StateHeader) + p->pols * per_pol;
+}
+
+StateHeader header_of(const cdd_plan p) {
+  StateHeader h = {};
+  h.magic = kStateMagic;
+  h.version = kStateVersion;
+  h.n_chan = p->n_chan;
+  h.n_fft = p->n_fft;
+  h.n_ov = p->n_ov;
+  h.hop = p->hop;
+  h.n_avg = p->n_avg;
+  h.q = p->q;
+  h.pols = p->pols;
+  h.taper = p->taper;
+  h.ring_len = p->r_max + n_out_per_block(p);
+  h.r_max = p->r_max;
+  h.f_center = p->f_center;
+  h.bandwidth = p->bandwidth;
+  h.dm = p->dm;
+  return h;
+}
+
+bool same_geometry(const StateHeader& a, const StateHeader& b) {
+  return a.magic == b.magic && a.version == b.version && a.n_chan == b.n_chan && a.n_fft == b.n_fft &&
+         a.n_ov == b.n_ov && a.hop == b.hop && a.n_avg == b.n_avg && a.q == b.q && a.pols == b.pols &&
+         a.taper == b.taper && a.ring_len == b.ring_len && a.r_max == b.r_max &&
+         a.f_center == b.f_center && a.bandwidth == b.bandwidth && a.dm == b.dm;
+}
+
+// The ring entries of stream indices [g_next - r_max, g_next) of every
+// channel: at most two column ranges of the [C][ring_len] ring.
+template <class F>
+int ring_window(cdd_plan p, long long g_next, F copy) {
+  const long long L = p->ring_len, rm = p->r_max;
+  if (rm == 0) return CDD_OK;
+  const long long start = ((g_next - rm) % L + L) % L;
+  const long long first = start + rm <= L ? rm : L - start;
+  int rc = copy(start, 0LL, first);
+  if (rc == CDD_OK && first < rm) rc = copy(0LL, first, rm - first);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cdd_plan_state_bytes(cdd_plan p, int64_t* bytes) {
+  if (!p || !bytes) return CDD_EINVAL;
+  *bytes = state_bytes(p);
+  return CDD_OK;
+}
+
+int cdd_plan_export_state(cdd_plan p, void* state, int64_t bytes, cudaStream_t s) {
+  if (!p || !state || bytes < state_bytes(p)) return CDD_EINVAL;
+  if (p->sticky) return p->sticky;
+  StateHeader h = header_of(p);
+  char* out = static_cast<char*>(state);
+  const size_t tb = (size_t)p->n_chan * p->n_ov * sizeof(char2);
+  const size_t rb = (size_t)p->n_chan * p->r_max * sizeof(float);
+  if (!p->committed) {                       // a fresh stream: zero history
+    h.g_next = h.g_next_b = h.blocks = 0;
+    memcpy(out, &h, sizeof(h));
+    memset(out + sizeof(h), 0, (size_t)(state_bytes(p) - (int64_t)sizeof(h)));
+    return CDD_OK;
+  }
+  int rc = check_device(p);
+  if (rc) return rc;
+  CDD_TRY(p, cudaStreamSynchronize(s));
+  h.g_next = p->g_next;
+  h.g_next_b = p->g_next_b;
+  h.blocks = p->blocks;
+  memcpy(out, &h, sizeof(h));
+  char* cur = out + sizeof(h);
+  for (int pol = 0; pol < p->pols; ++pol) {
+    const char2* tail = pol == 0 ? p->d_tail[p->parity] : p->d_tail_b[p->parity_b];
+    const float* ring = pol == 0 ? p->d_ring : p->d_ring_b;
+    const long long g = pol == 0 ? p->g_next : p->g_next_b;
+    if (tb) CDD_TRY(p, cudaMemcpy(cur, tail, tb, cudaMemcpyDeviceToHost));
+    float* rdst = reinterpret_cast<float*>(cur + tb);
+    rc = ring_window(p, g, [&](long long col, long long off, long long n) -> int {
+      CDD_TRY(p, cudaMemcpy2D(rdst + off, (size_t)p->r_max * sizeof(float), ring + col,
+                              (size_t)p->ring_len * sizeof(float), (size_t)n * sizeof(float),
+                              (size_t)p->n_chan, cudaMemcpyDeviceToHost));
+      return CDD_OK;
+    });
+    if (rc) return rc;
+    cur += tb + rb;
+  }
+  return CDD_OK;
+}
+
+int cdd_plan_import_state(cdd_plan p, const void* state, int64_t bytes, cudaStream_t s) {
+  if (!p || !state || bytes < state_bytes(p)) return CDD_EINVAL;
+  StateHeader h;
+  memcpy(&h, state, sizeof(h));
+  if (!same_geometry(h, header_of(p)) || h.g_next < 0 || h.g_next_b < 0 || h.blocks < 0)
+    return CDD_EINVAL;
+  int rc = prepare(p);
+  if (rc) return rc;
+  CDD_TRY(p, cudaStreamSynchronize(s));
+  const char* cur = static_cast<const char*>(state) + sizeof(h);
+  const size_t tb = (size_t)p->n_chan * p->n_ov * sizeof(char2);
+  const size_t rb = (size_t)p->n_chan * p->r_max * sizeof(float);
+  for (int pol = 0; pol < p->pols; ++pol) {
+    char2* tail = pol == 0 ? p->d_tail[0] : p->d_tail_b[0];
+    float* ring = pol == 0 ? p->d_ring : p->d_ring_b;
+    const long long g = pol == 0 ? h.g_next : h.g_next_b;
+    if (tb) CDD_TRY(p, cudaMemcpy(tail, cur, tb, cudaMemcpyHostToDevice));
+    const float* rsrc = reinterpret_cast<const float*>(cur + tb);
+    rc = ring_window(p, g, [&](long long col, long long off, long long n) -> int {
+      CDD_TRY(p, cudaMemcpy2D(ring + col, (size_t)p->ring_len * sizeof(float), rsrc + off,
+                              (size_t)p->r_max * sizeof(float), (size_t)n * sizeof(float),
+                              (size_t)p->n_chan, cudaMemcpyHostToDevice));
+      return CDD_OK;
+    });
+    if (rc) return rc;
+    cur += tb + rb;
+  }
+  p->g_next = h.g_next;
+  p->g_next_b = h.g_next_b;
+  p->parity = p->parity_b = 0;
+  p->blocks = h.blocks;
+  return CDD_OK;
+}
+
 int cdd_reset(cdd_plan p) {
   if (!p) return CDD_EINVAL;
   if (p->sticky) return p->sticky;

@@ -229,3 +229,26 @@ def test_fullband_rejects_bad_requests(cdd):
     with pytest.raises(cdd.CddError) as ei:                 # N = 2^28: beyond this build
         cdd.cdd_fullband_create(325.0, 32.0, 512, 200.0, 0, 16)
     assert ei.value.code == cdd.CDD_EUNSUPPORTED
+
+
+def test_stream_state_blob_before_any_launch(cdd):
+    """The checkpoint blob: its size, the fresh-stream export (no GPU touched),
+    and refusal of a blob from another geometry or of a short buffer."""
+    a = cdd.cdd_plan_create(325.0, 32.0, 64, 50.0, 8192, 16)
+    b = cdd.cdd_plan_create(325.0, 32.0, 64, 60.0, 8192, 16)         # another DM
+    try:
+        cdd.cdd_plan_set(a, "segments_per_block", 4)
+        cdd.cdd_plan_set(b, "segments_per_block", 4)
+        n = cdd.cdd_plan_state_bytes(a)
+        r_max, n_ov = cdd.cdd_plan_get(a, "r_max"), cdd.cdd_plan_get(a, "n_ov")
+        assert n > 64 * (2 * n_ov + 4 * r_max)
+        blob = cdd.cdd_plan_export_state(a)
+        assert len(blob) == n and blob[:4] == b"SDDC"
+        assert not any(blob[120:])                                  # zero history
+        for target, data in ((b, blob), (a, blob[:-1])):
+            with pytest.raises(cdd.CddError) as ei:
+                cdd.cdd_plan_import_state(target, data)
+            assert ei.value.code == cdd.CDD_EINVAL
+    finally:
+        cdd.cdd_destroy(a)
+        cdd.cdd_destroy(b)
