@@ -456,7 +456,7 @@ def _ols_flops(n_fft, segments):
 def row_plan_variant(args, dev, peaks, path):
     """lsb_hann: the GSB block as a lower-sideband band with the Hann taper.
     dual: the GSB block for two polarisations summed after detection.
-    precision: 150 MHz / DM 100 / N 65536 (a cluster of four CTAs per segment)."""
+    precision: 150 MHz / DM 100 / N 65536 (a cluster of eight CTAs per segment)."""
     import numpy as np
     import torch
     import oracle as O
@@ -489,7 +489,7 @@ def row_plan_variant(args, dev, peaks, path):
     samples = float(C) * rows * pols
     value = samples * args.steps / (total * 1e-3) / 1e6
     logn = int(math.log2(geo.n_fft))
-    kname = {"precision": "ols_cluster_kernel<14,4>"}.get(path, f"ols_persistent_kernel<{logn}>")
+    kname = {"precision": "ols_cluster_kernel<13,8>"}.get(path, f"ols_persistent_kernel<{logn}>")
     roof = _alu_roofline(kname, _ols_flops(geo.n_fft, C * q), kernel_ms, dev, peaks)
     roof["corner_turn_ms"] = st["corner_turn_ns"] / st["timed_blocks"] / 1e6
     cpu = None

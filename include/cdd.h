@@ -109,8 +109,8 @@ typedef struct cdd_plan_s* cdd_plan;
  *   f_center_mhz, bandwidth_mhz > 0: observing band (Sec. 2.1 f_o, Delta f).
  *   n_chan > 0: channels.  dm >= 0: dispersion measure in pc cm^-3 (Eq. 3).
  *   n_fft: FFT length N (power of two, 64..65536 in this build; above 16384
- *     a segment runs on a cluster of N/16384 CTAs and n_avg must be at most
- *     16384*16384/N), or 0 for the
+ *     a segment runs on a cluster of N/8192 CTAs and n_avg must be at most
+ *     8192*8192/N), or 0 for the
  *     Sec. 2.3 rule: the smallest power of two > 2*n_d (raised so that
  *     N > n_ov, N >= 2*n_avg and N >= 64).
  *   n_avg > 0: detected samples summed per output; h must be a multiple of it.

@@ -136,9 +136,10 @@ int geometry(Geometry* g, double f_center, double bandwidth, int n_chan, double 
     if (r > g->r_max) g->r_max = r;
   }
   if (logn < kMinLogN || logn > kMaxLogN) return CDD_EUNSUPPORTED;
-  // N > 16384 runs as a cluster of N/16384 CTAs; an integration window must not
-  // span two of them
-  if (logn > 14 && n_avg > (1 << 14) / (n_fft >> 14)) return CDD_EUNSUPPORTED;
+  // N > 16384 runs as a cluster of N/2^kClusterLogS CTAs, each holding every
+  // (N/2^kClusterLogS)-th sample run of 2^kClusterLogS/CL; an integration
+  // window must not span two of them
+  if (logn > 14 && n_avg > (1 << kClusterLogS) / (n_fft >> kClusterLogS)) return CDD_EUNSUPPORTED;
   return CDD_OK;
 }
 

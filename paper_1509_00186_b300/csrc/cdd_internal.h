@@ -67,6 +67,8 @@ cudaError_t launch_twiddle_table(int logn, float2* tw, cudaStream_t s);
 int twiddle_table_len(int logn);
 // N = 2^logn runs as a CTA cluster and reads only the channel-major copy.
 bool needs_channel_major(int logn);
+// log2 of the points one CTA of a cluster holds (N > 16384).
+constexpr int kClusterLogS = 13;
 
 // shift[k] = r_k for k < n_chan, computed on the device in FP64.
 cudaError_t launch_shift_table(int* shift, int n_chan, double f_base_mhz, double f_ref_mhz,

@@ -267,7 +267,9 @@ ols_persistent_kernel(const OlsArgs a) {
 // ------------------------------------------------------------------ clusters
 //
 // N = CL * 2^LOGS (32768 and 65536) does not fit one SM's shared memory, so a
-// cluster of CL CTAs holds one segment, 2^LOGS points per CTA.  A radix-CL pass
+// cluster of CL CTAs holds one segment, 2^LOGS points per CTA (2^13: the
+// 256-thread sub-transform of the single-CTA kernels, two CTAs per SM; CL = 4
+// and 8).  A radix-CL pass
 // across the cluster (DIF; inputs straight from global memory, outputs written
 // through distributed shared memory) leaves CTA r with the independent
 // sub-transform r (bins r + CL*b).  Each CTA then runs the single-CTA forward
@@ -275,7 +277,7 @@ ols_persistent_kernel(const OlsArgs a) {
 // the CL sub-results back across the cluster and the epilogue detects,
 // integrates and stores the CTA's quarter of the butterflies.
 template <int LOGS, int CL>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(PassPlan<LOGS>::T, 1)
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(PassPlan<LOGS>::T, PassPlan<LOGS>::T <= 256 ? 2 : 1)
 ols_cluster_kernel(const OlsArgs a) {
   namespace cg = cooperative_groups;
   using PL = PassPlan<LOGS>;
@@ -298,180 +300,159 @@ ols_cluster_kernel(const OlsArgs a) {
   constexpr int U = PERX * CL;
   const bool in_lanes = U == 32 && na <= 32 && (na & (na - 1)) == 0;
   cluster.sync();                        // every CTA of the cluster has started: DSMEM is live
-  // One segment per cluster: the body below.  Pairs (N = 32768) run as
-  // persistent clusters that loop over segments, each CTA asking L2 for its
-  // quarter of the next segment's input rows and chirp row while it works;
-  // clusters of four (N = 65536) run one segment each (measured faster).
-  const int n_clusters = (int)(gridDim.x / CL);
-  const int work = a.n_chan * a.s_count;
+  // One segment per cluster (a persistent form that loops over segments
+  // measured slower for clusters of eight and no faster for four).
   auto segment = [&](const int w) {
-  const int k = w % a.n_chan;
-  const int s = a.s_begin + w / a.n_chan;
+    const int k = w % a.n_chan;
+    const int s = a.s_begin + w / a.n_chan;
 
-  // ---- cross pass, forward: x[t + NS*j] -> DFT_CL -> w_N^{t*kk} -> CTA kk, index t
-  {
-    const long long row0 = (long long)s * a.hop - a.n_ov;
-    const unsigned short* src = reinterpret_cast<const unsigned short*>(a.in_cm) + (long long)k * a.rows;
-    const unsigned short* tail = reinterpret_cast<const unsigned short*>(a.tail_rd) + (long long)k * a.n_ov;
-    unsigned short* tail_out = reinterpret_cast<unsigned short*>(a.tail_wr) + (long long)k * a.n_ov;
-    const bool last = (s == a.q - 1) && a.n_ov > 0;
+    // ---- cross pass, forward: x[t + NS*j] -> DFT_CL -> w_N^{t*kk} -> CTA kk, index t
+    {
+      const long long row0 = (long long)s * a.hop - a.n_ov;
+      const unsigned short* src = reinterpret_cast<const unsigned short*>(a.in_cm) + (long long)k * a.rows;
+      const unsigned short* tail = reinterpret_cast<const unsigned short*>(a.tail_rd) + (long long)k * a.n_ov;
+      unsigned short* tail_out = reinterpret_cast<unsigned short*>(a.tail_wr) + (long long)k * a.n_ov;
+      const bool last = (s == a.q - 1) && a.n_ov > 0;
 #pragma unroll 2
+      for (int i = 0; i < PERX; ++i) {
+        const int t = rank * NB + lt + i * T;
+        unsigned short c[CL];
+#pragma unroll
+        for (int j = 0; j < CL; ++j) {
+          const long long row = row0 + t + (long long)NS * j;
+          c[j] = __ldg(row >= 0 ? src + row : tail + (row + a.n_ov));
+        }
+        float2 v[CL];
+#pragma unroll
+        for (int j = 0; j < CL; ++j) {
+          const int n = t + NS * j;
+          if (last && n >= N - a.n_ov) tail_out[n - (N - a.n_ov)] = c[j];
+          v[j] = unpack_i8x2(c[j]);
+        }
+        dft<CL, -1>(v);
+#pragma unroll
+        for (int kk = 1; kk < CL; ++kk) v[kk] = cmul(v[kk], __ldg(&twx[(kk - 1) * NS + t]));
+#pragma unroll
+        for (int kk = 0; kk < CL; ++kk) rbuf[kk][pad(t)] = v[kk];
+      }
+    }
+    cluster.sync();
+
+    // ---- sub-transform r of 2^LOGS points, all in this CTA (warp barriers
+    // around the chirp pass when the last two radices are equal)
+    constexpr bool kWarpMid = PL::P >= 3 && PL::R(PL::P - 2) == PL::RL && PL::RL <= 32;
+    static_for<0, PL::P - 1>([&](auto P_) {
+      constexpr int p = decltype(P_)::value;
+      fwd_pass<LOGS, p>(buf, a.tw, lt);
+      if constexpr (kWarpMid && p == PL::P - 2) __syncwarp();
+      else __syncthreads();
+    });
+    chirp_pass<LOGS>(buf, a.chirp + (size_t)k * N + (size_t)rank * NS, lt);
+    if constexpr (kWarpMid) __syncwarp();
+    else __syncthreads();
+    static_for<0, PL::P - 1>([&](auto I_) {
+      inv_pass<LOGS, PL::P - 2 - decltype(I_)::value>(buf, a.tw, lt);
+      __syncthreads();
+    });
+    cluster.sync();
+
+    // ---- cross pass, inverse: u_kk[t] from CTA kk -> w_N^{-t*kk} -> IDFT_CL -> z[t + NS*j]
+    float2 z[PERX][CL];
+#pragma unroll
     for (int i = 0; i < PERX; ++i) {
       const int t = rank * NB + lt + i * T;
-      unsigned short c[CL];
 #pragma unroll
-      for (int j = 0; j < CL; ++j) {
-        const long long row = row0 + t + (long long)NS * j;
-        c[j] = __ldg(row >= 0 ? src + row : tail + (row + a.n_ov));
-      }
-      float2 v[CL];
+      for (int kk = 0; kk < CL; ++kk) z[i][kk] = rbuf[kk][pad(t)];
 #pragma unroll
-      for (int j = 0; j < CL; ++j) {
-        const int n = t + NS * j;
-        if (last && n >= N - a.n_ov) tail_out[n - (N - a.n_ov)] = c[j];
-        v[j] = unpack_i8x2(c[j]);
-      }
-      dft<CL, -1>(v);
+      for (int kk = 1; kk < CL; ++kk) z[i][kk] = cmulc(z[i][kk], __ldg(&twx[(kk - 1) * NS + t]));
+      dft<CL, 1>(z[i]);
+      if (a.volt != nullptr) {
+        const long long vbase = ((long long)k * a.q + s) * a.hop - a.n_ov;
 #pragma unroll
-      for (int kk = 1; kk < CL; ++kk) v[kk] = cmul(v[kk], __ldg(&twx[(kk - 1) * NS + t]));
-#pragma unroll
-      for (int kk = 0; kk < CL; ++kk) rbuf[kk][pad(t)] = v[kk];
-    }
-  }
-  cluster.sync();
-
-  // ---- sub-transform r of 2^LOGS points, all in this CTA
-  static_for<0, PL::P - 1>([&](auto P_) {
-    fwd_pass<LOGS, decltype(P_)::value>(buf, a.tw, lt);
-    __syncthreads();
-  });
-  chirp_pass<LOGS>(buf, a.chirp + (size_t)k * N + (size_t)rank * NS, lt);
-  __syncthreads();
-  static_for<0, PL::P - 1>([&](auto I_) {
-    inv_pass<LOGS, PL::P - 2 - decltype(I_)::value>(buf, a.tw, lt);
-    __syncthreads();
-  });
-  cluster.sync();
-
-  // ---- cross pass, inverse: u_kk[t] from CTA kk -> w_N^{-t*kk} -> IDFT_CL -> z[t + NS*j]
-  float2 z[PERX][CL];
-#pragma unroll
-  for (int i = 0; i < PERX; ++i) {
-    const int t = rank * NB + lt + i * T;
-#pragma unroll
-    for (int kk = 0; kk < CL; ++kk) z[i][kk] = rbuf[kk][pad(t)];
-#pragma unroll
-    for (int kk = 1; kk < CL; ++kk) z[i][kk] = cmulc(z[i][kk], __ldg(&twx[(kk - 1) * NS + t]));
-    dft<CL, 1>(z[i]);
-    if (a.volt != nullptr) {
-      const long long vbase = ((long long)k * a.q + s) * a.hop - a.n_ov;
-#pragma unroll
-      for (int j = 0; j < CL; ++j) {
-        const int n = t + NS * j;
-        if (n >= a.n_ov) a.volt[vbase + n] = z[i][j];
-      }
-    }
-  }
-  cluster.sync();                        // no CTA reads another's buffer after this
-
-  const int n_int = a.hop / a.n_avg;
-  const int r = __ldg(&a.shift[k]);
-  const long long gseg = a.g0 + (long long)s * n_int;
-  float* outk = a.out + (size_t)k * a.n_out;
-  float* ringk = a.ring + (size_t)k * a.ring_len;
-  auto emit = [&](int n0, float acc) {      // the window starting at sample n0 >= n_ov
-    const long long gi = gseg + (n0 - a.n_ov) / a.n_avg;
-    const long long dst = gi + r - a.g0;
-    if (dst < a.n_out) outk[dst] = acc;
-    else ringk[gi % a.ring_len] = acc;
-  };
-  if (in_lanes) {
-    // ---- detect and integrate across lanes: a thread holds samples
-    // n = NS*j + rank*NB + lt + i*T, so a window is na neighbouring lanes
-    float u[U];
-#pragma unroll
-    for (int i = 0; i < PERX; ++i)
-#pragma unroll
-      for (int j = 0; j < CL; ++j) u[i * CL + j] = fmaf(z[i][j].x, z[i][j].x, z[i][j].y * z[i][j].y);
-    const int lane = lt & 31;
-    auto windows = [&](auto NA_) {
-      constexpr int NA = decltype(NA_)::value;
-      constexpr int V = U / NA;
-      lane_window_sums<U, NA>(u, lane);
-      const int lo = lane & (NA - 1);
-#pragma unroll
-      for (int q = 0; q < V; ++q) {
-        const int jj = V * lo + q;                    // flattened (i, j) of this sum
-        const int n0 = NS * (jj % CL) + rank * NB + (lt - lo) + (jj / CL) * T;
-        if (n0 >= a.n_ov) emit(n0, u[q]);
-      }
-    };
-    switch (na) {
-      case 1: windows(std::integral_constant<int, 1>{}); break;
-      case 2: windows(std::integral_constant<int, 2>{}); break;
-      case 4: windows(std::integral_constant<int, 4>{}); break;
-      case 8: windows(std::integral_constant<int, 8>{}); break;
-      case 16: windows(std::integral_constant<int, 16>{}); break;
-      default: windows(std::integral_constant<int, 32>{}); break;
-    }
-  } else {
-    // ---- detect into this CTA's buffer: (j, tt) -> j*NB + tt, one spare word per 32
-    float* pw = reinterpret_cast<float*>(buf);
-#pragma unroll
-    for (int i = 0; i < PERX; ++i) {
-#pragma unroll
-      for (int j = 0; j < CL; ++j) {
-        const int nl = j * NB + lt + i * T;
-        pw[nl + (nl >> 5)] = fmaf(z[i][j].x, z[i][j].x, z[i][j].y * z[i][j].y);
-      }
-    }
-    __syncthreads();
-    // ---- integrate, discard, align: n in [NS*j + rank*NB, NS*j + (rank+1)*NB)
-    const int per_j = NB / na;
-    for (int e = lt; e < CL * per_j; e += T) {
-      const int j = e / per_j, mm = e % per_j;
-      const int n0 = NS * j + rank * NB + mm * na;
-      if (n0 < a.n_ov) continue;                          // the overlap is discarded
-      const int nl0 = j * NB + mm * na;
-      float acc = 0.f;
-      for (int i = 0; i < na; ++i) acc += pw[(nl0 + i) + ((nl0 + i) >> 5)];
-      emit(n0, acc);
-    }
-  }
-  if (s == 0 && rank == 0) {
-    const int lim = r < a.n_out ? r : a.n_out;
-    for (int m = lt; m < lim; m += T) {
-      const long long src = a.g0 + m - r;
-      outk[m] = src >= 0 ? ringk[src % a.ring_len] : 0.f;
-    }
-  }
-  // The next forward cross pass writes into every CTA's buffer: with the
-  // shared-memory integration the buffers are still being read here.
-  if (!in_lanes) cluster.sync();
-  };
-  if constexpr (CL == 2) {
-    for (int w = (int)(blockIdx.x / CL); w < work; w += n_clusters) {
-      if (lt == 0 && w + n_clusters < work) {
-        const int wn = w + n_clusters;
-        const int kn = wn % a.n_chan;
-        const long long r0 = (long long)(a.s_begin + wn / a.n_chan) * a.hop - a.n_ov;
-        const char* row = reinterpret_cast<const char*>(a.in_cm + (long long)kn * a.rows);
-#pragma unroll
-        for (int j = 0; j < CL; ++j) {      // rows r0 + NS*j + [rank*NB, (rank+1)*NB), inside [0, rows)
-          long long b0 = r0 + (long long)NS * j + (long long)rank * NB;
-          const long long b1 = b0 + NB;
-          if (b0 < 0) b0 = 0;
-          const uintptr_t lo = (reinterpret_cast<uintptr_t>(row + 2 * b0) + 15) & ~uintptr_t(15);
-          const uintptr_t hi = reinterpret_cast<uintptr_t>(row + 2 * b1) & ~uintptr_t(15);
-          if (b1 > 0 && hi > lo) prefetch_l2(reinterpret_cast<const void*>(lo), (uint32_t)(hi - lo));
+        for (int j = 0; j < CL; ++j) {
+          const int n = t + NS * j;
+          if (n >= a.n_ov) a.volt[vbase + n] = z[i][j];
         }
-        prefetch_l2(a.chirp + (size_t)kn * N + (size_t)rank * NS, (uint32_t)(NS * sizeof(float2)));
       }
-      segment(w);
     }
-  } else {
-    segment((int)(blockIdx.x / CL));
-  }
+    cluster.sync();                        // no CTA reads another's buffer after this
+
+    const int n_int = a.hop / a.n_avg;
+    const int r = __ldg(&a.shift[k]);
+    const long long gseg = a.g0 + (long long)s * n_int;
+    float* outk = a.out + (size_t)k * a.n_out;
+    float* ringk = a.ring + (size_t)k * a.ring_len;
+    auto emit = [&](int n0, float acc) {      // the window starting at sample n0 >= n_ov
+      const long long gi = gseg + (n0 - a.n_ov) / a.n_avg;
+      const long long dst = gi + r - a.g0;
+      if (dst < a.n_out) outk[dst] = acc;
+      else ringk[gi % a.ring_len] = acc;
+    };
+    if (in_lanes) {
+      // ---- detect and integrate across lanes: a thread holds samples
+      // n = NS*j + rank*NB + lt + i*T, so a window is na neighbouring lanes
+      float u[U];
+#pragma unroll
+      for (int i = 0; i < PERX; ++i)
+#pragma unroll
+        for (int j = 0; j < CL; ++j) u[i * CL + j] = fmaf(z[i][j].x, z[i][j].x, z[i][j].y * z[i][j].y);
+      const int lane = lt & 31;
+      auto windows = [&](auto NA_) {
+        constexpr int NA = decltype(NA_)::value;
+        constexpr int V = U / NA;
+        lane_window_sums<U, NA>(u, lane);
+        const int lo = lane & (NA - 1);
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+          const int jj = V * lo + q;                    // flattened (i, j) of this sum
+          const int n0 = NS * (jj % CL) + rank * NB + (lt - lo) + (jj / CL) * T;
+          if (n0 >= a.n_ov) emit(n0, u[q]);
+        }
+      };
+      switch (na) {
+        case 1: windows(std::integral_constant<int, 1>{}); break;
+        case 2: windows(std::integral_constant<int, 2>{}); break;
+        case 4: windows(std::integral_constant<int, 4>{}); break;
+        case 8: windows(std::integral_constant<int, 8>{}); break;
+        case 16: windows(std::integral_constant<int, 16>{}); break;
+        default: windows(std::integral_constant<int, 32>{}); break;
+      }
+    } else {
+      // ---- detect into this CTA's buffer: (j, tt) -> j*NB + tt, one spare word per 32
+      float* pw = reinterpret_cast<float*>(buf);
+#pragma unroll
+      for (int i = 0; i < PERX; ++i) {
+#pragma unroll
+        for (int j = 0; j < CL; ++j) {
+          const int nl = j * NB + lt + i * T;
+          pw[nl + (nl >> 5)] = fmaf(z[i][j].x, z[i][j].x, z[i][j].y * z[i][j].y);
+        }
+      }
+      __syncthreads();
+      // ---- integrate, discard, align: n in [NS*j + rank*NB, NS*j + (rank+1)*NB)
+      const int per_j = NB / na;
+      for (int e = lt; e < CL * per_j; e += T) {
+        const int j = e / per_j, mm = e % per_j;
+        const int n0 = NS * j + rank * NB + mm * na;
+        if (n0 < a.n_ov) continue;                          // the overlap is discarded
+        const int nl0 = j * NB + mm * na;
+        float acc = 0.f;
+        for (int i = 0; i < na; ++i) acc += pw[(nl0 + i) + ((nl0 + i) >> 5)];
+        emit(n0, acc);
+      }
+    }
+    if (s == 0 && rank == 0) {
+      const int lim = r < a.n_out ? r : a.n_out;
+      for (int m = lt; m < lim; m += T) {
+        const long long src = a.g0 + m - r;
+        outk[m] = src >= 0 ? ringk[src % a.ring_len] : 0.f;
+      }
+    }
+    // The next forward cross pass writes into every CTA's buffer: with the
+    // shared-memory integration the buffers are still being read here.
+    if (!in_lanes) cluster.sync();
+  };
+  segment((int)(blockIdx.x / CL));
 }
 
 // Chirp table for a transform of CL * 2^LOGS points held as CL sub-transforms
@@ -686,25 +667,7 @@ cudaError_t launch_cluster_t(const OlsArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
-  // the kernel loops over segments: as many clusters as can be resident at once
-  const long long work = (long long)a.n_chan * a.s_count;
-  static int max_clusters[128] = {};
-  if (max_clusters[dev] == 0) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(CL * 148);
-    cfg.blockDim = dim3(PassPlan<LOGS>::T);
-    cfg.dynamicSmemBytes = SMEM;
-    int m = 0;
-    if (cudaOccupancyMaxActiveClusters(&m, (void*)ols_cluster_kernel<LOGS, CL>, &cfg) != cudaSuccess) {
-      cudaGetLastError();                   // no answer: one cluster per segment
-      m = 1 << 30;
-    }
-    max_clusters[dev] = m > 0 ? m : 1;
-  }
-  // Persistent clusters measured faster for pairs (N = 32768) and slower for
-  // clusters of four (N = 65536), which then run one segment each.
-  const long long cap = CL == 2 ? max_clusters[dev] : work;
-  const long long clusters = work < cap ? work : cap;
+  const long long clusters = (long long)a.n_chan * a.s_count;
   if (clusters <= 0) return cudaSuccess;
   ols_cluster_kernel<LOGS, CL><<<(unsigned)(clusters * CL), PassPlan<LOGS>::T, SMEM, s>>>(a);
   return cudaGetLastError();
@@ -729,8 +692,8 @@ cudaError_t launch_ols(int logn, const OlsArgs& a, cudaStream_t s) {
 #define X(L) case L: return launch_ols_t<L>(a, s);
     CDD_LOGN_CASES(X)
 #undef X
-    case 15: return launch_cluster_t<14, 2>(a, s);
-    case 16: return launch_cluster_t<14, 4>(a, s);
+    case 15: return launch_cluster_t<kClusterLogS, 4>(a, s);
+    case 16: return launch_cluster_t<kClusterLogS, 8>(a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -742,8 +705,8 @@ cudaError_t launch_chirp_table(int logn, float2* chirp, int n_chan, double f_bas
 #define X(L) case L: return launch_chirp_t<L, 1>(chirp, n_chan, f_base_mhz, chan_bw_mhz, dm, taper, sideband, s);
     CDD_LOGN_CASES(X)
 #undef X
-    case 15: return launch_chirp_t<14, 2>(chirp, n_chan, f_base_mhz, chan_bw_mhz, dm, taper, sideband, s);
-    case 16: return launch_chirp_t<14, 4>(chirp, n_chan, f_base_mhz, chan_bw_mhz, dm, taper, sideband, s);
+    case 15: return launch_chirp_t<kClusterLogS, 4>(chirp, n_chan, f_base_mhz, chan_bw_mhz, dm, taper, sideband, s);
+    case 16: return launch_chirp_t<kClusterLogS, 8>(chirp, n_chan, f_base_mhz, chan_bw_mhz, dm, taper, sideband, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -762,8 +725,8 @@ cudaError_t launch_twiddle_table(int logn, float2* tw, cudaStream_t s) {
 #define X(L) case L: return launch_twiddle_t<L, 1>(tw, s);
     CDD_LOGN_CASES(X)
 #undef X
-    case 15: return launch_twiddle_t<14, 2>(tw, s);
-    case 16: return launch_twiddle_t<14, 4>(tw, s);
+    case 15: return launch_twiddle_t<kClusterLogS, 4>(tw, s);
+    case 16: return launch_twiddle_t<kClusterLogS, 8>(tw, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -875,8 +838,8 @@ int twiddle_table_len(int logn) {
 #define X(L) case L: return twiddle_len_t<L, 1>();
     CDD_LOGN_CASES(X)
 #undef X
-    case 15: return twiddle_len_t<14, 2>();
-    case 16: return twiddle_len_t<14, 4>();
+    case 15: return twiddle_len_t<kClusterLogS, 4>();
+    case 16: return twiddle_len_t<kClusterLogS, 8>();
     default: return 0;
   }
 }

@@ -101,7 +101,7 @@ def test_invalid_geometry_is_rejected(cdd):
         cdd.cdd_plan_create(150.0, 32.0, 512, 100.0, 131072, 16)    # valid, not in this build
     assert ei.value.code == cdd.CDD_EUNSUPPORTED
     with pytest.raises(cdd.CddError) as ei:                         # window spans two CTAs
-        cdd.cdd_plan_create(150.0, 32.0, 512, 100.0, 65536, 8192)
+        cdd.cdd_plan_create(150.0, 32.0, 512, 100.0, 65536, 2048)
     assert ei.value.code in (cdd.CDD_EUNSUPPORTED, cdd.CDD_EINVAL)
 
 

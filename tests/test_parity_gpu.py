@@ -238,7 +238,7 @@ def test_gsb_full_size_sampled_channels(cuda_device):
 @pytest.mark.slow
 def test_precision_shape_full_size_sampled_channels(cuda_device):
     """The 32 MHz / 512-channel band at 150 MHz, DM 100, N 65536 (a cluster of
-    four CTAs per segment) at its full 10 s size, one block of 9 segments;
+    eight CTAs per segment) at its full 10 s size, one block of 9 segments;
     sampled channels against the oracle."""
     w = WORKLOADS["precision"]
     args = (w.f_center_mhz, w.bandwidth_mhz, w.n_chan, w.dm, w.n_fft, w.n_avg)
@@ -371,3 +371,20 @@ def test_checkpoint_resume_is_bit_identical(cuda_device, case):
         assert c.get("blocks_done") == 5
     for g, w in zip(got, want):
         assert np.array_equal(g, w)
+
+
+def test_cluster_window_at_the_limit(cuda_device):
+    """N = 65536 runs on clusters of eight 8192-point CTAs, each holding
+    1024-sample runs of the segment: n_avg = 1024 (integration through shared
+    memory, windows as long as a run) still matches the oracle."""
+    n, n_chan, n_avg = 65536, 3, 1024
+    chan_bw = 0.0625
+    dm = (n / 8) / O.dispersion_samples(317.0, chan_bw, 1.0)
+    args = (317.0 + n_chan * chan_bw / 2, n_chan * chan_bw, n_chan, dm, n, n_avg)
+    geo = O.plan_geometry(*args)
+    rng = np.random.default_rng(5)
+    T = 4 * geo.hop
+    vin = np.clip(np.rint(rng.normal(0, 20, (T, n_chan, 2))), -127, 127).astype(np.int8)
+    out_o, _ = oracle_run(vin, args, T)
+    out_g, _ = gpu_run(vin, args, 2, 2, volt=False)
+    assert np.all(rel_rms_rows(out_g, out_o) <= TOL)
