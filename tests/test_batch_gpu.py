@@ -74,3 +74,20 @@ def test_upgraded_gmrt_batch_full_size_sampled(cuda_device):
     for i, (d, k) in enumerate(pairs):
         want = O.dedisperse_batch(vin, g, channels=[k], dm_index=[d])[0, 0]
         assert O.rel_rms(got[i], want) <= TOL, (d, k)
+
+
+@pytest.mark.parametrize("n_avg", [32, 64])
+def test_batch_persistent_tiers(cuda_device, n_avg):
+    """Tiers of 8192 and 4096 points (the persistent batch kernel): n_avg 32
+    sums across lanes, 64 through shared memory; every DM plane against the
+    oracle, and a block split gives the same bits."""
+    args = (650.0, 1.5625, 16, [5.0, 10.0, 15.0], (8192, 4096), n_avg)
+    g = O.batch_geometry(*args)
+    h = g.hop(0)
+    vin = complex_int8_voltages(26, h * 4, 16, 20.0)
+    want = O.dedisperse_batch(vin, g)
+    got = run_batch(vin, args, 2, 2)
+    assert got.shape == want.shape
+    for d in range(len(args[3])):
+        assert O.rel_rms(got[d], want[d]) <= TOL, d
+    assert np.array_equal(run_batch(vin, args, 4, 1), got)

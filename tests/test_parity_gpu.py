@@ -388,3 +388,18 @@ def test_cluster_window_at_the_limit(cuda_device):
     out_o, _ = oracle_run(vin, args, T)
     out_g, _ = gpu_run(vin, args, 2, 2, volt=False)
     assert np.all(rel_rms_rows(out_g, out_o) <= TOL)
+
+
+@pytest.mark.parametrize("n_avg", [1, 32, 64, 256])
+def test_integration_lengths_n8192(cuda_device, n_avg):
+    """N = 8192 (the persistent kernel): n_avg 1 and 32 sum across lanes, 64 and
+    256 go through the shared-memory buffer (and the barrier that ends each
+    segment); all against the oracle over two blocks, split and whole alike."""
+    args = (313.0, 2.0, 32, 50.0, 8192, n_avg)
+    geo = O.plan_geometry(*args)
+    vin = complex_int8_voltages(25, 6 * geo.hop, 32, 20.0)
+    out_o, _ = oracle_run(vin, args, 6 * geo.hop)
+    whole, _ = gpu_run(vin, args, 6, 1, volt=False)
+    split, _ = gpu_run(vin, args, 3, 2, volt=False)
+    assert np.array_equal(split, whole)
+    assert np.all(rel_rms_rows(whole, out_o) <= TOL)
