@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "dedispersed Msamples/s, ×real-time, % HBM roofline; block p99 latency"
 WORKLOAD = "gsb"
-SAMPLE_CHANNELS = 192            # CPU baseline: channels of the full block (~10-20 s)
+SAMPLE_CHANNELS = 512            # CPU baseline: the whole block, threads over channels
 KERNEL_SOURCES = ("paper_1509_00186_b300/csrc/cdd_kernels.cu", "paper_1509_00186_b300/csrc/cdd_fft.cuh",
                   "paper_1509_00186_b300/csrc/cdd_passes.cuh")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ols_kernel_gsb_traffic.json")
@@ -172,19 +172,36 @@ def barrier(world: int) -> None:
 
 # ---------------------------------------------------------------- CPU oracle
 
+def oracle_threads() -> int:
+    """Host threads for the oracle: numpy's FFT and element-wise loops release
+    the GIL, so channels dedisperse in parallel threads (no copies)."""
+    return max(1, min(os.cpu_count() or 1, 64))
+
+
+def oracle_channels(vin, geo, channels, threads: int, taper: str = "none"):
+    """The oracle as it stands, over `channels` split round-robin across threads."""
+    import oracle as O
+    from concurrent.futures import ThreadPoolExecutor
+    chans = list(channels)
+    parts = [chans[i::threads] for i in range(threads) if chans[i::threads]]
+    with ThreadPoolExecutor(len(parts)) as ex:
+        list(ex.map(lambda c: O.dedisperse(vin, geo, taper, channels=c), parts))
+
+
 def cpu_oracle_rate(w, vin, n_channels: int) -> dict:
-    """The FP64 oracle as it stands, on the first n_channels channels of the
-    block: Msamples/s and what it ran on."""
+    """The FP64 oracle as it stands on the first n_channels channels of the
+    block, threads over channels: Msamples/s and what it ran on."""
     import oracle as O
     geo = O.plan_geometry(w.f_center_mhz, w.bandwidth_mhz, w.n_chan, w.dm, w.n_fft, w.n_avg)
+    threads = oracle_threads()
     t0 = time.perf_counter()
-    O.dedisperse(vin, geo, channels=range(n_channels))
+    oracle_channels(vin, geo, range(n_channels), threads)
     dt = time.perf_counter() - t0
     samples = n_channels * (vin.shape[0] // geo.hop) * geo.hop
-    return {"value": samples / dt / 1e6, "unit": "Msamples/s", "cores": 1, "kind": "oracle",
+    return {"value": samples / dt / 1e6, "unit": "Msamples/s", "cores": threads, "kind": "oracle",
             "seconds": dt,
             "sample": f"{n_channels} of {w.n_chan} channels x {vin.shape[0]} samples "
-                      f"(one block), numpy FP64, single thread"}
+                      f"(one block), numpy FP64, {threads} threads over channels"}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -200,14 +217,15 @@ def run_reference(args, world, rank):
     rows = q * geo.hop
     from synth import complex_int8_voltages as gen
     vin = gen(w.seed, rows, w.n_chan, w.sigma)
-    per_step = 8                                 # channels per step: ~0.5 s of CPU work
+    threads = oracle_threads()
+    per_step = min(w.n_chan, 2 * threads)        # channels per step: well under a second of wall time
     for _ in range(args.warmup):
-        O.dedisperse(vin, geo, channels=range(per_step))
+        oracle_channels(vin, geo, range(per_step), threads)
     times = []
     for s in range(args.steps):
         ch = [(s * per_step + i) % w.n_chan for i in range(per_step)]
         t0 = time.perf_counter()
-        O.dedisperse(vin, geo, channels=ch)
+        oracle_channels(vin, geo, ch, threads)
         times.append(time.perf_counter() - t0)
     samples = per_step * rows
     total = sum(times)
@@ -218,8 +236,9 @@ def run_reference(args, world, rank):
         "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_dict(w, q, geo.hop),
-        "cpu_baseline": {"value": value, "unit": "Msamples/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{per_step} channels of one {rows}-sample block per step"},
+        "cpu_baseline": {"value": value, "unit": "Msamples/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{per_step} channels of one {rows}-sample block per step, "
+                                   f"{threads} threads over channels"},
         "e2e": {"value": value, "unit": "Msamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -494,12 +513,14 @@ def row_plan_variant(args, dev, peaks, path):
     roof["corner_turn_ms"] = st["corner_turn_ns"] / st["timed_blocks"] / 1e6
     cpu = None
     if not args.no_cpu_baseline:
-        n_cpu = {"precision": 16, "dual": 48}.get(path, 96)
-        dt = _cpu_time(lambda: [O.dedisperse(v, geo, taper, channels=range(n_cpu))
+        threads = oracle_threads()
+        n_cpu = min(C, {"precision": 4, "dual": 4}.get(path, 8) * threads)
+        dt = _cpu_time(lambda: [oracle_channels(v, geo, range(n_cpu), threads, taper)
                                 for v in ((va, vb) if pols == 2 else (va,))])
-        cpu = {"value": n_cpu * q * geo.hop * pols / dt / 1e6, "unit": "Msamples/s", "cores": 1,
+        cpu = {"value": n_cpu * q * geo.hop * pols / dt / 1e6, "unit": "Msamples/s", "cores": threads,
                "kind": "oracle", "seconds": dt,
-               "sample": f"{n_cpu} of {C} channels x {q * geo.hop} samples x {pols} polarisation(s)"}
+               "sample": f"{n_cpu} of {C} channels x {q * geo.hop} samples x {pols} polarisation(s), "
+                         f"{threads} threads over channels"}
     wl = f"{w.f_center_mhz:g}MHz-{abs(bw):g}MHz-{'LSB' if bw < 0 else 'USB'}-{C}ch-DM{w.dm:g}-N{geo.n_fft}-x{w.n_avg}"
     config = {"workload": f"{path}:{wl}", "taper": taper, "polarisations": pols,
               "segments_per_block": q, "block_samples_per_channel": rows}
@@ -579,10 +600,19 @@ def row_batch(args, dev, peaks):
     cpu = None
     if not args.no_cpu_baseline:
         geo = O.batch_geometry(650.0, 200.0, C, dms, tiers, n_avg)
-        chans = [0, 512, 1024, 1536]
-        dt = _cpu_time(lambda: O.dedisperse_batch(vin, geo, channels=chans))
-        cpu = {"value": len(chans) * bs / dt / 1e6, "unit": "Msamples/s", "cores": 1, "kind": "oracle",
-               "seconds": dt, "sample": f"channels {chans} (one per tier) x {bs} samples x {len(dms)} DMs"}
+        threads = oracle_threads()
+        per_tier = max(1, threads // 4)
+        chans = [t * 512 + i for t in range(4) for i in range(per_tier)]
+        from concurrent.futures import ThreadPoolExecutor
+        parts = [chans[i::threads] for i in range(threads) if chans[i::threads]]
+
+        def run_parts():
+            with ThreadPoolExecutor(len(parts)) as ex:
+                list(ex.map(lambda c: O.dedisperse_batch(vin, geo, channels=c), parts))
+        dt = _cpu_time(run_parts)
+        cpu = {"value": len(chans) * bs / dt / 1e6, "unit": "Msamples/s", "cores": threads, "kind": "oracle",
+               "seconds": dt, "sample": f"{len(chans)} channels ({per_tier} per tier) x {bs} samples x "
+                                        f"{len(dms)} DMs, {threads} threads over channels"}
     config = {"workload": f"batch:650MHz-200MHz-{C}ch-{len(dms)}DM-N16384/8192/4096/2048-x{n_avg}",
               "block_samples_per_channel": bs, "dm_trials": len(dms)}
     return _line("batch", args, "input Msamples/s through all DM trials", value, "Msamples/s", ms,
