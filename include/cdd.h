@@ -294,7 +294,15 @@ int cdd_pool_admit(cdd_pool pool, double f_center_mhz, double bandwidth_mhz, int
                    int* stream_id);
 /* Plan attributes of a stream, plus CDD_ATTR_SEQ_GAPS. */
 int cdd_pool_stream_get(cdd_pool pool, int stream_id, int attr, int64_t* value);
-/* Enqueue block `seq` of a stream: d_in, d_out as for cdd_execute.  Returns at
+
+/* Checkpoint of an admitted stream (see cdd_plan_export_state): the plan's
+ * stream state after the stream's submitted blocks (waits for them), and the
+ * next sequence number the pool expects.  Import into an admitted stream of
+ * the same geometry in this or another pool, with the sequence number to
+ * continue from; the stream then resumes bit for bit. */
+int cdd_pool_stream_state_bytes(cdd_pool pool, int stream_id, int64_t* bytes);
+int cdd_pool_stream_export(cdd_pool pool, int stream_id, void* state, int64_t bytes, int64_t* next_seq);
+int cdd_pool_stream_import(cdd_pool pool, int stream_id, const void* state, int64_t bytes, int64_t next_seq);/* Enqueue block `seq` of a stream: d_in, d_out as for cdd_execute.  Returns at
  * once with a ticket for cdd_pool_wait. */
 int cdd_pool_submit(cdd_pool pool, int stream_id, int64_t seq, const int8_t* d_in, float* d_out,
                     int64_t* ticket);

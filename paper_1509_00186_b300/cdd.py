@@ -45,7 +45,8 @@ EXPORTS = ("cdd_plan_create", "cdd_plan_set", "cdd_plan_get", "cdd_plan_shifts",
            "cdd_pool_submit", "cdd_pool_wait", "cdd_pool_release", "cdd_pool_get",
            "cdd_pool_destroy", "cdd_fullband_create", "cdd_fullband_set", "cdd_fullband_get",
            "cdd_fullband_execute", "cdd_fullband_reset", "cdd_fullband_destroy",
-           "cdd_plan_state_bytes", "cdd_plan_export_state", "cdd_plan_import_state")
+           "cdd_plan_state_bytes", "cdd_plan_export_state", "cdd_plan_import_state",
+           "cdd_pool_stream_state_bytes", "cdd_pool_stream_export", "cdd_pool_stream_import")
 
 
 class CddError(RuntimeError):
@@ -68,6 +69,9 @@ def _load() -> ctypes.CDLL:
     lib.cdd_plan_state_bytes.argtypes = [vp, i64p]
     lib.cdd_plan_export_state.argtypes = [vp, vp, ctypes.c_int64, vp]
     lib.cdd_plan_import_state.argtypes = [vp, vp, ctypes.c_int64, vp]
+    lib.cdd_pool_stream_state_bytes.argtypes = [vp, ctypes.c_int, i64p]
+    lib.cdd_pool_stream_export.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64, i64p]
+    lib.cdd_pool_stream_import.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int64]
     lib.cdd_execute.argtypes = [vp, vp, vp, vp]
     lib.cdd_execute_voltages.argtypes = [vp, vp, vp, vp, vp]
     lib.cdd_execute_host.argtypes = [vp, vp, vp, vp]
@@ -375,6 +379,24 @@ def cdd_pool_get(pool: int, attr) -> int:
     v = ctypes.c_int64()
     _check(_lib.cdd_pool_get(ctypes.c_void_p(pool), a, ctypes.byref(v)), "cdd_pool_get")
     return int(v.value)
+
+
+def cdd_pool_stream_export(pool: int, stream_id: int):
+    """(state bytes, next sequence number) of an admitted stream."""
+    n = ctypes.c_int64()
+    _check(_lib.cdd_pool_stream_state_bytes(ctypes.c_void_p(pool), int(stream_id), ctypes.byref(n)),
+           "cdd_pool_stream_state_bytes")
+    buf = ctypes.create_string_buffer(n.value)
+    seq = ctypes.c_int64()
+    _check(_lib.cdd_pool_stream_export(ctypes.c_void_p(pool), int(stream_id), buf, n.value, ctypes.byref(seq)),
+           "cdd_pool_stream_export")
+    return buf.raw, seq.value
+
+
+def cdd_pool_stream_import(pool: int, stream_id: int, state: bytes, next_seq: int) -> None:
+    buf = ctypes.create_string_buffer(bytes(state), len(state))
+    _check(_lib.cdd_pool_stream_import(ctypes.c_void_p(pool), int(stream_id), buf, len(state), int(next_seq)),
+           "cdd_pool_stream_import")
 
 
 def cdd_pool_destroy(pool: int) -> None:

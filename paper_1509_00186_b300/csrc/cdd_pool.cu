@@ -197,6 +197,41 @@ int cdd_pool_wait(cdd_pool p, int64_t ticket, double* latency_ms) {
   return rc;
 }
 
+int cdd_pool_stream_state_bytes(cdd_pool p, int id, int64_t* bytes) {
+  if (!p || !bytes) return CDD_EINVAL;
+  std::lock_guard<std::mutex> lock(p->mu);
+  if (id < 0 || id >= (int)p->slots.size() || !p->slots[id].used) return CDD_EINVAL;
+  return cdd_plan_state_bytes(p->slots[id].plan, bytes);
+}
+
+int cdd_pool_stream_export(cdd_pool p, int id, void* state, int64_t bytes, int64_t* next_seq) {
+  if (!p || !state || !next_seq) return CDD_EINVAL;
+  std::lock_guard<std::mutex> lock(p->mu);
+  if (id < 0 || id >= (int)p->slots.size() || !p->slots[id].used) return CDD_EINVAL;
+  Slot& sl = p->slots[id];
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(p->device);
+  const int rc = cdd_plan_export_state(sl.plan, state, bytes, sl.stream);
+  if (prev >= 0) cudaSetDevice(prev);
+  if (rc == CDD_OK) *next_seq = sl.next_seq;
+  return rc;
+}
+
+int cdd_pool_stream_import(cdd_pool p, int id, const void* state, int64_t bytes, int64_t next_seq) {
+  if (!p || !state || next_seq < 0) return CDD_EINVAL;
+  std::lock_guard<std::mutex> lock(p->mu);
+  if (id < 0 || id >= (int)p->slots.size() || !p->slots[id].used) return CDD_EINVAL;
+  Slot& sl = p->slots[id];
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(p->device);
+  const int rc = cdd_plan_import_state(sl.plan, state, bytes, sl.stream);
+  if (prev >= 0) cudaSetDevice(prev);
+  if (rc == CDD_OK) sl.next_seq = next_seq;
+  return rc;
+}
+
 int cdd_pool_release(cdd_pool p, int id) {
   if (!p) return CDD_EINVAL;
   Slot sl;

@@ -100,6 +100,14 @@ class Pool:
     def release(self, sid):
         cdd.cdd_pool_release(self.handle, sid)
 
+    def export_stream(self, sid):
+        """(state, next sequence number) of a stream after its submitted blocks."""
+        return cdd.cdd_pool_stream_export(self.handle, sid)
+
+    def import_stream(self, sid, state, next_seq):
+        """Continue an exported stream in the admitted stream `sid`."""
+        cdd.cdd_pool_stream_import(self.handle, sid, state, next_seq)
+
     def used_bytes(self) -> int:
         return cdd.cdd_pool_get(self.handle, "used_bytes")
 

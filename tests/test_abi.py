@@ -252,3 +252,4 @@ def test_stream_state_blob_before_any_launch(cdd):
     finally:
         cdd.cdd_destroy(a)
         cdd.cdd_destroy(b)
+

@@ -73,3 +73,47 @@ def test_gsb_and_upgraded_gmrt_mix_meets_the_deadline(cuda_device):
     assert summary["streams_admitted"] == 8
     assert summary["missed_deadlines"] == 0
     assert summary["latency_ms"]["p99"] < summary["deadline_ms"]["min"] / 20
+
+
+def test_stream_moves_to_another_pool(cuda_device):
+    """A stream checkpointed after three blocks (state and next sequence number)
+    and imported into a stream of another pool continues bit for bit: its
+    outputs equal those of the stream run without interruption."""
+    import torch
+    from paper_1509_00186_b300.serving import Pool, make_block_inputs, run_alone
+    sp = small_specs()[1]
+    n_blocks = 6
+    want = run_alone(sp, n_blocks)
+    with Pool(8 << 30, max_streams=2) as first, Pool(8 << 30, max_streams=2) as second:
+        a = first.admit(sp)
+        bs = first.get(a, "block_samples")
+        n_out = first.get(a, "n_out_per_block")
+        x = torch.from_numpy(make_block_inputs(sp, bs, n_blocks)).cuda()
+        outs = torch.empty((n_blocks, sp.n_chan, n_out), device="cuda")
+        for b in range(3):
+            first.wait(first.submit(a, b, x[b * bs:(b + 1) * bs], outs[b]))
+        state, seq = first.export_stream(a)
+        assert seq == 3
+        first.release(a)
+        c = second.admit(sp)
+        second.import_stream(c, state, seq)
+        for b in range(3, n_blocks):
+            second.wait(second.submit(c, b, x[b * bs:(b + 1) * bs], outs[b]))
+        assert second.get(c, "seq_gaps") == 0
+        assert np.array_equal(outs.cpu().numpy(), want)
+
+
+def test_pool_checkpoint_refusals(cuda_device):
+    """Pool checkpoints refuse unknown streams and negative sequence numbers."""
+    from paper_1509_00186_b300 import cdd
+    from paper_1509_00186_b300.serving import Pool
+    with Pool(1 << 30, max_streams=2) as pool:
+        with pytest.raises(cdd.CddError) as ei:
+            pool.export_stream(0)
+        assert ei.value.code == cdd.CDD_EINVAL
+        sid = pool.admit(small_specs()[0])
+        state, seq = pool.export_stream(sid)
+        for bad_sid, bad_seq in ((1, 0), (sid, -1)):
+            with pytest.raises(cdd.CddError) as ei:
+                pool.import_stream(bad_sid, state, bad_seq)
+            assert ei.value.code == cdd.CDD_EINVAL
