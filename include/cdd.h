@@ -95,10 +95,13 @@ enum cdd_attr {
   CDD_ATTR_TIMED_BLOCKS = 18,      /* blocks timed so far (stage timing on)    */
   CDD_ATTR_CORNER_TURN_NS = 19,    /* summed device time of the corner turns
                                       of the timed blocks, nanoseconds         */
-  CDD_ATTR_OLS_NS = 20             /* summed device time of the fused segment
+  CDD_ATTR_OLS_NS = 20,            /* summed device time of the fused segment
                                       kernels of the timed blocks, ns.  Reading
                                       18..20 waits for the timed blocks still
                                       in flight; the sums never reset.         */
+  CDD_ATTR_PHASE_FLOATS = 22       /* batch only: 1 when the DM = 1 chirp phase
+                                      table is single floats (no chirp phase
+                                      above 16 turns), else 2 (two floats)     */
 };
 
 enum cdd_taper { CDD_TAPER_NONE = 0, CDD_TAPER_HANN = 1, CDD_TAPER_WELCH = 2 };
@@ -229,7 +232,8 @@ int cdd_batch_create(cdd_batch* batch, double f_center_mhz, double bandwidth_mhz
 /* Only CDD_ATTR_SEGMENTS_PER_BLOCK, before the first execute. */
 int cdd_batch_set(cdd_batch batch, int attr, int64_t value);
 /* SEGMENTS_PER_BLOCK, BLOCK_SAMPLES, N_OUT_PER_BLOCK, R_MAX, BYTES_DEVICE,
- * BLOCKS_DONE, KERNEL_LAUNCHES, N_CHAN, N_AVG, HOP (the longest hop). */
+ * BLOCKS_DONE, KERNEL_LAUNCHES, N_CHAN, N_AVG, HOP (the longest hop),
+ * PHASE_FLOATS. */
 int cdd_batch_get(cdd_batch batch, int attr, int64_t* value);
 /* Geometry of tier t (any output pointer may be NULL). */
 int cdd_batch_tier(cdd_batch batch, int t, int64_t* n_fft, int64_t* n_ov, int64_t* first_chan,

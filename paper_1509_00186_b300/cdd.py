@@ -30,7 +30,7 @@ ATTR = {
     "block_samples": 6, "n_out_per_block": 7, "r_max": 8, "bytes_device": 9, "taper": 10,
     "blocks_done": 11, "pipeline_chunks": 12, "kernel_launches": 13, "bytes_needed": 14,
     "seq_gaps": 15, "polarisations": 16, "stage_timing": 17, "timed_blocks": 18,
-    "corner_turn_ns": 19, "ols_ns": 20,
+    "corner_turn_ns": 19, "ols_ns": 20, "phase_floats": 22,
 }
 POOL_ATTR = {"budget": 100, "used_bytes": 101, "streams": 102}
 TAPER = {"none": 0, "hann": 1, "welch": 2}

@@ -33,6 +33,7 @@ struct BatchArgs {
   long long rows;
   float* out;               // [n_dm][C][n_out]
   const float2* t1;         // [n_tchan][N] DM = 1 chirp phase in turns (hi, lo), chirp-pass order
+  const float* t1f;         // the same as single floats when every phase is small (else nullptr)
   const float2* tw;         // twiddles of this N
   const char2* tail_rd;     // [C][tail_stride] last samples of the previous block
   char2* tail_wr;
@@ -60,7 +61,19 @@ __device__ __forceinline__ float2 dm_chirp(float2 t1, float2 dm) {
 // spectrum to its scratch row, then every DM trial.  SH: tw is in shared
 // memory.  sync() is the group's barrier.  Returns true when buf (the power
 // samples) was read after the last barrier.
-template <int LOGN, bool SH, class Sync>
+// The same with the DM = 1 phase as one float: used when no phase exceeds
+// 16 turns, so its rounding (2^-24 relative) stays below 6e-6 rad.
+__device__ __forceinline__ float2 dm_chirp1(float t1, float2 dm) {
+  const float p = dm.x * t1;
+  const float e = fmaf(dm.x, t1, -p);
+  const float lo = fmaf(dm.y, t1, e);
+  const float frac = (p - rintf(p)) + lo;
+  float sn, cs;
+  __sincosf(6.28318530717958647692f * frac, &sn, &cs);
+  return make_float2(cs, -sn);
+}
+
+template <int LOGN, bool SH, bool T1F, class Sync>
 __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, const float2* tw, int lt,
                                               bool active, int w, Sync sync) {
   using PL = PassPlan<LOGN>;
@@ -141,6 +154,7 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
   }
 
   const float2* t1k = a.t1 + (size_t)kt * N;
+  const float* t1fk = a.t1f + (size_t)kt * N;
   const int na = a.n_avg;
   const int n_int = a.hop / na;
   bool in_lanes = false;
@@ -158,7 +172,8 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
         float2 x[RL];
 #pragma unroll
         for (int kk = 0; kk < RL; ++kk)
-          x[kk] = cmul(xk[kk * NG + q], dm_chirp(__ldg(&t1k[kk * NG + q]), dm));
+          x[kk] = cmul(xk[kk * NG + q], T1F ? dm_chirp1(__ldg(&t1fk[kk * NG + q]), dm)
+                                            : dm_chirp(__ldg(&t1k[kk * NG + q]), dm));
         dft<RL, 1>(x);
         float2* pb = buf + pad(q * RL);
 #pragma unroll
@@ -220,7 +235,7 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
   return !in_lanes;
 }
 
-template <int LOGN>
+template <int LOGN, bool T1F>
 __global__ void __launch_bounds__(Cfg<LOGN>::THREADS, Cfg<LOGN>::MINB)
 batch_kernel(const BatchArgs a) {
   using PL = PassPlan<LOGN>;
@@ -231,7 +246,7 @@ batch_kernel(const BatchArgs a) {
   float2* buf = smem + g * CF::SEG_F2;
   const int w = blockIdx.x * CF::G + g;
   const bool active = w < a.n_tchan * a.q;
-  batch_segment<LOGN, false>(a, buf, a.tw, lt, active, w, [] { __syncthreads(); });
+  batch_segment<LOGN, false, T1F>(a, buf, a.tw, lt, active, w, [] { __syncthreads(); });
 }
 
 // Persistent form for N = 4096 and 8192: one CTA per SM, two groups of 256
@@ -246,7 +261,7 @@ struct BatchPersist {
   static constexpr size_t SMEM = (size_t(PL::TW_LEN) + size_t(GROUPS) * padded_len(PL::N)) * sizeof(float2);
 };
 
-template <int LOGN>
+template <int LOGN, bool T1F>
 __global__ void __launch_bounds__(BatchPersist<LOGN>::THREADS, 1)
 batch_persistent_kernel(const BatchArgs a) {
   using PL = PassPlan<LOGN>;
@@ -263,7 +278,7 @@ batch_persistent_kernel(const BatchArgs a) {
   auto sync = [bar] { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(T) : "memory"); };
   const int work = a.n_tchan * a.q;
   for (int w = blockIdx.x * BP::GROUPS + g; w < work; w += gridDim.x * BP::GROUPS) {
-    if (batch_segment<LOGN, true>(a, buf, tws, lt, true, w, sync))
+    if (batch_segment<LOGN, true, T1F>(a, buf, tws, lt, true, w, sync))
       sync();                                  // buf is rewritten by the next work item
   }
 }
@@ -271,7 +286,7 @@ batch_persistent_kernel(const BatchArgs a) {
 // T1[kt][idx]: Eq. 3 phase in turns at DM = 1 for channel chan0 + kt and the
 // bin held at table index idx (FP64, split into two floats).
 template <int LOGN>
-__global__ void t1_table_kernel(float2* t1, int n_tchan, int chan0, double f_lo0, double chan_bw) {
+__global__ void t1_table_kernel(float2* t1, float* t1f, int n_tchan, int chan0, double f_lo0, double chan_bw) {
   using PL = PassPlan<LOGN>;
   constexpr int N = PL::N;
   constexpr int NG = N / PL::RL;
@@ -287,12 +302,13 @@ __global__ void t1_table_kernel(float2* t1, int n_tchan, int chan0, double f_lo0
     const double f_l = sbin * (chan_bw / N) + 0.5 * chan_bw;
     const double turns = kDispD * 1e6 * f_l * f_l / ((f_l + f_lo) * f_lo * f_lo);
     const float hi = (float)turns;
-    t1[e] = make_float2(hi, (float)(turns - (double)hi));
+    if (t1f) t1f[e] = hi;
+    else t1[e] = make_float2(hi, (float)(turns - (double)hi));
   }
 }
 
-template <int LOGN>
-cudaError_t launch_batch_t(const BatchArgs& a, cudaStream_t s) {
+template <int LOGN, bool T1F>
+cudaError_t launch_batch_tt(const BatchArgs& a, cudaStream_t s) {
   using CF = Cfg<LOGN>;
   static bool attr_set[128] = {};
   int dev = 0;
@@ -300,7 +316,7 @@ cudaError_t launch_batch_t(const BatchArgs& a, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
   if (!attr_set[dev]) {
-    e = cudaFuncSetAttribute(batch_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CF::SMEM);
+    e = cudaFuncSetAttribute(batch_kernel<LOGN, T1F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CF::SMEM);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
@@ -309,7 +325,7 @@ cudaError_t launch_batch_t(const BatchArgs& a, cudaStream_t s) {
     using BP = BatchPersist<LOGN>;
     static bool pset[128] = {};
     if (!pset[dev]) {
-      e = cudaFuncSetAttribute(batch_persistent_kernel<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(batch_persistent_kernel<LOGN, T1F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)BP::SMEM);
       if (e != cudaSuccess) return e;
       pset[dev] = true;
@@ -319,19 +335,24 @@ cudaError_t launch_batch_t(const BatchArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const long long need = (work + BP::GROUPS - 1) / BP::GROUPS;
     const unsigned grid = (unsigned)(need < sms ? need : sms);
-    batch_persistent_kernel<LOGN><<<grid, BP::THREADS, BP::SMEM, s>>>(a);
+    batch_persistent_kernel<LOGN, T1F><<<grid, BP::THREADS, BP::SMEM, s>>>(a);
     return cudaGetLastError();
   }
-  batch_kernel<LOGN><<<(unsigned)((work + CF::G - 1) / CF::G), CF::THREADS, CF::SMEM, s>>>(a);
+  batch_kernel<LOGN, T1F><<<(unsigned)((work + CF::G - 1) / CF::G), CF::THREADS, CF::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int LOGN>
-cudaError_t launch_t1_t(float2* t1, int n_tchan, int chan0, double f_lo0, double chan_bw,
+cudaError_t launch_batch_t(const BatchArgs& a, cudaStream_t s) {
+  return a.t1f ? launch_batch_tt<LOGN, true>(a, s) : launch_batch_tt<LOGN, false>(a, s);
+}
+
+template <int LOGN>
+cudaError_t launch_t1_t(float2* t1, float* t1f, int n_tchan, int chan0, double f_lo0, double chan_bw,
                         cudaStream_t s) {
   const long long total = (long long)n_tchan << LOGN;
   const unsigned grid = (unsigned)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
-  t1_table_kernel<LOGN><<<grid, 256, 0, s>>>(t1, n_tchan, chan0, f_lo0, chan_bw);
+  t1_table_kernel<LOGN><<<grid, 256, 0, s>>>(t1, t1f, n_tchan, chan0, f_lo0, chan_bw);
   return cudaGetLastError();
 }
 
@@ -346,10 +367,10 @@ cudaError_t launch_batch(int logn, const BatchArgs& a, cudaStream_t s) {
   }
 }
 
-cudaError_t launch_t1(int logn, float2* t1, int n_tchan, int chan0, double f_lo0, double chan_bw,
+cudaError_t launch_t1(int logn, float2* t1, float* t1f, int n_tchan, int chan0, double f_lo0, double chan_bw,
                       cudaStream_t s) {
   switch (logn) {
-#define X(L) case L: return launch_t1_t<L>(t1, n_tchan, chan0, f_lo0, chan_bw, s);
+#define X(L) case L: return launch_t1_t<L>(t1, t1f, n_tchan, chan0, f_lo0, chan_bw, s);
     CDD_BATCH_CASES(X)
 #undef X
     default: return cudaErrorInvalidValue;
@@ -366,6 +387,7 @@ struct cdd_batch_s {
     int n_fft = 0, logn = 0, n_ov = 0, hop = 0, chan0 = 0, n_tchan = 0;
     float2* d_tw = nullptr;
     float2* d_t1 = nullptr;
+    float* d_t1f = nullptr;
   };
   double f_center = 0, bandwidth = 0, chan_bw = 0, f_lo0 = 0;
   int n_chan = 0, n_avg = 0, n_dm = 0;
@@ -375,6 +397,7 @@ struct cdd_batch_s {
   int64_t r_max = 0;
   int hop_max = 0, n_ov_max = 0;
   int q = 1;                             // block = q * hop_max samples per channel
+  bool t1_single = false;                // DM = 1 phase table as single floats (small phases)
   bool committed = false;
   int device = -1;
   int sticky = CDD_OK;
@@ -426,6 +449,7 @@ void bfree(cdd_batch b) {
   for (auto& t : b->tiers) {
     cudaFree(t.d_tw);
     cudaFree(t.d_t1);
+    cudaFree(t.d_t1f);
   }
   cudaFree(b->d_in_cm);
   cudaFree(b->d_tail[0]);
@@ -449,8 +473,22 @@ int bzero_state(cdd_batch b, cudaStream_t s) {
   return CDD_OK;
 }
 
+// Largest phase a chirp of this batch reaches, in turns: the top bin of the
+// lowest channel at the largest DM (Eq. 3 grows with f_l and falls with f_o).
+double max_phase_turns(const cdd_batch b) {
+  double dm_max = 0;
+  for (double d : b->dms) dm_max = d > dm_max ? d : dm_max;
+  const double f_l = b->chan_bw, f_o = b->f_lo0;
+  return kDispDHost * 1e6 * dm_max * f_l * f_l / ((f_l + f_o) * f_o * f_o);
+}
+
+// Up to this many turns the single-float DM = 1 phase (relative rounding
+// 2^-24) keeps every chirp phase within 2*pi * 16 * 2^-24 ~ 6e-6 rad.
+constexpr double kT1SingleTurns = 16.0;
+
 int bcommit_once(cdd_batch b) {
   BTRY(b, cudaGetDevice(&b->device));
+  b->t1_single = max_phase_turns(b) <= kT1SingleTurns;
   if (n_out(b) < b->r_max) return CDD_EINVAL;        // a block must outlast the largest delay
   int rc;
   const int64_t rows = block_samples(b);
@@ -468,7 +506,11 @@ int bcommit_once(cdd_batch b) {
     const size_t segs = (size_t)t.n_tchan * (rows / t.hop);
     if (segs * t.n_fft > xs) xs = segs * t.n_fft;
     if ((rc = balloc(b, &t.d_tw, (size_t)cdd::twiddle_table_len(t.logn) * sizeof(float2)))) return rc;
-    if ((rc = balloc(b, &t.d_t1, (size_t)t.n_tchan * t.n_fft * sizeof(float2)))) return rc;
+    if (b->t1_single) {
+      if ((rc = balloc(b, &t.d_t1f, (size_t)t.n_tchan * t.n_fft * sizeof(float)))) return rc;
+    } else if ((rc = balloc(b, &t.d_t1, (size_t)t.n_tchan * t.n_fft * sizeof(float2)))) {
+      return rc;
+    }
   }
   if ((rc = balloc(b, &b->d_xs, xs * sizeof(float2)))) return rc;
 
@@ -485,7 +527,8 @@ int bcommit_once(cdd_batch b) {
   cudaError_t e = cudaSuccess;
   for (auto& t : b->tiers) {
     if (e == cudaSuccess) e = cdd::launch_twiddle_table(t.logn, t.d_tw, s);
-    if (e == cudaSuccess) e = cdd::launch_t1(t.logn, t.d_t1, t.n_tchan, t.chan0, b->f_lo0, b->chan_bw, s);
+    if (e == cudaSuccess)
+      e = cdd::launch_t1(t.logn, t.d_t1, t.d_t1f, t.n_tchan, t.chan0, b->f_lo0, b->chan_bw, s);
   }
   if (e == cudaSuccess && (rc = bzero_state(b, s)) != CDD_OK) {
     cudaStreamDestroy(s);
@@ -627,6 +670,7 @@ int cdd_batch_get(cdd_batch b, int attr, int64_t* v) {
     case CDD_ATTR_BYTES_DEVICE: *v = (int64_t)b->bytes_device; break;
     case CDD_ATTR_BLOCKS_DONE: *v = b->blocks; break;
     case CDD_ATTR_KERNEL_LAUNCHES: *v = b->last_launches; break;
+    case CDD_ATTR_PHASE_FLOATS: *v = max_phase_turns(b) <= kT1SingleTurns ? 1 : 2; break;
     case CDD_ATTR_N_CHAN: *v = b->n_chan; break;
     case CDD_ATTR_N_AVG: *v = b->n_avg; break;
     case CDD_ATTR_HOP: *v = b->hop_max; break;
@@ -665,6 +709,7 @@ int cdd_batch_execute(cdd_batch b, const int8_t* d_in, float* d_out, cudaStream_
     a.rows = rows;
     a.out = d_out;
     a.t1 = t.d_t1;
+    a.t1f = t.d_t1f;
     a.tw = t.d_tw;
     a.tail_rd = b->d_tail[b->parity];
     a.tail_wr = b->d_tail[b->parity ^ 1];

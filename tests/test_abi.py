@@ -253,3 +253,17 @@ def test_stream_state_blob_before_any_launch(cdd):
         cdd.cdd_destroy(a)
         cdd.cdd_destroy(b)
 
+
+
+def test_batch_phase_table_form(cdd):
+    """The batch keeps the DM = 1 chirp phase as single floats when no phase
+    exceeds 16 turns (650 MHz, DMs to 51.5: 12.2 turns) and as two floats
+    otherwise (150 MHz, DM 20: 238 turns)."""
+    for args, want in (((650.0, 200.0, 2048, list(20.0 + 0.5 * np.arange(64)),
+                         (16384, 8192, 4096, 2048), 16), 1),
+                       ((150.0, 1.5625, 16, [15.0, 20.0], (16384,), 4), 2)):
+        b = cdd.cdd_batch_create(*args)
+        try:
+            assert cdd.cdd_batch_get(b, "phase_floats") == want
+        finally:
+            cdd.cdd_batch_destroy(b)

@@ -91,3 +91,25 @@ def test_batch_persistent_tiers(cuda_device, n_avg):
     for d in range(len(args[3])):
         assert O.rel_rms(got[d], want[d]) <= TOL, d
     assert np.array_equal(run_batch(vin, args, 4, 1), got)
+
+
+def test_batch_two_float_phase_table(cuda_device):
+    """Chirp phases up to 238 turns (150 MHz, DM 20) keep the two-float phase
+    table; every DM plane against the oracle."""
+    from paper_1509_00186_b300.cdd import Batch
+    args = (150.0, 1.5625, 16, [15.0, 20.0], (16384,), 4)
+    g = O.batch_geometry(*args)
+    vin = complex_int8_voltages(27, g.hop(0) * 3, 16, 20.0)
+    with Batch(*args, segments_per_block=1) as b:
+        assert b.get("phase_floats") == 2
+    want = O.dedisperse_batch(vin, g)
+    got = run_batch(vin, args, 1, 3)
+    for d in range(2):
+        assert O.rel_rms(got[d], want[d]) <= TOL, d
+
+
+def test_batch_one_float_phase_table(small):
+    """The small band's phases (under 3 turns) use the single-float table."""
+    from paper_1509_00186_b300.cdd import Batch
+    with Batch(*SMALL, segments_per_block=1) as b:
+        assert b.get("phase_floats") == 1
