@@ -276,6 +276,13 @@ ols_persistent_kernel(const OlsArgs a) {
 }
 
 
+// A cluster barrier that publishes nothing and follows no memory access:
+// arrive without the release fence (the wait still acquires).  Used where the
+// CTAs only need to know that every CTA of the cluster has started.
+__device__ __forceinline__ void cluster_barrier_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ clusters
 //
 // N = CL * 2^LOGS (32768 and 65536) does not fit one SM's shared memory, so a
@@ -311,7 +318,7 @@ ols_cluster_kernel(const OlsArgs a) {
   const int na = a.n_avg;
   constexpr int U = PERX * CL;
   const bool in_lanes = U == 32 && na <= 32 && (na & (na - 1)) == 0;
-  cluster.sync();                        // every CTA of the cluster has started: DSMEM is live
+  cluster_barrier_relaxed();             // every CTA of the cluster has started: DSMEM is live
   // One segment per cluster (a persistent form that loops over segments
   // measured slower for clusters of eight and no faster for four).
   auto segment = [&](const int w) {
@@ -390,7 +397,9 @@ ols_cluster_kernel(const OlsArgs a) {
         }
       }
     }
-    cluster.sync();                        // no CTA reads another's buffer after this
+    // no CTA reads another's buffer after this; the release arrive also makes
+    // sure this CTA's loads from its neighbours are done before they exit
+    cluster.sync();
 
     const int n_int = a.hop / a.n_avg;
     const int r = __ldg(&a.shift[k]);
@@ -463,9 +472,6 @@ ols_cluster_kernel(const OlsArgs a) {
         outk[m] = src >= 0 ? ringk[src % a.ring_len] : 0.f;
       }
     }
-    // The next forward cross pass writes into every CTA's buffer: with the
-    // shared-memory integration the buffers are still being read here.
-    if (!in_lanes) cluster.sync();
   };
   segment((int)(blockIdx.x / CL));
 }
