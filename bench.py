@@ -270,7 +270,7 @@ def run_gpu(args, world, rank, local):
 
     w, q = workload_info(args.channels)
     plan = Plan(w.f_center_mhz, w.bandwidth_mhz, w.n_chan, w.dm, w.n_fft, w.n_avg,
-                segments_per_block=q, pipeline_chunks=4, stage_timing=True)
+                segments_per_block=q, stage_timing=True)
     hop = plan.get("hop")
     assert hop * q == plan.block_samples and q == w.n_samp // hop
     rows, n_out, C = plan.block_samples, plan.n_out, w.n_chan

@@ -79,7 +79,8 @@ enum cdd_attr {
   CDD_ATTR_TAPER = 10,             /* enum cdd_taper, settable                 */
   CDD_ATTR_BLOCKS_DONE = 11,       /* execute calls since create / reset       */
   CDD_ATTR_PIPELINE_CHUNKS = 12,   /* host-buffer path: copy/compute chunks per
-                                      block (settable, default 4, divides q)   */
+                                      block (settable; divides q; default the
+                                      most chunks of >= 4 segments each)       */
   CDD_ATTR_KERNEL_LAUNCHES = 13,   /* kernels launched by the last execute     */
   CDD_ATTR_BYTES_NEEDED = 14,      /* device bytes the first execute allocates
                                       (known before it; with the host path,

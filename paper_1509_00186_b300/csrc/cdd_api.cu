@@ -161,6 +161,15 @@ int fail_cuda(cdd_plan p, cudaError_t e) {
 
 int64_t n_out_per_block(const cdd_plan p) { return (int64_t)p->q * p->hop / p->n_avg; }
 
+// Host-buffer pipeline: the most chunks (a divisor of q) of at least 4
+// segments each, so the copy-out and compute of the last chunk, which
+// nothing overlaps, stay short (19 chunks of 4 for q = 76).
+int default_chunks(int q) {
+  for (int d = q / 4; d > 1; --d)
+    if (q % d == 0) return d;
+  return 1;
+}
+
 // Device bytes the first execute allocates (tables, tails, ring, shifts and the
 // channel-major block copy), exactly as commit_once requests them.
 int64_t bytes_needed(const cdd_plan p) {
@@ -475,8 +484,7 @@ int cdd_plan_set(cdd_plan p, int attr, int64_t value) {
       if ((int64_t)value * p->hop * p->n_chan > (int64_t)1 << 40) return CDD_EINVAL;
       if ((int64_t)value * p->n_chan >= (int64_t)1 << 31) return CDD_EINVAL;
       p->q = (int)value;
-      if (!p->chunks_set || p->q % p->chunks)
-        p->chunks = p->q % 4 == 0 ? 4 : p->q % 2 == 0 ? 2 : 1;
+      if (!p->chunks_set || p->q % p->chunks) p->chunks = default_chunks(p->q);
       return CDD_OK;
     case CDD_ATTR_TAPER:
       if (value < CDD_TAPER_NONE || value > CDD_TAPER_WELCH) return CDD_EINVAL;

@@ -113,7 +113,7 @@ def test_setters(cdd):
             with pytest.raises(cdd.CddError):
                 cdd.cdd_plan_set(p, attr, val)
         cdd.cdd_plan_set(p, "segments_per_block", 76)
-        assert cdd.cdd_plan_get(p, "pipeline_chunks") == 4
+        assert cdd.cdd_plan_get(p, "pipeline_chunks") == 19          # 19 chunks of 4 segments
         cdd.cdd_plan_set(p, "pipeline_chunks", 2)
         assert cdd.cdd_plan_get(p, "pipeline_chunks") == 2
         cdd.cdd_plan_set(p, "taper", cdd.TAPER["welch"])
