@@ -157,6 +157,8 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
   const float* t1fk = a.t1f + (size_t)kt * N;
   const int na = a.n_avg;
   const int n_int = a.hop / na;
+  // integration across lanes as in the single-DM kernel; N = 16384 keeps the
+  // shared-memory form (the register form spills there and measured slower)
   bool in_lanes = false;
   if constexpr (T % 32 == 0 && LOGN <= 13) in_lanes = na <= R0 && na <= 32 && (na & (na - 1)) == 0;
   float* pw = reinterpret_cast<float*>(buf);
