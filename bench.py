@@ -579,7 +579,14 @@ def row_batch(args, dev, peaks):
     dms = [20.0 + 0.5 * i for i in range(64)]
     tiers = (16384, 8192, 4096, 2048)
     C, n_avg = 2048, 16
-    b = Batch(650.0, 200.0, C, dms, tiers, n_avg, segments_per_block=24)
+    f_c, bw = 650.0, 200.0
+    if args.channels is not None and args.channels != C:
+        # the lowest channels only (same channel width and lowest edge), for profiling captures
+        if args.channels % 4:
+            raise SystemExit("--path batch: --channels must be a multiple of the 4 tiers")
+        C, bw = args.channels, bw * args.channels / C
+        f_c = 650.0 - 100.0 + bw / 2
+    b = Batch(f_c, bw, C, dms, tiers, n_avg, segments_per_block=24)
     bs, n_out = b.block_samples, b.n_out
     vin = complex_int8_voltages(4, bs, C, 20.0)
     x = torch.from_numpy(vin).to(dev)
@@ -599,10 +606,10 @@ def row_batch(args, dev, peaks):
     roof["output_bytes_per_step"] = out.numel() * 4
     cpu = None
     if not args.no_cpu_baseline:
-        geo = O.batch_geometry(650.0, 200.0, C, dms, tiers, n_avg)
+        geo = O.batch_geometry(f_c, bw, C, dms, tiers, n_avg)
         threads = oracle_threads()
         per_tier = max(1, threads // 4)
-        chans = [t * 512 + i for t in range(4) for i in range(per_tier)]
+        chans = [t * (C // 4) + i for t in range(4) for i in range(min(per_tier, C // 4))]
         from concurrent.futures import ThreadPoolExecutor
         parts = [chans[i::threads] for i in range(threads) if chans[i::threads]]
 
@@ -613,11 +620,11 @@ def row_batch(args, dev, peaks):
         cpu = {"value": len(chans) * bs / dt / 1e6, "unit": "Msamples/s", "cores": threads, "kind": "oracle",
                "seconds": dt, "sample": f"{len(chans)} channels ({per_tier} per tier) x {bs} samples x "
                                         f"{len(dms)} DMs, {threads} threads over channels"}
-    config = {"workload": f"batch:650MHz-200MHz-{C}ch-{len(dms)}DM-N16384/8192/4096/2048-x{n_avg}",
+    config = {"workload": f"batch:{f_c:g}MHz-{bw:g}MHz-{C}ch-{len(dms)}DM-N16384/8192/4096/2048-x{n_avg}",
               "block_samples_per_channel": bs, "dm_trials": len(dms)}
     return _line("batch", args, "input Msamples/s through all DM trials", value, "Msamples/s", ms,
                  steps_ms, config, roof, cpu, clocks, launches * args.steps,
-                 x_realtime=value * 1e6 / (200.0e6))
+                 x_realtime=value * 1e6 / (bw * 1e6))
 
 
 def row_fullband(args, dev, peaks):

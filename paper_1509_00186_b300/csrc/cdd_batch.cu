@@ -57,10 +57,6 @@ __device__ __forceinline__ float2 dm_chirp(float2 t1, float2 dm) {
   return make_float2(cs, -sn);
 }
 
-// One (channel, segment) work item w of a tier: the forward transform, the
-// spectrum to its scratch row, then every DM trial.  SH: tw is in shared
-// memory.  sync() is the group's barrier.  Returns true when buf (the power
-// samples) was read after the last barrier.
 // The same with the DM = 1 phase as one float: used when no phase exceeds
 // 16 turns, so its rounding (2^-24 relative) stays below 6e-6 rad.
 __device__ __forceinline__ float2 dm_chirp1(float t1, float2 dm) {
@@ -73,6 +69,10 @@ __device__ __forceinline__ float2 dm_chirp1(float t1, float2 dm) {
   return make_float2(cs, -sn);
 }
 
+// One (channel, segment) work item w of a tier: the forward transform, the
+// spectrum to its scratch row, then every DM trial.  SH: tw is in shared
+// memory.  sync() is the group's barrier.  Returns true when buf (the power
+// samples) was read after the last barrier.
 template <int LOGN, bool SH, bool T1F, class Sync>
 __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, const float2* tw, int lt,
                                               bool active, int w, Sync sync) {
