@@ -18,6 +18,11 @@
 #include <new>
 #include <vector>
 
+// Packed FP32 only for the butterflies without a multiplication: the general
+// ones, packed, measured slower here (register pressure of the DM loop).
+#ifndef CDD_PACKED
+#define CDD_PACKED 1
+#endif
 #include "../../include/cdd.h"
 #include "cdd_fft.cuh"
 #include "cdd_internal.h"
@@ -67,6 +72,25 @@ __device__ __forceinline__ float2 dm_chirp1(float t1, float2 dm) {
   float sn, cs;
   __sincosf(6.28318530717958647692f * frac, &sn, &cs);
   return make_float2(cs, -sn);
+}
+
+// dm_chirp1 for two bins at once, the phase arithmetic in packed FP32:
+// c0, c1 = exp(-2 pi i DM T1) for t1 = (T1 of bin 0, T1 of bin 1).  dmx, ndm
+// and dmy hold (DM hi, DM hi), (-DM hi, -DM hi) and (DM lo, DM lo).  -p is
+// formed as (-DM hi) t1, which rounds to exactly the negated product, and
+// p - rint(p) = rint(-p) - (-p), so every value equals the scalar form's.
+__device__ __forceinline__ void dm_chirp1x2(float2 t1, float2 dmx, float2 ndm, float2 dmy, float2& c0,
+                                            float2& c1) {
+  const float2 np = mul2(ndm, t1);                                      // -p
+  const float2 e = fma2(dmx, t1, np);                                   // rounding error of p
+  const float2 lo = fma2(dmy, t1, e);
+  const float2 frac = add2(sub2(make_float2(rintf(np.x), rintf(np.y)), np), lo);
+  const float2 arg = mul2(make_float2(6.28318530717958647692f, 6.28318530717958647692f), frac);
+  float sn, cs;
+  __sincosf(arg.x, &sn, &cs);
+  c0 = make_float2(cs, -sn);
+  __sincosf(arg.y, &sn, &cs);
+  c1 = make_float2(cs, -sn);
 }
 
 // One (channel, segment) work item w of a tier: the forward transform, the
@@ -172,10 +196,23 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
       for (int i = 0; i < PERC; ++i) {
         const int q = lt + i * T;
         float2 x[RL];
+        if constexpr (T1F && RL % 2 == 0) {
+          const float2 dmx = make_float2(dm.x, dm.x), ndm = make_float2(-dm.x, -dm.x);
+          const float2 dmy = make_float2(dm.y, dm.y);
 #pragma unroll
-        for (int kk = 0; kk < RL; ++kk)
-          x[kk] = cmul(xk[kk * NG + q], T1F ? dm_chirp1(__ldg(&t1fk[kk * NG + q]), dm)
-                                            : dm_chirp(__ldg(&t1k[kk * NG + q]), dm));
+          for (int kk = 0; kk < RL; kk += 2) {
+            float2 c0, c1;
+            dm_chirp1x2(make_float2(__ldg(&t1fk[kk * NG + q]), __ldg(&t1fk[(kk + 1) * NG + q])), dmx, ndm, dmy,
+                        c0, c1);
+            x[kk] = cmul(xk[kk * NG + q], c0);
+            x[kk + 1] = cmul(xk[(kk + 1) * NG + q], c1);
+          }
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < RL; ++kk)
+            x[kk] = cmul(xk[kk * NG + q], T1F ? dm_chirp1(__ldg(&t1fk[kk * NG + q]), dm)
+                                              : dm_chirp(__ldg(&t1k[kk * NG + q]), dm));
+        }
         dft<RL, 1>(x);
         float2* pb = buf + pad(q * RL);
 #pragma unroll

@@ -88,6 +88,48 @@ __host__ __device__ constexpr double cos32d(int k) {
   return m <= 8 ? c[m] : m <= 16 ? -c[16 - m] : m <= 24 ? -c[m - 16] : c[32 - m];
 }
 
+// Packed two-lane FP32 (add/sub/fma.rn.f32x2, sm_100 and later): one
+// instruction applies the operation to both halves of a float2, each half
+// rounded as the scalar instruction would round it, so results are bit for
+// bit those of the scalar form.  CDD_PACKED selects which radix-2 butterflies
+// use it: 1 those without a multiplication (a +- b), 2 also the final a +- f u
+// of the butterflies with a general rotation (two more register pairs of
+// constants).  A translation unit may set it before including this header.
+#ifndef CDD_PACKED
+#define CDD_PACKED 2
+#endif
+__device__ __forceinline__ unsigned long long f2_pack(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(r);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(r);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(r);
+}
+// a * b + c on both halves
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)), "l"(f2_pack(c)));
+  return f2_unpack(r);
+}
+
 // Radix-2 butterfly (a, b) -> (a + w b, a - w b), w = exp(DIR * 2*pi*i * J / LEN).
 // For a non-trivial w = c + i s the product is factored through the larger of
 // |c| and |s|: w b = c (b + i (s/c) b) or w b = s ((c/s) b + i b), so that the
@@ -97,7 +139,11 @@ __host__ __device__ constexpr double cos32d(int k) {
 template <int LEN, int DIR, int J>
 __device__ __forceinline__ void bfly(float2& a, float2& b) {
   constexpr int m = J * (32 / LEN);       // angle in units of 2*pi/32
-  if constexpr (m == 0 || m == 8) {
+  if constexpr (m == 0 && CDD_PACKED >= 1) {
+    const float2 d = sub2(a, b);
+    a = add2(a, b);
+    b = d;
+  } else if constexpr (m == 0 || m == 8) {
     const float2 w = rot<LEN, DIR, J>(b);
     b = csub(a, w);
     a = cadd(a, w);
@@ -117,8 +163,14 @@ __device__ __forceinline__ void bfly(float2& a, float2& b) {
       ux = fmaf(r, b.x, -b.y);
       uy = fmaf(r, b.y, b.x);
     }
-    b = make_float2(fmaf(-f, ux, a.x), fmaf(-f, uy, a.y));
-    a = make_float2(fmaf(f, ux, a.x), fmaf(f, uy, a.y));
+    if constexpr (CDD_PACKED >= 2) {
+      const float2 u = make_float2(ux, uy);
+      b = fma2(make_float2(-f, -f), u, a);
+      a = fma2(make_float2(f, f), u, a);
+    } else {
+      b = make_float2(fmaf(-f, ux, a.x), fmaf(-f, uy, a.y));
+      a = make_float2(fmaf(f, ux, a.x), fmaf(f, uy, a.y));
+    }
   }
 }
 

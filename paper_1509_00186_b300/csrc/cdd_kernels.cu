@@ -311,9 +311,21 @@ ols_cluster_kernel(const OlsArgs a) {
   extern __shared__ float2 smem[];
   float2* buf = smem;
   const int lt = threadIdx.x;
-  float2* rbuf[CL];
+  // the cluster's buffers as 32-bit shared::cluster addresses (one register each)
+  uint32_t rbuf[CL];
+  {
+    const uint32_t local = (uint32_t)__cvta_generic_to_shared(buf);
 #pragma unroll
-  for (int j = 0; j < CL; ++j) rbuf[j] = cluster.map_shared_rank(buf, j);
+    for (int j = 0; j < CL; ++j) asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(rbuf[j]) : "r"(local), "r"(j));
+  }
+  auto dsm_st = [](uint32_t addr, float2 v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+  };
+  auto dsm_ld = [](uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+    return v;
+  };
   const float2* twx = a.tw + PL::TW_LEN;
   const int na = a.n_avg;
   constexpr int U = PERX * CL;
@@ -355,7 +367,7 @@ ols_cluster_kernel(const OlsArgs a) {
 #pragma unroll
         for (int kk = 1; kk < CL; ++kk) v[kk] = cmul(v[kk], __ldg(&twx[(kk - 1) * NS + t]));
 #pragma unroll
-        for (int kk = 0; kk < CL; ++kk) rbuf[kk][pad(t)] = v[kk];
+        for (int kk = 0; kk < CL; ++kk) dsm_st(rbuf[kk] + 8u * (uint32_t)pad(t), v[kk]);
       }
     }
     cluster.sync();
@@ -384,7 +396,7 @@ ols_cluster_kernel(const OlsArgs a) {
     for (int i = 0; i < PERX; ++i) {
       const int t = rank * NB + lt + i * T;
 #pragma unroll
-      for (int kk = 0; kk < CL; ++kk) z[i][kk] = rbuf[kk][pad(t)];
+      for (int kk = 0; kk < CL; ++kk) z[i][kk] = dsm_ld(rbuf[kk] + 8u * (uint32_t)pad(t));
 #pragma unroll
       for (int kk = 1; kk < CL; ++kk) z[i][kk] = cmulc(z[i][kk], __ldg(&twx[(kk - 1) * NS + t]));
       dft<CL, 1>(z[i]);

@@ -42,12 +42,12 @@ __device__ __forceinline__ constexpr int poff(int j) { return S * j + ((S * j) >
 
 // int8 pair (re, im) held in the low 16 bits -> float2 without I2F: bias each
 // byte to unsigned, drop it into the mantissa of 2^23 and subtract 2^23 + 128
-// (exact for every int8 value).
+// (exact for every int8 value; one packed subtraction for both halves).
 __device__ __forceinline__ float2 unpack_i8x2(uint32_t raw16) {
   const uint32_t w = raw16 ^ 0x8080u;
-  const float re = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540)) - 8388736.0f;
-  const float im = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7541)) - 8388736.0f;
-  return make_float2(re, im);
+  const float re = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540));
+  const float im = __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7541));
+  return sub2(make_float2(re, im), make_float2(8388736.0f, 8388736.0f));
 }
 
 // Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16; the
@@ -150,11 +150,23 @@ __device__ __forceinline__ void lane_window_sums(float (&u)[R0], int lane) {
   if constexpr (NA > 1) {
     constexpr int o = NA / 2, H = V / 2;
     const bool hi = (lane & o) != 0;
+    if constexpr (H % 2 == 0) {                  // two sums per packed addition
 #pragma unroll
-    for (int i = 0; i < H; ++i) {
-      const float keep = hi ? u[i + H] : u[i];
-      const float send = hi ? u[i] : u[i + H];
-      u[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      for (int i = 0; i < H; i += 2) {
+        const float2 keep = hi ? make_float2(u[i + H], u[i + H + 1]) : make_float2(u[i], u[i + 1]);
+        const float s0 = hi ? u[i] : u[i + H], s1 = hi ? u[i + 1] : u[i + H + 1];
+        const float2 got = make_float2(__shfl_xor_sync(0xffffffffu, s0, o), __shfl_xor_sync(0xffffffffu, s1, o));
+        const float2 sum = add2(keep, got);
+        u[i] = sum.x;
+        u[i + 1] = sum.y;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < H; ++i) {
+        const float keep = hi ? u[i + H] : u[i];
+        const float send = hi ? u[i] : u[i + H];
+        u[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
     }
     lane_window_sums<R0, NA / 2, H>(u, lane);
   }
