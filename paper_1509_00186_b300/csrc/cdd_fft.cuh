@@ -134,8 +134,11 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 // For a non-trivial w = c + i s the product is factored through the larger of
 // |c| and |s|: w b = c (b + i (s/c) b) or w b = s ((c/s) b + i b), so that the
 // butterfly is two fused multiply-adds for the inner factor and four for
-// a +- c u (six instructions instead of four for the product and four adds).
-// The ratio is at most 1 in magnitude, so no intermediate grows.
+// a +- c u (six lane operations instead of four for the product and four
+// adds; with CDD_PACKED >= 2 the last four issue as two packed instructions).
+// The ratio is at most 1 in magnitude, so no intermediate grows.  w = +-i
+// stays scalar: its packed form needs (b.y, b.x) in a register pair, and the
+// moves that build it cost what the packing saves.
 template <int LEN, int DIR, int J>
 __device__ __forceinline__ void bfly(float2& a, float2& b) {
   constexpr int m = J * (32 / LEN);       // angle in units of 2*pi/32
