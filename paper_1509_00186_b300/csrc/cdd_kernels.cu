@@ -203,7 +203,7 @@ ols_kernel(const OlsArgs a) {
   ols_segment<LOGN, CM, false>(a, buf, a.tw, lt, active, k, s, [] { __syncthreads(); });
 }
 
-// Persistent form for N = 4096 and 8192: one CTA per SM with two groups of 256
+// Persistent form for N = 8192: one CTA per SM with two groups of 256
 // threads, each looping over segments with its own named barrier, and the whole
 // twiddle table staged once in shared memory (in L1 it was evicted by the
 // streaming chirp rows).  Reads the channel-major block.
@@ -287,7 +287,7 @@ __device__ __forceinline__ void cluster_barrier_relaxed() {
 //
 // N = CL * 2^LOGS (32768 and 65536) does not fit one SM's shared memory, so a
 // cluster of CL CTAs holds one segment, 2^LOGS points per CTA (2^13: the
-// 256-thread sub-transform of the single-CTA kernels, two CTAs per SM; CL = 4
+// 256-thread sub-transform of the single-CTA kernels, three CTAs per SM; CL = 4
 // and 8).  A radix-CL pass
 // across the cluster (DIF; inputs straight from global memory, outputs written
 // through distributed shared memory) leaves CTA r with the independent
@@ -296,7 +296,9 @@ __device__ __forceinline__ void cluster_barrier_relaxed() {
 // the CL sub-results back across the cluster and the epilogue detects,
 // integrates and stores the CTA's quarter of the butterflies.
 template <int LOGS, int CL>
-__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(PassPlan<LOGS>::T, PassPlan<LOGS>::T <= 256 ? 2 : 1)
+// Three 256-thread CTAs per SM (80 registers): measured faster than two
+// (N = 32768: 2.85 against 3.02 ms per block; N = 65536: 3.13 against 3.16).
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(PassPlan<LOGS>::T, PassPlan<LOGS>::T <= 256 ? 3 : 1)
 ols_cluster_kernel(const OlsArgs a) {
   namespace cg = cooperative_groups;
   using PL = PassPlan<LOGS>;
@@ -659,7 +661,9 @@ cudaError_t launch_ols_t(const OlsArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     attr_set[dev][cm] = true;
   }
-  if constexpr (LOGN == 12 || LOGN == 13) {
+  // N = 8192 only: N = 4096 (radix 16 per thread) runs faster as three
+  // 256-thread CTAs per SM (1.58 against 1.68 ms per 512-channel block)
+  if constexpr (LOGN == 13) {
     if (cm && kUsePersistent) {
       static bool pset[128] = {};
       if (!pset[dev]) {

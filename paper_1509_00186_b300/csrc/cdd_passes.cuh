@@ -26,10 +26,12 @@ struct Cfg {
   static constexpr int T = PL::T;
   static constexpr int G = T >= kMinCtaThreads ? 1 : kMinCtaThreads / T;   // transforms per CTA
   static constexpr int THREADS = G * T;
+  // CTAs per SM to aim for: three 256-thread CTAs (80 registers) where a
+  // thread's largest radix is 16, two where it is 32 (three would spill)
 #ifdef CDD_OLS_MINB
-  static constexpr int MINB = THREADS <= 256 ? CDD_OLS_MINB : 1;          // CTAs per SM to aim for
+  static constexpr int MINB = THREADS <= 256 ? CDD_OLS_MINB : 1;
 #else
-  static constexpr int MINB = THREADS <= 256 ? 2 : 1;
+  static constexpr int MINB = THREADS <= 256 ? (PL::R(0) <= 16 ? 3 : 2) : 1;
 #endif
   static constexpr int SEG_F2 = padded_len(PL::N);                       // float2 per transform
   static constexpr size_t SMEM = size_t(G) * SEG_F2 * sizeof(float2);
