@@ -336,11 +336,15 @@ ols_cluster_kernel(const OlsArgs a) {
   // One segment per cluster (a persistent form that loops over segments
   // measured slower for clusters of eight and no faster for four).
   auto segment = [&](const int w) {
-    // channel-fastest: segment-fastest, or blocks of 4, 8 or 16 channels with
-    // segments cycling inside, read each 512 KB chirp row (N = 65536) from L2
-    // instead of DRAM but measured 0.3-2% slower
-    const int k = w % a.n_chan;
-    const int s = a.s_begin + w / a.n_chan;
+    // segment-fastest, so that a channel's chirp row (512 KB at N = 65536;
+    // the whole table exceeds L2) serves its consecutive segments from L2,
+    // and each CTA asks L2 for its slice of that row before the forward
+    // passes: 2.94 against 3.13 ms per N = 65536 block at three CTAs per SM
+    // (at two CTAs per SM both measured 0.3-2% slower)
+    const int k = w / a.s_count;
+    const int s = a.s_begin + w % a.s_count;
+    if (lt < 8)
+      prefetch_l2(a.chirp + (size_t)k * N + (size_t)rank * NS + lt * (NS / 8), (uint32_t)(NS / 8 * sizeof(float2)));
 
     // ---- cross pass, forward: x[t + NS*j] -> DFT_CL -> w_N^{t*kk} -> CTA kk, index t
     {
