@@ -78,9 +78,9 @@ def test_upgraded_gmrt_batch_full_size_sampled(cuda_device):
 
 @pytest.mark.parametrize("n_avg", [32, 64])
 def test_batch_persistent_tiers(cuda_device, n_avg):
-    """Tiers of 8192 and 4096 points (the persistent batch kernel): n_avg 32
-    sums across lanes, 64 through shared memory; every DM plane against the
-    oracle, and a block split gives the same bits."""
+    """Tiers of 8192 points (the persistent batch kernel) and 4096 points
+    (three CTAs per SM): n_avg 32 sums across lanes, 64 through shared memory;
+    every DM plane against the oracle, and a block split gives the same bits."""
     args = (650.0, 1.5625, 16, [5.0, 10.0, 15.0], (8192, 4096), n_avg)
     g = O.batch_geometry(*args)
     h = g.hop(0)
