@@ -100,12 +100,27 @@ enum cdd_attr {
                                       kernels of the timed blocks, ns.  Reading
                                       18..20 waits for the timed blocks still
                                       in flight; the sums never reset.         */
-  CDD_ATTR_PHASE_FLOATS = 22       /* batch only: 1 when the DM = 1 chirp phase
+  CDD_ATTR_PHASE_FLOATS = 22,      /* batch only: 1 when the DM = 1 chirp phase
                                       table is single floats (no chirp phase
                                       above 16 turns), else 2 (two floats)     */
+  CDD_ATTR_PRECISION = 23          /* enum cdd_precision, settable: FP32 only;
+                                      the other forms return CDD_EUNSUPPORTED  */
 };
 
 enum cdd_taper { CDD_TAPER_NONE = 0, CDD_TAPER_HANN = 1, CDD_TAPER_WELCH = 2 };
+
+/* Arithmetic of the transforms.  This build computes in FP32, with every chirp
+ * phase formed in FP64 and reduced modulo one turn before rounding.  FP16 or
+ * BF16 transforms (alone or as hi/lo pairs on the tensor cores) are not built:
+ * FP16 and BF16 alone miss the 1e-5 relative RMS bound against the FP64
+ * reference, and the split forms are not implemented.  Setting any of them
+ * returns CDD_EUNSUPPORTED and leaves the plan at FP32. */
+enum cdd_precision {
+  CDD_PRECISION_FP32 = 0,
+  CDD_PRECISION_FP16 = 1,
+  CDD_PRECISION_FP16X2 = 2,
+  CDD_PRECISION_BF16X2 = 3
+};
 
 typedef struct cdd_plan_s* cdd_plan;
 

@@ -30,10 +30,11 @@ ATTR = {
     "block_samples": 6, "n_out_per_block": 7, "r_max": 8, "bytes_device": 9, "taper": 10,
     "blocks_done": 11, "pipeline_chunks": 12, "kernel_launches": 13, "bytes_needed": 14,
     "seq_gaps": 15, "polarisations": 16, "stage_timing": 17, "timed_blocks": 18,
-    "corner_turn_ns": 19, "ols_ns": 20, "phase_floats": 22,
+    "corner_turn_ns": 19, "ols_ns": 20, "phase_floats": 22, "precision": 23,
 }
 POOL_ATTR = {"budget": 100, "used_bytes": 101, "streams": 102}
 TAPER = {"none": 0, "hann": 1, "welch": 2}
+PRECISION = {"fp32": 0, "fp16": 1, "fp16x2": 2, "bf16x2": 3}
 
 # every symbol include/cdd.h declares
 EXPORTS = ("cdd_plan_create", "cdd_plan_set", "cdd_plan_get", "cdd_plan_shifts", "cdd_execute",

@@ -503,6 +503,9 @@ int cdd_plan_set(cdd_plan p, int attr, int64_t value) {
       if (value != 0 && value != 1) return CDD_EINVAL;
       p->timing = value == 1;
       return CDD_OK;
+    case CDD_ATTR_PRECISION:
+      if (value == CDD_PRECISION_FP32) return CDD_OK;
+      return value >= CDD_PRECISION_FP16 && value <= CDD_PRECISION_BF16X2 ? CDD_EUNSUPPORTED : CDD_EINVAL;
     default:
       return CDD_EINVAL;
   }
@@ -528,6 +531,7 @@ int cdd_plan_get(cdd_plan p, int attr, int64_t* v) {
     case CDD_ATTR_BYTES_NEEDED: *v = bytes_needed(p); break;
     case CDD_ATTR_POLARISATIONS: *v = p->pols; break;
     case CDD_ATTR_STAGE_TIMING: *v = p->timing ? 1 : 0; break;
+    case CDD_ATTR_PRECISION: *v = CDD_PRECISION_FP32; break;
     case CDD_ATTR_TIMED_BLOCKS:
     case CDD_ATTR_CORNER_TURN_NS:
     case CDD_ATTR_OLS_NS: {

@@ -118,6 +118,16 @@ def test_setters(cdd):
         assert cdd.cdd_plan_get(p, "pipeline_chunks") == 2
         cdd.cdd_plan_set(p, "taper", cdd.TAPER["welch"])
         assert cdd.cdd_plan_get(p, "taper") == 2
+        # precision: FP32 only; the FP16 / BF16 forms are refused as unsupported
+        cdd.cdd_plan_set(p, "precision", cdd.PRECISION["fp32"])
+        for name in ("fp16", "fp16x2", "bf16x2"):
+            with pytest.raises(cdd.CddError) as ei:
+                cdd.cdd_plan_set(p, "precision", cdd.PRECISION[name])
+            assert ei.value.code == cdd.CDD_EUNSUPPORTED
+        with pytest.raises(cdd.CddError) as ei:
+            cdd.cdd_plan_set(p, "precision", 9)
+        assert ei.value.code == cdd.CDD_EINVAL
+        assert cdd.cdd_plan_get(p, "precision") == cdd.PRECISION["fp32"]
     finally:
         cdd.cdd_destroy(p)
     cdd.cdd_destroy(0)     # NULL is accepted
