@@ -682,7 +682,9 @@ def row_serving(args, dev, peaks):
     200 MHz / 2048 channels at 650 MHz; DM 5..150), 8 blocks each, submitted as
     fast as possible; each stream's first block (its plan commit) is served
     before the timed region; the value is the aggregate rate of the other 7
-    blocks of every stream, latency per block."""
+    blocks of every stream, latency per block.  Blocks of the small streams
+    take about 40 us on the GPU, as long as a submit call through Python, so
+    the aggregate measures the submit loop more than the GPU."""
     from paper_1509_00186_b300 import serving
     specs = serving.mixed_scenario(8)
     summary, _ = serving.run_mix(specs, 8, speedup=1e9)
