@@ -259,6 +259,21 @@ int cdd_batch_shifts(cdd_batch batch, int64_t* shifts);
 int cdd_batch_execute(cdd_batch batch, const int8_t* d_in, float* d_out, cudaStream_t stream);
 int cdd_batch_reset(cdd_batch batch);
 int cdd_batch_destroy(cdd_batch batch);
+/* Stream checkpoint of a batch, as for a plan (cdd_plan_export_state): the
+ * overlap tail of every channel, the carried outputs of every DM plane (the
+ * last r_max of each channel) and the block count.  A blob imports only into
+ * a batch of the same geometry (frequencies, bandwidth, channels, DM list,
+ * tiers, n_avg, segments per block), else CDD_EINVAL with nothing changed.
+ *   cdd_batch_state_bytes: size of the blob, host side only.
+ *   cdd_batch_export_state: waits for `stream`, then copies the state into
+ *     host memory `state` of `bytes` >= the size (a batch that has not run
+ *     exports a fresh stream).
+ *   cdd_batch_import_state: commits the batch if needed, waits for `stream`,
+ *     and replaces its stream state.
+ * Blocks run after an import continue the exported stream bit for bit. */
+int cdd_batch_state_bytes(cdd_batch batch, int64_t* bytes);
+int cdd_batch_export_state(cdd_batch batch, void* state, int64_t bytes, cudaStream_t stream);
+int cdd_batch_import_state(cdd_batch batch, const void* state, int64_t bytes, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
  * Full-band mode: the paper's own design (Sec. 2.3, Sec. 3.1, Sec. 4.3).

@@ -47,7 +47,8 @@ EXPORTS = ("cdd_plan_create", "cdd_plan_set", "cdd_plan_get", "cdd_plan_shifts",
            "cdd_pool_destroy", "cdd_fullband_create", "cdd_fullband_set", "cdd_fullband_get",
            "cdd_fullband_execute", "cdd_fullband_reset", "cdd_fullband_destroy",
            "cdd_plan_state_bytes", "cdd_plan_export_state", "cdd_plan_import_state",
-           "cdd_pool_stream_state_bytes", "cdd_pool_stream_export", "cdd_pool_stream_import")
+           "cdd_pool_stream_state_bytes", "cdd_pool_stream_export", "cdd_pool_stream_import",
+           "cdd_batch_state_bytes", "cdd_batch_export_state", "cdd_batch_import_state")
 
 
 class CddError(RuntimeError):
@@ -71,6 +72,9 @@ def _load() -> ctypes.CDLL:
     lib.cdd_plan_export_state.argtypes = [vp, vp, ctypes.c_int64, vp]
     lib.cdd_plan_import_state.argtypes = [vp, vp, ctypes.c_int64, vp]
     lib.cdd_pool_stream_state_bytes.argtypes = [vp, ctypes.c_int, i64p]
+    lib.cdd_batch_state_bytes.argtypes = [vp, i64p]
+    lib.cdd_batch_export_state.argtypes = [vp, vp, ctypes.c_int64, vp]
+    lib.cdd_batch_import_state.argtypes = [vp, vp, ctypes.c_int64, vp]
     lib.cdd_pool_stream_export.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64, i64p]
     lib.cdd_pool_stream_import.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int64]
     lib.cdd_execute.argtypes = [vp, vp, vp, vp]
@@ -182,6 +186,26 @@ def cdd_plan_import_state(plan: int, state: bytes, stream: int = 0) -> None:
     buf = ctypes.create_string_buffer(bytes(state), len(state))
     _check(_lib.cdd_plan_import_state(ctypes.c_void_p(plan), buf, len(state), ctypes.c_void_p(stream)),
            "cdd_plan_import_state")
+
+
+def cdd_batch_state_bytes(batch: int) -> int:
+    v = ctypes.c_int64()
+    _check(_lib.cdd_batch_state_bytes(ctypes.c_void_p(batch), ctypes.byref(v)), "cdd_batch_state_bytes")
+    return v.value
+
+
+def cdd_batch_export_state(batch: int, stream: int = 0) -> bytes:
+    n = cdd_batch_state_bytes(batch)
+    buf = ctypes.create_string_buffer(n)
+    _check(_lib.cdd_batch_export_state(ctypes.c_void_p(batch), buf, n, ctypes.c_void_p(stream)),
+           "cdd_batch_export_state")
+    return buf.raw
+
+
+def cdd_batch_import_state(batch: int, state: bytes, stream: int = 0) -> None:
+    buf = ctypes.create_string_buffer(bytes(state), len(state))
+    _check(_lib.cdd_batch_import_state(ctypes.c_void_p(batch), buf, len(state), ctypes.c_void_p(stream)),
+           "cdd_batch_import_state")
 
 
 def cdd_execute(plan: int, d_in: int, d_out: int, stream: int = 0) -> None:
@@ -551,6 +575,18 @@ class Batch:
 
     def shifts(self):
         return cdd_batch_shifts(self.handle, self.n_dm, self.n_chan)
+
+    def export_state(self) -> bytes:
+        """The stream state after the blocks executed so far (host bytes)."""
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+        return cdd_batch_export_state(self.handle, stream)
+
+    def import_state(self, state: bytes) -> None:
+        """Continue the stream an export_state() blob describes."""
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+        cdd_batch_import_state(self.handle, state, stream)
 
     def execute(self, vin, out=None):
         import torch

@@ -778,6 +778,120 @@ int cdd_batch_execute(cdd_batch b, const int8_t* d_in, float* d_out, cudaStream_
   return CDD_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+struct BatchStateHeader {
+  uint32_t magic, version;
+  int32_t n_chan, n_dm, n_tiers, n_avg, q, tail_stride;
+  int64_t r_max, hop_max, blocks;
+  double f_center, bandwidth;
+  uint64_t lists;                            // hash of the DM list and the tiers
+};
+constexpr uint32_t kBatchStateMagic = 0x42444453u;   // "SDDB"
+constexpr uint32_t kBatchStateVersion = 1;
+
+size_t batch_tail_bytes(const cdd_batch b) {
+  return (size_t)b->n_chan * (b->n_ov_max > 0 ? b->n_ov_max : 1) * sizeof(char2);
+}
+size_t batch_ring_bytes(const cdd_batch b) {
+  return (size_t)b->n_dm * b->n_chan * (b->r_max > 0 ? b->r_max : 1) * sizeof(float);
+}
+int64_t batch_state_bytes(const cdd_batch b) {
+  return (int64_t)(sizeof(BatchStateHeader) + batch_tail_bytes(b) + batch_ring_bytes(b));
+}
+
+// FNV-1a over the bytes of the DM list and each tier's N and overlap
+uint64_t batch_lists_hash(const cdd_batch b) {
+  uint64_t h = 1469598103934665603ull;
+  auto add = [&](const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+  };
+  add(b->dms.data(), b->dms.size() * sizeof(double));
+  for (const auto& t : b->tiers) {
+    add(&t.n_fft, sizeof(t.n_fft));
+    add(&t.n_ov, sizeof(t.n_ov));
+  }
+  return h;
+}
+
+BatchStateHeader batch_header(const cdd_batch b) {
+  BatchStateHeader h = {};
+  h.magic = kBatchStateMagic;
+  h.version = kBatchStateVersion;
+  h.n_chan = b->n_chan;
+  h.n_dm = b->n_dm;
+  h.n_tiers = (int32_t)b->tiers.size();
+  h.n_avg = b->n_avg;
+  h.q = b->q;
+  h.tail_stride = b->n_ov_max > 0 ? b->n_ov_max : 1;
+  h.r_max = b->r_max;
+  h.hop_max = b->hop_max;
+  h.f_center = b->f_center;
+  h.bandwidth = b->bandwidth;
+  h.lists = batch_lists_hash(b);
+  return h;
+}
+
+bool same_batch_geometry(const BatchStateHeader& a, const BatchStateHeader& c) {
+  return a.magic == c.magic && a.version == c.version && a.n_chan == c.n_chan && a.n_dm == c.n_dm &&
+         a.n_tiers == c.n_tiers && a.n_avg == c.n_avg && a.q == c.q && a.tail_stride == c.tail_stride &&
+         a.r_max == c.r_max && a.hop_max == c.hop_max && a.f_center == c.f_center &&
+         a.bandwidth == c.bandwidth && a.lists == c.lists;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cdd_batch_state_bytes(cdd_batch b, int64_t* bytes) {
+  if (!b || !bytes) return CDD_EINVAL;
+  *bytes = batch_state_bytes(b);
+  return CDD_OK;
+}
+
+int cdd_batch_export_state(cdd_batch b, void* state, int64_t bytes, cudaStream_t s) {
+  if (!b || !state || bytes < batch_state_bytes(b)) return CDD_EINVAL;
+  if (b->sticky) return b->sticky;
+  BatchStateHeader h = batch_header(b);
+  char* out = static_cast<char*>(state);
+  const size_t tb = batch_tail_bytes(b), rb = batch_ring_bytes(b);
+  if (!b->committed) {                       // a fresh stream: zero history
+    h.blocks = 0;
+    memcpy(out, &h, sizeof(h));
+    memset(out + sizeof(h), 0, tb + rb);
+    return CDD_OK;
+  }
+  int dev = -1;
+  BTRY(b, cudaGetDevice(&dev));
+  if (dev != b->device) return CDD_EINVAL;
+  BTRY(b, cudaStreamSynchronize(s));
+  h.blocks = b->blocks;
+  memcpy(out, &h, sizeof(h));
+  BTRY(b, cudaMemcpy(out + sizeof(h), b->d_tail[b->parity], tb, cudaMemcpyDeviceToHost));
+  BTRY(b, cudaMemcpy(out + sizeof(h) + tb, b->d_ring[b->parity], rb, cudaMemcpyDeviceToHost));
+  return CDD_OK;
+}
+
+int cdd_batch_import_state(cdd_batch b, const void* state, int64_t bytes, cudaStream_t s) {
+  if (!b || !state || bytes < batch_state_bytes(b)) return CDD_EINVAL;
+  BatchStateHeader h;
+  memcpy(&h, state, sizeof(h));
+  if (!same_batch_geometry(h, batch_header(b)) || h.blocks < 0) return CDD_EINVAL;
+  int rc = bprepare(b);
+  if (rc) return rc;
+  BTRY(b, cudaStreamSynchronize(s));
+  const char* in = static_cast<const char*>(state) + sizeof(h);
+  const size_t tb = batch_tail_bytes(b), rb = batch_ring_bytes(b);
+  BTRY(b, cudaMemcpy(b->d_tail[0], in, tb, cudaMemcpyHostToDevice));
+  BTRY(b, cudaMemcpy(b->d_ring[0], in + tb, rb, cudaMemcpyHostToDevice));
+  b->parity = 0;
+  b->blocks = h.blocks;
+  return CDD_OK;
+}
+
 int cdd_batch_reset(cdd_batch b) {
   if (!b) return CDD_EINVAL;
   if (b->sticky) return b->sticky;

@@ -265,6 +265,31 @@ def test_stream_state_blob_before_any_launch(cdd):
 
 
 
+def test_batch_state_blob_before_any_launch(cdd):
+    """The batch checkpoint blob: size, fresh-stream export (no GPU touched),
+    refusal of another geometry (DM list, segments per block) or a short
+    buffer."""
+    tiers = (2048, 1024, 512, 256)
+    a = cdd.cdd_batch_create(650.0, 6.25, 64, [5.0, 10.0, 15.0, 20.0], tiers, 4)
+    b = cdd.cdd_batch_create(650.0, 6.25, 64, [5.0, 10.0, 15.0, 21.0], tiers, 4)   # another DM list
+    c = cdd.cdd_batch_create(650.0, 6.25, 64, [5.0, 10.0, 15.0, 20.0], tiers, 4)
+    try:
+        cdd.cdd_batch_set(c, "segments_per_block", cdd.cdd_batch_get(a, "segments_per_block") + 1)
+        n = cdd.cdd_batch_state_bytes(a)
+        r_max = cdd.cdd_batch_get(a, "r_max")
+        assert n >= 80 + 64 * 2 + 4 * 64 * 4 * r_max
+        blob = cdd.cdd_batch_export_state(a)
+        assert len(blob) == n and blob[:4] == b"SDDB"
+        assert not any(blob[80:])                                   # zero history
+        for target, data in ((b, blob), (c, blob), (a, blob[:-1])):
+            with pytest.raises(cdd.CddError) as ei:
+                cdd.cdd_batch_import_state(target, data)
+            assert ei.value.code == cdd.CDD_EINVAL
+    finally:
+        for h in (a, b, c):
+            cdd.cdd_batch_destroy(h)
+
+
 def test_batch_phase_table_form(cdd):
     """The batch keeps the DM = 1 chirp phase as single floats when no phase
     exceeds 16 turns (650 MHz, DMs to 51.5: 12.2 turns) and as two floats

@@ -53,6 +53,29 @@ def test_batch_block_split_is_bit_identical(small):
     assert np.array_equal(a, b) and np.array_equal(a, c)
 
 
+def test_batch_checkpoint_resume_is_bit_identical(small):
+    """Two blocks in one batch, its state exported; a new batch of the same
+    geometry imports it and runs the next two: all four blocks equal the
+    uninterrupted run bit for bit."""
+    import torch
+    from paper_1509_00186_b300.cdd import Batch
+    vin, g, _ = small
+    ref = run_batch(vin, SMALL, 2, 4)
+    with Batch(*SMALL, segments_per_block=2) as b:
+        bs = b.block_samples
+        x = torch.from_numpy(np.ascontiguousarray(vin[: bs * 4])).cuda()
+        first = [b.execute(x[i * bs:(i + 1) * bs]) for i in range(2)]
+        blob = b.export_state()
+        assert b.get("blocks_done") == 2
+    with Batch(*SMALL, segments_per_block=2) as b2:
+        b2.import_state(blob)
+        assert b2.get("blocks_done") == 2
+        rest = [b2.execute(x[i * bs:(i + 1) * bs]) for i in range(2, 4)]
+        torch.cuda.synchronize()
+    got = torch.cat(first + rest, 2).cpu().numpy()
+    assert np.array_equal(got, ref)
+
+
 @pytest.mark.slow
 def test_upgraded_gmrt_batch_full_size_sampled(cuda_device):
     """200 MHz at 650 MHz, 2048 channels, 64 DM trials 20.0..51.5, tiers
