@@ -315,6 +315,7 @@ class BatchGeometry:
     n_avg: int
     tier_of: np.ndarray       # [C] tier index of each channel
     shift: np.ndarray         # [D][C] alignment shifts, integrated samples
+    sideband: int = 1         # +1 upper, -1 lower (channel 0 highest)
 
     def hop(self, t: int) -> int:
         return self.tier_nfft[t] - self.tier_nov[t]
@@ -325,36 +326,41 @@ def batch_geometry(f_center_mhz: float, bandwidth_mhz: float, n_chan: int, dms, 
     """Geometry of the batched form.
 
     The band is cut into len(tier_nfft) equal groups of channels, lowest
-    frequencies first; tier t coherently dedisperses with N_t points.  Its
-    overlap is N_t/32, raised if needed to the dispersion samples of the tier's
-    lowest channel at the largest DM (Sec. 2.2: at least the impulse response)
-    and rounded up to a multiple of n_avg.  Shifts follow the single-DM rule for
-    every DM (Sec. 1.2)."""
+    frequencies first (for a lower sideband, bandwidth < 0, channel 0 is the
+    highest, so tier 0 holds the last channels); tier t coherently dedisperses
+    with N_t points.  Its overlap is N_t/32, raised if needed to the dispersion
+    samples of the tier's lowest channel at the largest DM (Sec. 2.2: at least
+    the impulse response) and rounded up to a multiple of n_avg.  Shifts follow
+    the single-DM rule for every DM (Sec. 1.2), relative to the band's lowest
+    channel."""
     dms = np.asarray(dms, dtype=np.float64)
     n_t = len(tier_nfft)
-    if n_chan % n_t or np.any(dms < 0) or dms.size == 0:
-        raise ValueError("channels must split evenly into tiers; DMs >= 0")
+    if n_chan % n_t or np.any(dms < 0) or dms.size == 0 or bandwidth_mhz == 0:
+        raise ValueError("channels must split evenly into tiers; DMs >= 0; bandwidth non-zero")
     f_lo, chan_bw = channel_lower_edges(f_center_mhz, bandwidth_mhz, n_chan)
     per = n_chan // n_t
+    k = np.arange(n_chan)
+    tier_of = k // per if bandwidth_mhz > 0 else (n_chan - 1 - k) // per
     nov = []
     for t, n in enumerate(tier_nfft):
-        n_d = dispersion_samples(float(f_lo[t * per]), chan_bw, float(dms.max()))
+        n_d = dispersion_samples(float(f_lo[tier_of == t].min()), chan_bw, float(dms.max()))
         ov = max(n // 32, int(math.ceil(n_d)))
         ov = -(-ov // n_avg) * n_avg
         if n & (n - 1) or n <= ov or (n - ov) % n_avg:
             raise ValueError(f"tier {t}: N={n} does not fit overlap {ov} and n_avg {n_avg}")
         nov.append(ov)
-    shift = np.stack([np.rint(-dispersion_delay_s(f_lo, f_lo[0], dm) * chan_bw * 1e6 / n_avg)
+    shift = np.stack([np.rint(-dispersion_delay_s(f_lo, f_lo.min(), dm) * chan_bw * 1e6 / n_avg)
                       for dm in dms]).astype(np.int64)
     return BatchGeometry(n_chan, chan_bw, f_lo, dms, tuple(int(n) for n in tier_nfft),
-                         tuple(nov), int(n_avg), np.arange(n_chan) // per, shift)
+                         tuple(nov), int(n_avg), tier_of, shift, 1 if bandwidth_mhz > 0 else -1)
 
 
-def dedisperse_batch(vin: np.ndarray, geo: BatchGeometry, channels=None, dm_index=None):
+def dedisperse_batch(vin: np.ndarray, geo: BatchGeometry, channels=None, dm_index=None,
+                     taper_kind: str = "none"):
     """Out[d][k][m] for every DM trial d: channel k runs the single-DM steps
-    (overlap-save with its tier's N and overlap, detection, integration,
-    alignment) once per DM.  All channels are cut to the same number of
-    outputs: whole segments of the longest hop."""
+    (overlap-save with its tier's N and overlap, the chirp with the taper,
+    detection, integration, alignment) once per DM.  All channels are cut to
+    the same number of outputs: whole segments of the longest hop."""
     chans = range(geo.n_chan) if channels is None else list(channels)
     dsel = range(len(geo.dms)) if dm_index is None else list(dm_index)
     h_max = max(geo.hop(t) for t in range(len(geo.tier_nfft)))
@@ -365,7 +371,7 @@ def dedisperse_batch(vin: np.ndarray, geo: BatchGeometry, channels=None, dm_inde
         x = unpack(vin[:n_samp], k)
         for di, d in enumerate(dsel):
             filt = dedispersion_filter(float(geo.f_lo_mhz[k]), geo.chan_bw_mhz, float(geo.dms[d]),
-                                       geo.tier_nfft[t])
+                                       geo.tier_nfft[t], taper_kind, geo.sideband)
             v = overlap_save(x, filt, geo.tier_nov[t])
             out[di, ci] = align(integrate(detect(v), geo.n_avg), int(geo.shift[d, k]))
     return out

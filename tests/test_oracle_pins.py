@@ -288,6 +288,34 @@ def test_batch_with_one_dm_and_one_tier_is_the_single_dm_path():
     assert a.shape == b.shape and np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("bandwidth,taper", [(-0.25, "none"), (0.25, "hann"), (-0.25, "welch")])
+def test_batch_lower_sideband_and_taper_reduce_to_the_single_dm_path(bandwidth, taper):
+    """One DM, one tier: a lower-sideband or tapered batch equals the single-DM
+    path of the same band, bit for bit."""
+    rng = np.random.default_rng(23)
+    vin = rng.integers(-60, 60, size=(256 * 6, 4, 2)).astype(np.int8)
+    g1 = O.plan_geometry(325.0, bandwidth, 4, 20.0, 256, 4)
+    gb = O.batch_geometry(325.0, bandwidth, 4, [20.0], (256,), 4)
+    assert gb.sideband == g1.sideband and gb.tier_nov[0] == g1.n_ov
+    assert np.array_equal(gb.shift[0], g1.shift)
+    a = O.dedisperse(vin, g1, taper)
+    b = O.dedisperse_batch(vin, gb, taper_kind=taper)[0]
+    assert np.array_equal(a, b)
+
+
+def test_batch_lower_sideband_tiers_follow_frequency():
+    """Lower sideband: channel 0 is the highest, so the longest transform
+    (tier 0, lowest frequencies) takes the last channels, and the shifts are
+    the upper-sideband band's in reverse channel order."""
+    dms = [10.0, 40.0]
+    gu = O.batch_geometry(650.0, 6.25, 64, dms, (2048, 1024), 4)
+    gl = O.batch_geometry(650.0, -6.25, 64, dms, (2048, 1024), 4)
+    assert np.all(gl.tier_of[:32] == 1) and np.all(gl.tier_of[32:] == 0)
+    assert gl.tier_nov == gu.tier_nov
+    assert np.allclose(gl.f_lo_mhz, gu.f_lo_mhz[::-1])
+    assert np.array_equal(gl.shift, gu.shift[:, ::-1])
+
+
 def test_batch_dm_trials_are_independent_single_dm_runs():
     """Each DM trial of a batch equals the single-DM overlap-save with the same
     N and overlap (one DM at a time, written with the plain steps)."""
