@@ -228,7 +228,9 @@ int cdd_execute_static(double f_center_mhz, double bandwidth_mhz, int n_chan, do
 
 /* ------------------------------------------------------------------------
  * Batched form: n_dm DM trials over one band, the channels cut into n_tiers
- * equal groups (lowest frequencies first) that dedisperse with their own N.
+ * equal groups (lowest frequencies first: the first channels of an upper
+ * sideband, the last of a lower one, bandwidth_mhz < 0 as for a plan) that
+ * dedisperse with their own N.
  * Each segment's forward transform is computed once and shared by every DM
  * trial (Sec. 2.2 deconvolution repeated per trial DM; Sec. 1.2 alignment per
  * trial).  Tier t uses N_t = tier_nfft[t] (power of two, 64..16384) and the
@@ -245,11 +247,12 @@ typedef struct cdd_batch_s* cdd_batch;
 
 int cdd_batch_create(cdd_batch* batch, double f_center_mhz, double bandwidth_mhz, int n_chan,
                      const double* dms, int n_dm, const int* tier_nfft, int n_tiers, int n_avg);
-/* Only CDD_ATTR_SEGMENTS_PER_BLOCK, before the first execute. */
+/* CDD_ATTR_SEGMENTS_PER_BLOCK and CDD_ATTR_TAPER (applied to every DM trial),
+ * before the first execute. */
 int cdd_batch_set(cdd_batch batch, int attr, int64_t value);
 /* SEGMENTS_PER_BLOCK, BLOCK_SAMPLES, N_OUT_PER_BLOCK, R_MAX, BYTES_DEVICE,
  * BLOCKS_DONE, KERNEL_LAUNCHES, N_CHAN, N_AVG, HOP (the longest hop),
- * PHASE_FLOATS. */
+ * PHASE_FLOATS, TAPER. */
 int cdd_batch_get(cdd_batch batch, int attr, int64_t* value);
 /* Geometry of tier t (any output pointer may be NULL). */
 int cdd_batch_tier(cdd_batch batch, int t, int64_t* n_fft, int64_t* n_ov, int64_t* first_chan,
@@ -262,8 +265,9 @@ int cdd_batch_destroy(cdd_batch batch);
 /* Stream checkpoint of a batch, as for a plan (cdd_plan_export_state): the
  * overlap tail of every channel, the carried outputs of every DM plane (the
  * last r_max of each channel) and the block count.  A blob imports only into
- * a batch of the same geometry (frequencies, bandwidth, channels, DM list,
- * tiers, n_avg, segments per block), else CDD_EINVAL with nothing changed.
+ * a batch of the same geometry (frequencies, bandwidth and sideband, channels,
+ * DM list, tiers, n_avg, segments per block, taper), else CDD_EINVAL with
+ * nothing changed.
  *   cdd_batch_state_bytes: size of the blob, host side only.
  *   cdd_batch_export_state: waits for `stream`, then copies the state into
  *     host memory `state` of `bytes` >= the size (a batch that has not run

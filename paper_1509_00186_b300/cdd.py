@@ -549,11 +549,13 @@ class Batch:
     """Owning wrapper of a batched (many-DM, tiered-N) plan."""
 
     def __init__(self, f_center_mhz, bandwidth_mhz, n_chan, dms, tier_nfft, n_avg,
-                 segments_per_block=None):
+                 segments_per_block=None, taper="none"):
         self.handle = cdd_batch_create(f_center_mhz, bandwidth_mhz, n_chan, dms, tier_nfft, n_avg)
         try:
             if segments_per_block is not None:
                 cdd_batch_set(self.handle, "segments_per_block", segments_per_block)
+            if taper != "none":
+                cdd_batch_set(self.handle, "taper", TAPER[taper])
         except Exception:
             cdd_batch_destroy(self.handle)
             raise

@@ -39,6 +39,7 @@ struct BatchArgs {
   float* out;               // [n_dm][C][n_out]
   const float2* t1;         // [n_tchan][N] DM = 1 chirp phase in turns (hi, lo), chirp-pass order
   const float* t1f;         // the same as single floats when every phase is small (else nullptr)
+  const float* taper;       // [N] taper per bin, chirp-pass order (nullptr: none)
   const float2* tw;         // twiddles of this N
   const char2* tail_rd;     // [C][tail_stride] last samples of the previous block
   char2* tail_wr;
@@ -172,8 +173,12 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
       for (int j = 0; j < RL; ++j) x[j] = pb[j];
       dft<RL, -1>(x);
 #pragma unroll
-      for (int kk = 0; kk < RL; ++kk)
-        xk[kk * NG + q] = make_float2(x[kk].x * (1.0f / N), x[kk].y * (1.0f / N));
+      for (int kk = 0; kk < RL; ++kk) {
+        // the taper (Sec. 2.2) depends on the bin only, so it is applied here
+        // once for every DM trial, with the 1/N of the inverse transform
+        const float sc = a.taper ? __ldg(&a.taper[kk * NG + q]) * (1.0f / N) : 1.0f / N;
+        xk[kk * NG + q] = make_float2(x[kk].x * sc, x[kk].y * sc);
+      }
     }
   }
 
@@ -323,9 +328,13 @@ batch_persistent_kernel(const BatchArgs a) {
 }
 
 // T1[kt][idx]: Eq. 3 phase in turns at DM = 1 for channel chan0 + kt and the
-// bin held at table index idx (FP64, split into two floats).
+// bin held at table index idx (FP64, split into two floats).  A lower-sideband
+// channel (sideband < 0; f_base the band's top edge) holds the conjugate
+// mirror: bin j sits where the upper-sideband bin -j does, and its correction
+// is the conjugate, so its table holds minus the phase.
 template <int LOGN>
-__global__ void t1_table_kernel(float2* t1, float* t1f, int n_tchan, int chan0, double f_lo0, double chan_bw) {
+__global__ void t1_table_kernel(float2* t1, float* t1f, int n_tchan, int chan0, double f_base, double chan_bw,
+                                int sideband) {
   using PL = PassPlan<LOGN>;
   constexpr int N = PL::N;
   constexpr int NG = N / PL::RL;
@@ -336,10 +345,11 @@ __global__ void t1_table_kernel(float2* t1, float* t1f, int n_tchan, int chan0, 
     const int idx = (int)(e % N);
     const int pos = (idx % NG) * PL::RL + idx / NG;
     const int bin = position_to_bin<LOGN>(pos);
-    const int sbin = bin < N / 2 ? bin : bin - N;
-    const double f_lo = f_lo0 + chan_bw * (chan0 + kt);
+    const int obin = sideband > 0 ? bin : (N - bin) % N;
+    const int sbin = obin < N / 2 ? obin : obin - N;
+    const double f_lo = sideband > 0 ? f_base + chan_bw * (chan0 + kt) : f_base - chan_bw * (chan0 + kt + 1.0);
     const double f_l = sbin * (chan_bw / N) + 0.5 * chan_bw;
-    const double turns = kDispD * 1e6 * f_l * f_l / ((f_l + f_lo) * f_lo * f_lo);
+    const double turns = (sideband > 0 ? 1.0 : -1.0) * kDispD * 1e6 * f_l * f_l / ((f_l + f_lo) * f_lo * f_lo);
     const float hi = (float)turns;
     if (t1f) t1f[e] = hi;
     else t1[e] = make_float2(hi, (float)(turns - (double)hi));
@@ -389,11 +399,11 @@ cudaError_t launch_batch_t(const BatchArgs& a, cudaStream_t s) {
 }
 
 template <int LOGN>
-cudaError_t launch_t1_t(float2* t1, float* t1f, int n_tchan, int chan0, double f_lo0, double chan_bw,
-                        cudaStream_t s) {
+cudaError_t launch_t1_t(float2* t1, float* t1f, int n_tchan, int chan0, double f_base, double chan_bw,
+                        int sideband, cudaStream_t s) {
   const long long total = (long long)n_tchan << LOGN;
   const unsigned grid = (unsigned)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
-  t1_table_kernel<LOGN><<<grid, 256, 0, s>>>(t1, t1f, n_tchan, chan0, f_lo0, chan_bw);
+  t1_table_kernel<LOGN><<<grid, 256, 0, s>>>(t1, t1f, n_tchan, chan0, f_base, chan_bw, sideband);
   return cudaGetLastError();
 }
 
@@ -408,10 +418,46 @@ cudaError_t launch_batch(int logn, const BatchArgs& a, cudaStream_t s) {
   }
 }
 
-cudaError_t launch_t1(int logn, float2* t1, float* t1f, int n_tchan, int chan0, double f_lo0, double chan_bw,
-                      cudaStream_t s) {
+// taper[idx] for the bin held at chirp-pass index idx: Hann sin^2(pi x) or
+// Welch 1 - (2x - 1)^2, x = f_l / chan_bw (Sec. 2.2), mirrored for a lower
+// sideband (FP64, rounded).
+template <int LOGN>
+__global__ void batch_taper_kernel(float* tap, int taper, int sideband) {
+  using PL = PassPlan<LOGN>;
+  constexpr int N = PL::N;
+  constexpr int NG = N / PL::RL;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
+    const int pos = (idx % NG) * PL::RL + idx / NG;
+    const int bin = position_to_bin<LOGN>(pos);
+    const int obin = sideband > 0 ? bin : (N - bin) % N;
+    const int sbin = obin < N / 2 ? obin : obin - N;
+    const double x = (double)sbin / N + 0.5;
+    double w = 1.0;
+    if (taper == CDD_TAPER_HANN) {
+      const double sx = sinpi(x);
+      w = sx * sx;
+    } else if (taper == CDD_TAPER_WELCH) {
+      const double y = 2.0 * x - 1.0;
+      w = 1.0 - y * y;
+    }
+    tap[idx] = (float)w;
+  }
+}
+
+cudaError_t launch_batch_taper(int logn, float* tap, int taper, int sideband, cudaStream_t s) {
   switch (logn) {
-#define X(L) case L: return launch_t1_t<L>(t1, t1f, n_tchan, chan0, f_lo0, chan_bw, s);
+#define X(L) case L: batch_taper_kernel<L><<<((1 << L) + 255) / 256, 256, 0, s>>>(tap, taper, sideband); break;
+    CDD_BATCH_CASES(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_t1(int logn, float2* t1, float* t1f, int n_tchan, int chan0, double f_base, double chan_bw,
+                      int sideband, cudaStream_t s) {
+  switch (logn) {
+#define X(L) case L: return launch_t1_t<L>(t1, t1f, n_tchan, chan0, f_base, chan_bw, sideband, s);
     CDD_BATCH_CASES(X)
 #undef X
     default: return cudaErrorInvalidValue;
@@ -427,10 +473,14 @@ struct cdd_batch_s {
   struct Tier {
     int n_fft = 0, logn = 0, n_ov = 0, hop = 0, chan0 = 0, n_tchan = 0;
     float2* d_tw = nullptr;
+    float* d_taper = nullptr;              // [N] taper per bin (CDD_ATTR_TAPER set), else nullptr
     float2* d_t1 = nullptr;
     float* d_t1f = nullptr;
   };
   double f_center = 0, bandwidth = 0, chan_bw = 0, f_lo0 = 0;
+  int sideband = 1;                      // +1 upper (channel 0 lowest), -1 lower (channel 0 highest)
+  double f_base = 0;                     // upper: f_lo0; lower: the band's top edge
+  int taper = CDD_TAPER_NONE;
   int n_chan = 0, n_avg = 0, n_dm = 0;
   std::vector<double> dms;
   std::vector<Tier> tiers;
@@ -489,6 +539,7 @@ int64_t n_out(const cdd_batch b) { return block_samples(b) / b->n_avg; }
 void bfree(cdd_batch b) {
   for (auto& t : b->tiers) {
     cudaFree(t.d_tw);
+    cudaFree(t.d_taper);
     cudaFree(t.d_t1);
     cudaFree(t.d_t1f);
   }
@@ -547,6 +598,7 @@ int bcommit_once(cdd_batch b) {
     const size_t segs = (size_t)t.n_tchan * (rows / t.hop);
     if (segs * t.n_fft > xs) xs = segs * t.n_fft;
     if ((rc = balloc(b, &t.d_tw, (size_t)cdd::twiddle_table_len(t.logn) * sizeof(float2)))) return rc;
+    if (b->taper != CDD_TAPER_NONE && (rc = balloc(b, &t.d_taper, (size_t)t.n_fft * sizeof(float)))) return rc;
     if (b->t1_single) {
       if ((rc = balloc(b, &t.d_t1f, (size_t)t.n_tchan * t.n_fft * sizeof(float)))) return rc;
     } else if ((rc = balloc(b, &t.d_t1, (size_t)t.n_tchan * t.n_fft * sizeof(float2)))) {
@@ -569,7 +621,8 @@ int bcommit_once(cdd_batch b) {
   for (auto& t : b->tiers) {
     if (e == cudaSuccess) e = cdd::launch_twiddle_table(t.logn, t.d_tw, s);
     if (e == cudaSuccess)
-      e = cdd::launch_t1(t.logn, t.d_t1, t.d_t1f, t.n_tchan, t.chan0, b->f_lo0, b->chan_bw, s);
+      e = cdd::launch_t1(t.logn, t.d_t1, t.d_t1f, t.n_tchan, t.chan0, b->f_base, b->chan_bw, b->sideband, s);
+    if (e == cudaSuccess && t.d_taper) e = cdd::launch_batch_taper(t.logn, t.d_taper, b->taper, b->sideband, s);
   }
   if (e == cudaSuccess && (rc = bzero_state(b, s)) != CDD_OK) {
     cudaStreamDestroy(s);
@@ -606,7 +659,7 @@ int cdd_batch_create(cdd_batch* out, double f_center_mhz, double bandwidth_mhz, 
   if (!out) return CDD_EINVAL;
   *out = nullptr;
   if (!dms || n_dm <= 0 || !tier_nfft || n_tiers <= 0 || n_chan <= 0 || n_chan % n_tiers ||
-      n_avg <= 0 || !(f_center_mhz > 0) || !(bandwidth_mhz > 0))
+      n_avg <= 0 || !(f_center_mhz > 0) || !isfinite(bandwidth_mhz) || bandwidth_mhz == 0)
     return CDD_EINVAL;
   cdd_batch b = new (std::nothrow) cdd_batch_s();
   if (!b) return CDD_ENOMEM;
@@ -615,8 +668,10 @@ int cdd_batch_create(cdd_batch* out, double f_center_mhz, double bandwidth_mhz, 
   b->n_chan = n_chan;
   b->n_avg = n_avg;
   b->n_dm = n_dm;
-  b->chan_bw = bandwidth_mhz / n_chan;
-  b->f_lo0 = f_center_mhz - bandwidth_mhz / 2.0;
+  b->sideband = bandwidth_mhz > 0 ? 1 : -1;
+  b->chan_bw = fabs(bandwidth_mhz) / n_chan;
+  b->f_lo0 = f_center_mhz - fabs(bandwidth_mhz) / 2.0;             // the band's lowest edge
+  b->f_base = b->sideband > 0 ? b->f_lo0 : f_center_mhz + fabs(bandwidth_mhz) / 2.0;
   b->dms.assign(dms, dms + n_dm);
   double dm_max = 0;
   for (double d : b->dms) {
@@ -635,11 +690,14 @@ int cdd_batch_create(cdd_batch* out, double f_center_mhz, double bandwidth_mhz, 
   for (int t = 0; t < n_tiers && rc == CDD_OK; ++t) {
     cdd_batch_s::Tier tr;
     tr.n_fft = tier_nfft[t];
-    tr.chan0 = t * per;
+    // tiers run from the lowest frequencies up: the first channels of an upper
+    // sideband, the last of a lower one
+    tr.chan0 = b->sideband > 0 ? t * per : n_chan - (t + 1) * per;
     tr.n_tchan = per;
     // overlap: N/32, raised to the tier's lowest-channel smear at the largest DM,
     // rounded up to a multiple of n_avg
-    const double f = b->f_lo0 + b->chan_bw * tr.chan0;
+    const double f = b->sideband > 0 ? b->f_base + b->chan_bw * tr.chan0
+                                     : b->f_base - b->chan_bw * (tr.chan0 + per);
     const double n_d = kDispDHost * dm_max * (pow(f, -2.0) - pow(f + b->chan_bw, -2.0)) * b->chan_bw * 1e6;
     long long ov = tr.n_fft / 32;
     if ((long long)ceil(n_d) > ov) ov = (long long)ceil(n_d);
@@ -660,8 +718,8 @@ int cdd_batch_create(cdd_batch* out, double f_center_mhz, double bandwidth_mhz, 
     for (int d = 0; d < n_dm && rc == CDD_OK; ++d) {
       cdd::Geometry g{};
       g.f_lo0 = b->f_lo0;
-      g.sideband = 1;
-      g.f_base = b->f_lo0;
+      g.sideband = b->sideband;
+      g.f_base = b->f_base;
       g.f_ref = b->f_lo0;
       g.chan_bw = b->chan_bw;
       g.dm = b->dms[d];
@@ -692,6 +750,11 @@ int cdd_batch_create(cdd_batch* out, double f_center_mhz, double bandwidth_mhz, 
 int cdd_batch_set(cdd_batch b, int attr, int64_t value) {
   if (!b) return CDD_EINVAL;
   if (b->committed) return CDD_ESTATE;
+  if (attr == CDD_ATTR_TAPER) {
+    if (value < CDD_TAPER_NONE || value > CDD_TAPER_WELCH) return CDD_EINVAL;
+    b->taper = (int)value;
+    return CDD_OK;
+  }
   if (attr != CDD_ATTR_SEGMENTS_PER_BLOCK) return CDD_EINVAL;
   if (value < 1 || value * b->hop_max * b->n_chan > ((int64_t)1 << 40)) return CDD_EINVAL;
   if (value * b->hop_max / b->n_avg < b->r_max) return CDD_EINVAL;
@@ -715,6 +778,7 @@ int cdd_batch_get(cdd_batch b, int attr, int64_t* v) {
     case CDD_ATTR_N_CHAN: *v = b->n_chan; break;
     case CDD_ATTR_N_AVG: *v = b->n_avg; break;
     case CDD_ATTR_HOP: *v = b->hop_max; break;
+    case CDD_ATTR_TAPER: *v = b->taper; break;
     default: return CDD_EINVAL;
   }
   return CDD_OK;
@@ -751,6 +815,7 @@ int cdd_batch_execute(cdd_batch b, const int8_t* d_in, float* d_out, cudaStream_
     a.out = d_out;
     a.t1 = t.d_t1;
     a.t1f = t.d_t1f;
+    a.taper = t.d_taper;
     a.tw = t.d_tw;
     a.tail_rd = b->d_tail[b->parity];
     a.tail_wr = b->d_tail[b->parity ^ 1];
@@ -784,7 +849,7 @@ namespace {
 
 struct BatchStateHeader {
   uint32_t magic, version;
-  int32_t n_chan, n_dm, n_tiers, n_avg, q, tail_stride;
+  int32_t n_chan, n_dm, n_tiers, n_avg, q, tail_stride, taper, reserved;
   int64_t r_max, hop_max, blocks;
   double f_center, bandwidth;
   uint64_t lists;                            // hash of the DM list and the tiers
@@ -827,6 +892,7 @@ BatchStateHeader batch_header(const cdd_batch b) {
   h.n_avg = b->n_avg;
   h.q = b->q;
   h.tail_stride = b->n_ov_max > 0 ? b->n_ov_max : 1;
+  h.taper = b->taper;
   h.r_max = b->r_max;
   h.hop_max = b->hop_max;
   h.f_center = b->f_center;
@@ -838,6 +904,7 @@ BatchStateHeader batch_header(const cdd_batch b) {
 bool same_batch_geometry(const BatchStateHeader& a, const BatchStateHeader& c) {
   return a.magic == c.magic && a.version == c.version && a.n_chan == c.n_chan && a.n_dm == c.n_dm &&
          a.n_tiers == c.n_tiers && a.n_avg == c.n_avg && a.q == c.q && a.tail_stride == c.tail_stride &&
+         a.taper == c.taper &&
          a.r_max == c.r_max && a.hop_max == c.hop_max && a.f_center == c.f_center &&
          a.bandwidth == c.bandwidth && a.lists == c.lists;
 }

@@ -166,6 +166,8 @@ BATCH_GEOMS = [
     (650.0, 200.0, 2048, 20.0 + 0.5 * np.arange(64), (16384, 8192, 4096, 2048), 16),
     (650.0, 6.25, 64, [5.0, 10.0, 15.0, 20.0], (2048, 1024, 512, 256), 4),
     (325.0, 0.25, 4, [20.0], (256,), 4),
+    (650.0, -6.25, 64, [5.0, 10.0, 15.0, 20.0], (2048, 1024, 512, 256), 4),   # lower sideband
+    (325.0, -0.25, 4, [20.0], (256,), 4),
 ]
 
 
@@ -178,7 +180,8 @@ def test_batch_geometry_matches_oracle(cdd, geo):
         for t in range(len(tiers)):
             n_fft, n_ov, chan0, n_t = cdd.cdd_batch_tier(b, t)
             assert (n_fft, n_ov) == (g.tier_nfft[t], g.tier_nov[t])
-            assert chan0 == t * (n_chan // len(tiers)) and n_t == n_chan // len(tiers)
+            in_tier = np.flatnonzero(g.tier_of == t)              # tiers by frequency
+            assert chan0 == in_tier.min() and n_t == in_tier.size == n_chan // len(tiers)
         assert np.array_equal(np.array(cdd.cdd_batch_shifts(b, len(dms), n_chan)), g.shift)
         assert cdd.cdd_batch_get(b, "r_max") == int(g.shift.max())
         n_out = cdd.cdd_batch_get(b, "n_out_per_block")
@@ -198,6 +201,11 @@ def test_batch_rejects_bad_requests(cdd):
         cdd.cdd_batch_create(650.0, 6.25, 63, [5.0], (2048, 1024), 4)
     b = cdd.cdd_batch_create(650.0, 6.25, 64, [5.0, 20.0], (2048, 1024, 512, 256), 4)
     try:
+        assert cdd.cdd_batch_get(b, "taper") == 0
+        with pytest.raises(cdd.CddError):          # not a taper
+            cdd.cdd_batch_set(b, "taper", 3)
+        cdd.cdd_batch_set(b, "taper", cdd.TAPER["hann"])
+        assert cdd.cdd_batch_get(b, "taper") == 1
         r_max = cdd.cdd_batch_get(b, "r_max")
         with pytest.raises(cdd.CddError):          # a block shorter than the largest delay
             cdd.cdd_batch_set(b, "segments_per_block", 1) if r_max > 1984 // 4 else \
@@ -277,10 +285,10 @@ def test_batch_state_blob_before_any_launch(cdd):
         cdd.cdd_batch_set(c, "segments_per_block", cdd.cdd_batch_get(a, "segments_per_block") + 1)
         n = cdd.cdd_batch_state_bytes(a)
         r_max = cdd.cdd_batch_get(a, "r_max")
-        assert n >= 80 + 64 * 2 + 4 * 64 * 4 * r_max
+        assert n >= 88 + 64 * 2 + 4 * 64 * 4 * r_max
         blob = cdd.cdd_batch_export_state(a)
         assert len(blob) == n and blob[:4] == b"SDDB"
-        assert not any(blob[80:])                                   # zero history
+        assert not any(blob[88:])                                   # zero history
         for target, data in ((b, blob), (c, blob), (a, blob[:-1])):
             with pytest.raises(cdd.CddError) as ei:
                 cdd.cdd_batch_import_state(target, data)

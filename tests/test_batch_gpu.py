@@ -12,10 +12,10 @@ TOL = 1e-5
 SMALL = (650.0, 6.25, 64, [5.0, 10.0, 15.0, 20.0], (2048, 1024, 512, 256), 4)
 
 
-def run_batch(vin, args, q, n_blocks):
+def run_batch(vin, args, q, n_blocks, taper="none"):
     import torch
     from paper_1509_00186_b300.cdd import Batch
-    with Batch(*args, segments_per_block=q) as b:
+    with Batch(*args, segments_per_block=q, taper=taper) as b:
         bs = b.block_samples
         x = torch.from_numpy(np.ascontiguousarray(vin[: bs * n_blocks])).cuda()
         outs = [b.execute(x[i * bs:(i + 1) * bs]) for i in range(n_blocks)]
@@ -51,6 +51,20 @@ def test_batch_block_split_is_bit_identical(small):
     b = run_batch(vin, SMALL, 2, 4)
     c = run_batch(vin, SMALL, 1, 8)
     assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("bandwidth,taper", [(-6.25, "none"), (6.25, "hann"), (-6.25, "welch")])
+def test_batch_lower_sideband_and_taper(cuda_device, bandwidth, taper):
+    """A lower-sideband band (tiers by frequency: the longest transform on the
+    last channels) and tapered chirps, every DM plane against the oracle."""
+    args = (650.0, bandwidth, 64, [5.0, 10.0, 15.0, 20.0], (2048, 1024, 512, 256), 4)
+    g = O.batch_geometry(*args)
+    vin = complex_int8_voltages(28, 1984 * 4, 64, 20.0)
+    want = O.dedisperse_batch(vin, g, taper_kind=taper)
+    got = run_batch(vin, args, 2, 2, taper)
+    assert got.shape == want.shape
+    for d in range(len(args[3])):
+        assert O.rel_rms(got[d], want[d]) <= TOL, d
 
 
 def test_batch_checkpoint_resume_is_bit_identical(small):
