@@ -98,7 +98,7 @@ __device__ __forceinline__ void dm_chirp1x2(float2 t1, float2 dmx, float2 ndm, f
 // spectrum to its scratch row, then every DM trial.  SH: tw is in shared
 // memory.  sync() is the group's barrier.  Returns true when buf (the power
 // samples) was read after the last barrier.
-template <int LOGN, bool SH, bool T1F, class Sync>
+template <int LOGN, bool SH, bool T1F, bool TAP, class Sync>
 __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, const float2* tw, int lt,
                                               bool active, int w, Sync sync) {
   using PL = PassPlan<LOGN>;
@@ -172,12 +172,19 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
 #pragma unroll
       for (int j = 0; j < RL; ++j) x[j] = pb[j];
       dft<RL, -1>(x);
+      // the taper (Sec. 2.2) depends on the bin only, so it is applied here
+      // once for every DM trial, with the 1/N of the inverse transform (a
+      // compile-time switch: the untapered kernels keep their own code)
+      if constexpr (TAP) {
 #pragma unroll
-      for (int kk = 0; kk < RL; ++kk) {
-        // the taper (Sec. 2.2) depends on the bin only, so it is applied here
-        // once for every DM trial, with the 1/N of the inverse transform
-        const float sc = a.taper ? __ldg(&a.taper[kk * NG + q]) * (1.0f / N) : 1.0f / N;
-        xk[kk * NG + q] = make_float2(x[kk].x * sc, x[kk].y * sc);
+        for (int kk = 0; kk < RL; ++kk) {
+          const float sc = __ldg(&a.taper[kk * NG + q]) * (1.0f / N);
+          xk[kk * NG + q] = make_float2(x[kk].x * sc, x[kk].y * sc);
+        }
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < RL; ++kk)
+          xk[kk * NG + q] = make_float2(x[kk].x * (1.0f / N), x[kk].y * (1.0f / N));
       }
     }
   }
@@ -279,7 +286,7 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
   return !in_lanes;
 }
 
-template <int LOGN, bool T1F>
+template <int LOGN, bool T1F, bool TAP>
 __global__ void __launch_bounds__(Cfg<LOGN>::THREADS, Cfg<LOGN>::MINB)
 batch_kernel(const BatchArgs a) {
   using PL = PassPlan<LOGN>;
@@ -290,7 +297,7 @@ batch_kernel(const BatchArgs a) {
   float2* buf = smem + g * CF::SEG_F2;
   const int w = blockIdx.x * CF::G + g;
   const bool active = w < a.n_tchan * a.q;
-  batch_segment<LOGN, false, T1F>(a, buf, a.tw, lt, active, w, [] { __syncthreads(); });
+  batch_segment<LOGN, false, T1F, TAP>(a, buf, a.tw, lt, active, w, [] { __syncthreads(); });
 }
 
 // Persistent form for N = 8192: one CTA per SM, two groups of 256
@@ -305,7 +312,7 @@ struct BatchPersist {
   static constexpr size_t SMEM = (size_t(PL::TW_LEN) + size_t(GROUPS) * padded_len(PL::N)) * sizeof(float2);
 };
 
-template <int LOGN, bool T1F>
+template <int LOGN, bool T1F, bool TAP>
 __global__ void __launch_bounds__(BatchPersist<LOGN>::THREADS, 1)
 batch_persistent_kernel(const BatchArgs a) {
   using PL = PassPlan<LOGN>;
@@ -322,7 +329,7 @@ batch_persistent_kernel(const BatchArgs a) {
   auto sync = [bar] { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(T) : "memory"); };
   const int work = a.n_tchan * a.q;
   for (int w = blockIdx.x * BP::GROUPS + g; w < work; w += gridDim.x * BP::GROUPS) {
-    if (batch_segment<LOGN, true, T1F>(a, buf, tws, lt, true, w, sync))
+    if (batch_segment<LOGN, true, T1F, TAP>(a, buf, tws, lt, true, w, sync))
       sync();                                  // buf is rewritten by the next work item
   }
 }
@@ -356,7 +363,7 @@ __global__ void t1_table_kernel(float2* t1, float* t1f, int n_tchan, int chan0, 
   }
 }
 
-template <int LOGN, bool T1F>
+template <int LOGN, bool T1F, bool TAP>
 cudaError_t launch_batch_tt(const BatchArgs& a, cudaStream_t s) {
   using CF = Cfg<LOGN>;
   static bool attr_set[128] = {};
@@ -365,7 +372,7 @@ cudaError_t launch_batch_tt(const BatchArgs& a, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
   if (!attr_set[dev]) {
-    e = cudaFuncSetAttribute(batch_kernel<LOGN, T1F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CF::SMEM);
+    e = cudaFuncSetAttribute(batch_kernel<LOGN, T1F, TAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CF::SMEM);
     if (e != cudaSuccess) return e;
     attr_set[dev] = true;
   }
@@ -376,7 +383,7 @@ cudaError_t launch_batch_tt(const BatchArgs& a, cudaStream_t s) {
     using BP = BatchPersist<LOGN>;
     static bool pset[128] = {};
     if (!pset[dev]) {
-      e = cudaFuncSetAttribute(batch_persistent_kernel<LOGN, T1F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(batch_persistent_kernel<LOGN, T1F, TAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)BP::SMEM);
       if (e != cudaSuccess) return e;
       pset[dev] = true;
@@ -386,16 +393,17 @@ cudaError_t launch_batch_tt(const BatchArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const long long need = (work + BP::GROUPS - 1) / BP::GROUPS;
     const unsigned grid = (unsigned)(need < sms ? need : sms);
-    batch_persistent_kernel<LOGN, T1F><<<grid, BP::THREADS, BP::SMEM, s>>>(a);
+    batch_persistent_kernel<LOGN, T1F, TAP><<<grid, BP::THREADS, BP::SMEM, s>>>(a);
     return cudaGetLastError();
   }
-  batch_kernel<LOGN, T1F><<<(unsigned)((work + CF::G - 1) / CF::G), CF::THREADS, CF::SMEM, s>>>(a);
+  batch_kernel<LOGN, T1F, TAP><<<(unsigned)((work + CF::G - 1) / CF::G), CF::THREADS, CF::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int LOGN>
 cudaError_t launch_batch_t(const BatchArgs& a, cudaStream_t s) {
-  return a.t1f ? launch_batch_tt<LOGN, true>(a, s) : launch_batch_tt<LOGN, false>(a, s);
+  if (a.taper) return a.t1f ? launch_batch_tt<LOGN, true, true>(a, s) : launch_batch_tt<LOGN, false, true>(a, s);
+  return a.t1f ? launch_batch_tt<LOGN, true, false>(a, s) : launch_batch_tt<LOGN, false, false>(a, s);
 }
 
 template <int LOGN>
