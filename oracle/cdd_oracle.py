@@ -419,6 +419,7 @@ class FullbandGeometry:
     hop: int
     n_avg: int
     n_disp: float             # dispersion samples across the whole band
+    sideband: int = 1         # +1 upper; -1 lower: the series is the band inverted
 
 
 def fullband_geometry(f_center_mhz: float, bandwidth_mhz: float, n_chan: int, dm: float,
@@ -427,8 +428,10 @@ def fullband_geometry(f_center_mhz: float, bandwidth_mhz: float, n_chan: int, dm
     dispersion samples across the band (real samples at 2B).  The overlap is
     the dispersion samples rounded up to a whole number of frames and of
     integration windows, so segments and blocks stay on frame boundaries."""
-    if n_chan <= 0 or n_avg <= 0 or bandwidth_mhz <= 0 or dm < 0:
-        raise ValueError("n_chan, n_avg, bandwidth must be positive and DM >= 0")
+    if n_chan <= 0 or n_avg <= 0 or bandwidth_mhz == 0 or dm < 0:
+        raise ValueError("n_chan, n_avg must be positive, bandwidth non-zero and DM >= 0")
+    sideband = 1 if bandwidth_mhz > 0 else -1
+    bandwidth_mhz = abs(bandwidth_mhz)
     f_lo = f_center_mhz - bandwidth_mhz / 2.0
     fs = 2.0 * bandwidth_mhz
     n_d = float(dispersion_delay_s(f_lo, f_lo + bandwidth_mhz, dm) * fs * 1e6)
@@ -442,7 +445,7 @@ def fullband_geometry(f_center_mhz: float, bandwidth_mhz: float, n_chan: int, dm
     if n_fft & (n_fft - 1) or n_fft <= n_ov or (n_fft - n_ov) % unit:
         raise ValueError(f"N={n_fft} does not fit overlap {n_ov}")
     return FullbandGeometry(f_lo, bandwidth_mhz, n_chan, frame, fs, float(dm), int(n_fft),
-                            int(n_ov), int(n_fft - n_ov), int(n_avg), n_d)
+                            int(n_ov), int(n_fft - n_ov), int(n_avg), n_d, sideband)
 
 
 def inverse_channelise(vin: np.ndarray) -> np.ndarray:
@@ -457,10 +460,14 @@ def inverse_channelise(vin: np.ndarray) -> np.ndarray:
 def fullband_filter(geo: FullbandGeometry, taper_kind: str = "none") -> np.ndarray:
     """The chirp function on the N/2 + 1 bins of the long real FFT (Sec. 4.3):
     bin j sits f_l = j * fs / N above the band's lower edge f_o (Eq. 3 with f_o
-    the band edge, Sec. 2.1)."""
-    f_l = np.arange(geo.n_fft // 2 + 1) * (geo.fs_mhz / geo.n_fft)
+    the band edge, Sec. 2.1).  A lower-sideband series is the band inverted
+    (bin j at B - j * fs / N above f_o, with the conjugate phase), so its
+    correction is the conjugate of the upper-sideband one at that offset."""
+    f_bb = np.arange(geo.n_fft // 2 + 1) * (geo.fs_mhz / geo.n_fft)
+    f_l = f_bb if geo.sideband > 0 else geo.bandwidth_mhz - f_bb
     h = np.exp(1j * chirp_phase(geo.f_lo_mhz, f_l, geo.dm))
-    return np.conj(h) * taper(f_l, geo.bandwidth_mhz, taper_kind)
+    corr = np.conj(h) if geo.sideband > 0 else h
+    return corr * taper(f_l, geo.bandwidth_mhz, taper_kind)
 
 
 def dedisperse_fullband(vin: np.ndarray, geo: FullbandGeometry, return_voltages: bool = False):

@@ -416,6 +416,30 @@ def test_fullband_geometry_and_the_paper_max_dm():
             3000 / 750 if f == 610.0 else 480 / 120, rel=0.1)
 
 
+def test_fullband_lower_sideband_is_the_inverted_upper_band():
+    """A lower-sideband series is the upper one spectrally inverted,
+    x_L[n] = (-1)^n x_U[n]: frame bin b of the lower band holds the conjugate
+    of the upper band's bin C - b (DC and Nyquist left empty).  Dedispersed
+    with its own (mirrored, conjugate) chirp it must give the upper band's
+    intensities; with the upper band's chirp it must not."""
+    rng = np.random.default_rng(41)
+    C, n_frames = 16, 64 * 12
+    spec = rng.integers(-40, 40, size=(n_frames, C, 2)).astype(np.int8)
+    spec[:, 0, :] = 0                                            # no DC
+    lsb = np.zeros_like(spec)
+    lsb[:, 1:, 0] = spec[:, :0:-1, 0]                            # bin b <- conj of bin C - b
+    lsb[:, 1:, 1] = -spec[:, :0:-1, 1]
+    xu, xl = O.inverse_channelise(spec), O.inverse_channelise(lsb)
+    assert np.allclose(xl, xu * (-1.0) ** np.arange(xu.size), atol=1e-12)
+    gu = O.fullband_geometry(325.0, 1.0, C, 30.0, 0, 4)
+    gl = O.fullband_geometry(325.0, -1.0, C, 30.0, 0, 4)
+    assert (gl.n_fft, gl.n_ov, gl.sideband) == (gu.n_fft, gu.n_ov, -1)
+    a, b = O.dedisperse_fullband(spec, gu), O.dedisperse_fullband(lsb, gl)
+    assert np.allclose(b, a, rtol=1e-9, atol=1e-9 * np.abs(a).max())
+    wrong = O.dedisperse_fullband(lsb, gu)                       # upper-sideband chirp on it
+    assert O.rel_rms(wrong, a) > 1e-2
+
+
 def test_fullband_recovers_a_dispersed_impulse():
     """A real impulse dispersed with the cold-plasma 1/f phase over the whole
     band, recorded as frames of 2C-point spectra, comes back as an impulse at
