@@ -291,7 +291,10 @@ int cdd_batch_import_state(cdd_batch batch, const void* state, int64_t bytes, cu
  * across the band), the chirp of Eq. 3 with f_o the band's lower edge on every
  * bin, inverse transforms, overlap-save with an overlap of the dispersion
  * samples rounded up to whole frames and integration windows, squaring and
- * integration over n_avg samples (a power of two).  Upper sideband only.
+ * integration over n_avg samples (a power of two).  bandwidth_mhz < 0: a
+ * lower sideband, whose real series is the band inverted (frame bin b at
+ * |B| - b |B|/C above the lower edge); its chirp is the conjugate at that
+ * mirrored offset.
  *   d_in: device int8 [frames][C][2], frames = q*h/(2C) per block
  *         (CDD_ATTR_BLOCK_SAMPLES reports frames for this plan type);
  *   d_out: device float [q*h/n_avg], the band's intensity series.

@@ -370,11 +370,13 @@ __global__ void fb_twiddle_kernel(float2* hi, float2* lo, long long n) {
 }
 
 // chirp[qq * NS + idx] for the bin held there: Hermitian (bins above N/2 take
-// the conjugate of their mirror) so the inverse transform stays real.
+// the conjugate of their mirror) so the inverse transform stays real.  A
+// lower-sideband series (sideband < 0) is the band inverted: bin j sits
+// B - j fs / N above the lower edge and takes the conjugate correction.
 template <int LOGS>
 __global__ void fb_chirp_kernel(float2* chirp, long long n, int n_outer, const int* radix_out,
                                 const long long* stride_out, const long long* rprod_out,
-                                double f_lo, double fs, double dm) {
+                                double f_lo, double fs, double dm, int sideband) {
   using PL = PassPlan<LOGS>;
   constexpr int NS = PL::N;
   constexpr int NG = NS / PL::RL;
@@ -391,14 +393,17 @@ __global__ void fb_chirp_kernel(float2* chirp, long long n, int n_outer, const i
     const int pos = (idx % NG) * PL::RL + idx / NG;
     const long long bin = b_out + l_out * position_to_bin<LOGS>(pos);
     const long long mb = bin <= n / 2 ? bin : n - bin;     // mirror for the upper half
-    const double f_l = (double)mb * (fs / (double)n);
+    const double f_bb = (double)mb * (fs / (double)n);
+    const double f_l = sideband > 0 ? f_bb : 0.5 * fs - f_bb;
     const double turns = kDispD * 1e6 * dm * f_l * f_l / ((f_l + f_lo) * f_lo * f_lo);
     const double frac = turns - rint(turns);
     double sn, cs;
     sincospi(2.0 * frac, &sn, &cs);
     const double sc = 1.0 / (double)n;
-    // exp(-i Phi) / N below N/2 (and at it); the conjugate above
-    chirp[e] = make_float2((float)(cs * sc), (float)((bin <= n / 2 ? -sn : sn) * sc));
+    // exp(-i Phi) / N below N/2 (and at it), the conjugate above; both
+    // conjugated for a lower sideband
+    const double s_im = (bin <= n / 2 ? -sn : sn) * (sideband > 0 ? 1.0 : -1.0);
+    chirp[e] = make_float2((float)(cs * sc), (float)(s_im * sc));
   }
 }
 
@@ -521,10 +526,10 @@ cudaError_t launch_outer(bool forward, bool edge, int radix, float2* w, const fl
 
 cudaError_t launch_fb_chirp(int logs, float2* chirp, long long n, int n_outer, const int* radix,
                             const long long* stride, const long long* rprod, double f_lo, double fs,
-                            double dm, cudaStream_t s) {
+                            double dm, int sideband, cudaStream_t s) {
   const unsigned grid = grid_for(n);
   switch (logs) {
-#define X(L) case L: fb_chirp_kernel<L><<<grid, 256, 0, s>>>(chirp, n, n_outer, radix, stride, rprod, f_lo, fs, dm); break;
+#define X(L) case L: fb_chirp_kernel<L><<<grid, 256, 0, s>>>(chirp, n, n_outer, radix, stride, rprod, f_lo, fs, dm, sideband); break;
     CDD_FB_CASES(X)
 #undef X
     default: return cudaErrorInvalidValue;
@@ -539,6 +544,7 @@ cudaError_t launch_fb_chirp(int logs, float2* chirp, long long n, int n_outer, c
 
 struct cdd_fullband_s {
   double f_center = 0, bandwidth = 0, dm = 0, f_lo = 0, fs = 0, n_disp = 0;
+  int sideband = 1;                          // -1: lower sideband, the series is the band inverted
   int n_chan = 0, frame = 0, logf = 0, n_avg = 0;
   long long n_fft = 0, n_ov = 0, hop = 0;
   int logs = 0;                              // log2 L_mid
@@ -636,7 +642,7 @@ int fcommit_once(cdd_fullband f) {
   }
   if (e == cudaSuccess)
     e = cdd::launch_fb_chirp(f->logs, f->d_chirp, n, (int)f->radix_out.size(), f->d_radix, f->d_stride,
-                             f->d_rprod, f->f_lo, f->fs, f->dm, s);
+                             f->d_rprod, f->f_lo, f->fs, f->dm, f->sideband, s);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i)
     e = cudaMemsetAsync(f->d_ts[i], 0, (size_t)ts_len(f) * sizeof(float), s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -691,9 +697,11 @@ int cdd_fullband_create(cdd_fullband* out, double f_center_mhz, double bandwidth
                         double dm, long long n_fft, int n_avg) {
   if (!out) return CDD_EINVAL;
   *out = nullptr;
-  if (!(f_center_mhz > 0) || !(bandwidth_mhz > 0) || n_chan <= 0 || !(dm >= 0) || !isfinite(dm) ||
-      n_avg <= 0 || n_fft < 0)
+  if (!(f_center_mhz > 0) || !isfinite(bandwidth_mhz) || bandwidth_mhz == 0 || n_chan <= 0 || !(dm >= 0) ||
+      !isfinite(dm) || n_avg <= 0 || n_fft < 0)
     return CDD_EINVAL;
+  const int sideband = bandwidth_mhz > 0 ? 1 : -1;
+  bandwidth_mhz = fabs(bandwidth_mhz);
   const int frame = 2 * n_chan;
   if ((frame & (frame - 1)) || (n_avg & (n_avg - 1))) return CDD_EINVAL;
   int logf = 0;
@@ -703,6 +711,7 @@ int cdd_fullband_create(cdd_fullband* out, double f_center_mhz, double bandwidth
   if (!f) return CDD_ENOMEM;
   f->f_center = f_center_mhz;
   f->bandwidth = bandwidth_mhz;
+  f->sideband = sideband;
   f->dm = dm;
   f->n_chan = n_chan;
   f->frame = frame;

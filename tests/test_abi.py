@@ -216,6 +216,7 @@ def test_batch_rejects_bad_requests(cdd):
 
 FULLBAND = [
     (325.0, 32.0, 512, 50.0, 0, 16),        # the 32 MHz GSB mode: N = 2^26
+    (325.0, -32.0, 512, 50.0, 0, 16),       # the same band as a lower sideband
     (610.0, 16.0, 256, 10.0, 0, 16),
     (610.0, 1.0, 32, 20.0, 0, 4),
     (325.0, 2.0, 64, 5.0, 1 << 20, 8),
@@ -241,7 +242,7 @@ def test_fullband_geometry_matches_oracle(cdd, geo):
 def test_fullband_rejects_bad_requests(cdd):
     for args in [(325.0, 32.0, 500, 50.0, 0, 16),          # frame not a power of two
                  (325.0, 32.0, 512, 50.0, 1 << 20, 16),    # N below the smear
-                 (325.0, -32.0, 512, 50.0, 0, 16)]:        # lower sideband
+                 (325.0, 0.0, 512, 50.0, 0, 16)]:          # no bandwidth
         with pytest.raises(cdd.CddError):
             cdd.cdd_fullband_create(*args)
     with pytest.raises(cdd.CddError) as ei:                 # N = 2^28: beyond this build

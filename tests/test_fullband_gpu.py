@@ -29,6 +29,8 @@ def run_fullband(vin, args, q, n_blocks):
     (325.0, 2.0, 64, 5.0, 1 << 18, 1),       # N = 2^18: one radix-16 pass, integrated across lanes (n_avg 1)
     (325.0, 4.0, 128, 40.0, 0, 16),          # N = 2^20: radix 16 then 4, lanes sum 16 samples
     (325.0, 8.0, 256, 30.0, 0, 32),          # N = 2^21: n_avg 32 > 16 keeps the integration kernel
+    (610.0, -1.0, 32, 20.0, 0, 4),           # lower sideband, the shared-memory transform only
+    (325.0, -2.0, 64, 5.0, 1 << 18, 1),      # lower sideband through the outer passes
 ])
 def test_fullband_matches_oracle(cuda_device, args):
     g = O.fullband_geometry(*args)
