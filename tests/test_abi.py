@@ -92,6 +92,9 @@ def test_invalid_geometry_is_rejected(cdd):
         (325.0, 32.0, 512, 50.0, 0, 0),        # no integration
         (10.0, 32.0, 512, 50.0, 0, 16),        # band below 0 MHz
         (325.0, 32.0, 512, 50.0, 128, 48),     # hop not a multiple of n_avg
+        (float("nan"), 32.0, 512, 50.0, 0, 16),  # not a frequency
+        (325.0, 32.0, 512, float("inf"), 0, 16),  # not a DM
+        (325.0, 32.0, 512, 50.0, -8192, 16),   # negative N
     ]
     for args in bad:
         with pytest.raises(cdd.CddError) as ei:
@@ -109,7 +112,10 @@ def test_setters(cdd):
     p = cdd.cdd_plan_create(325.0, 32.0, 512, 50.0, 8192, 16)
     try:
         for attr, val in (("segments_per_block", 0), ("taper", 7), ("pipeline_chunks", 3),
-                          ("n_fft", 1024)):
+                          ("n_fft", 1024),
+                          ("segments_per_block", (1 << 24) + 1),     # beyond the per-call limit
+                          ("segments_per_block", 1 << 20),           # q*h*C above 2^40 samples
+                          ("polarisations", 3), ("stage_timing", 2), ("r_max", 5)):
             with pytest.raises(cdd.CddError):
                 cdd.cdd_plan_set(p, attr, val)
         cdd.cdd_plan_set(p, "segments_per_block", 76)
