@@ -120,7 +120,7 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
   const int kt = active ? w % a.n_tchan : 0;     // channel within the tier, fastest
   const int s = active ? w / a.n_tchan : 0;
   const int k = a.chan0 + kt;
-  float2* pb0 = buf + pad(lt);
+  float2* pb0 = buf + pad<LOGN>(lt);
   float2 v[R0];
 
   // ---- pass 0, forward, straight from the channel-major block
@@ -148,7 +148,7 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
 #pragma unroll
     for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
 #pragma unroll
-    for (int kk = 0; kk < R0; ++kk) pb0[poff<T>(kk)] = v[kk];
+    for (int kk = 0; kk < R0; ++kk) pb0[poff<LOGN, T>(kk)] = v[kk];
   }
   sync();
   static_for<1, PL::P - 1>([&](auto P_) {
@@ -167,10 +167,9 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
 #pragma unroll 1
     for (int i = 0; i < PERC; ++i) {
       const int q = lt + i * T;
-      const float2* pb = buf + pad(q * RL);
+      const float2* pb = buf + pad<LOGN>(q * RL);
       float2 x[RL];
-#pragma unroll
-      for (int j = 0; j < RL; ++j) x[j] = pb[j];
+      load_group<LOGN, RL>(pb, x);
       dft<RL, -1>(x);
       // the taper (Sec. 2.2) depends on the bin only, so it is applied here
       // once for every DM trial, with the 1/N of the inverse transform (a
@@ -226,9 +225,7 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
                                               : dm_chirp(__ldg(&t1k[kk * NG + q]), dm));
         }
         dft<RL, 1>(x);
-        float2* pb = buf + pad(q * RL);
-#pragma unroll
-        for (int j = 0; j < RL; ++j) pb[j] = x[j];
+        store_group<LOGN, RL>(buf + pad<LOGN>(q * RL), x);
       }
     }
     if constexpr (PL::P >= 3) mid_sync();
@@ -240,7 +237,7 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
     // ---- pass 0, inverse, detection
     if (active) {
 #pragma unroll
-      for (int kk = 0; kk < R0; ++kk) v[kk] = pb0[poff<T>(kk)];
+      for (int kk = 0; kk < R0; ++kk) v[kk] = pb0[poff<LOGN, T>(kk)];
 #pragma unroll
       for (int kk = 1; kk < R0; ++kk) v[kk] = cmulc(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
       dft<R0, 1>(v);
@@ -291,7 +288,7 @@ __global__ void __launch_bounds__(Cfg<LOGN>::THREADS, Cfg<LOGN>::MINB)
 batch_kernel(const BatchArgs a) {
   using PL = PassPlan<LOGN>;
   using CF = Cfg<LOGN>;
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
   const int g = threadIdx.x / PL::T;
   const int lt = threadIdx.x % PL::T;
   float2* buf = smem + g * CF::SEG_F2;
@@ -309,7 +306,7 @@ struct BatchPersist {
   using PL = PassPlan<LOGN>;
   static constexpr int GROUPS = 2;
   static constexpr int THREADS = GROUPS * PL::T;
-  static constexpr size_t SMEM = (size_t(PL::TW_LEN) + size_t(GROUPS) * padded_len(PL::N)) * sizeof(float2);
+  static constexpr size_t SMEM = (size_t(PL::TW_LEN) + size_t(GROUPS) * padded_len<LOGN>()) * sizeof(float2);
 };
 
 template <int LOGN, bool T1F, bool TAP>
@@ -318,13 +315,13 @@ batch_persistent_kernel(const BatchArgs a) {
   using PL = PassPlan<LOGN>;
   using BP = BatchPersist<LOGN>;
   constexpr int T = PL::T;
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
   float2* tws = smem;
   for (int i = threadIdx.x; i < PL::TW_LEN; i += blockDim.x) tws[i] = __ldg(&a.tw[i]);
   __syncthreads();
   const int g = threadIdx.x / T;
   const int lt = threadIdx.x % T;
-  float2* buf = smem + PL::TW_LEN + g * padded_len(PL::N);
+  float2* buf = smem + PL::TW_LEN + g * padded_len<LOGN>();
   const int bar = g + 1;                       // named barriers 1, 2 (0 is __syncthreads)
   auto sync = [bar] { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(T) : "memory"); };
   const int work = a.n_tchan * a.q;

@@ -282,9 +282,24 @@ __host__ __device__ inline int bin_to_position(int bin) {
   return pos;
 }
 
-// Padded shared-memory index: one spare float2 after every 16, so that the
-// stride-1 groups of the middle pass hit distinct banks.
-__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
-__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4); }
+// Padded shared-memory index: spare float2 words after every 16 points, so
+// that the strided gathers and the stride-1 groups hit distinct banks.  Pad
+// words after every 16 points of a transform's buffer.  Two where every
+// radix pass but the last gathers at a stride of 16 or more: each stride-1
+// group of the last pass then starts on a 16-byte boundary and moves as
+// 128-bit accesses, and every gather stays free of bank conflicts.  One where
+// a pass gathers at a smaller stride (N = 64, 128, 1024, 2048): two words
+// would put both halves of a warp on the same banks there.
+template <int LOGN>
+__host__ __device__ constexpr int pad_words() {
+  using PL = PassPlan<LOGN>;
+  for (int p = 0; p + 1 < PL::P; ++p)
+    if (PL::S(p) < 16) return 1;
+  return 2;
+}
+template <int LOGN>
+__device__ __forceinline__ int pad(int i) { return i + pad_words<LOGN>() * (i >> 4); }
+template <int LOGN>
+__host__ __device__ constexpr int padded_len() { return (1 << LOGN) + pad_words<LOGN>() * ((1 << LOGN) >> 4); }
 
 }  // namespace cdd

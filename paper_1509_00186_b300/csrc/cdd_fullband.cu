@@ -72,7 +72,7 @@ icf_kernel(const char2* __restrict__ in, float* __restrict__ ts, const float2* _
   constexpr int R0 = PL::R(0);
   constexpr int RL = PL::RL;
   static_assert(RL <= 16, "stride-1 groups must not cross a padding word");
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
   const int g = threadIdx.x / T;
   const int lt = threadIdx.x % T;
   float2* buf = smem + g * CF::SEG_F2;
@@ -96,9 +96,9 @@ icf_kernel(const char2* __restrict__ in, float* __restrict__ ts, const float2* _
     dft<R0, -1>(v);
 #pragma unroll
     for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], __ldg(&twf[kk * T + lt]));
-    float2* pb0 = buf + pad(lt);
+    float2* pb0 = buf + pad<LOGF>(lt);
 #pragma unroll
-    for (int kk = 0; kk < R0; ++kk) pb0[poff<T>(kk)] = v[kk];
+    for (int kk = 0; kk < R0; ++kk) pb0[poff<LOGF, T>(kk)] = v[kk];
   }
   __syncthreads();
   static_for<1, PL::P - 1>([&](auto P_) {
@@ -108,20 +108,18 @@ icf_kernel(const char2* __restrict__ in, float* __restrict__ ts, const float2* _
   if constexpr (PL::P >= 2) {                 // the last radix on stride-1 groups
     if (active) {
       for (int q = lt; q < F / RL; q += T) {
-        float2* pb = buf + pad(q * RL);
+        float2* pb = buf + pad<LOGF>(q * RL);
         float2 x[RL];
-#pragma unroll
-        for (int j = 0; j < RL; ++j) x[j] = pb[j];
+        load_group<LOGF, RL>(pb, x);
         dft<RL, -1>(x);
-#pragma unroll
-        for (int j = 0; j < RL; ++j) pb[j] = x[j];
+        store_group<LOGF, RL>(pb, x);
       }
     }
     __syncthreads();
   }
   if (active) {
     float* out = ts + t * F;
-    for (int n = lt; n < F; n += T) out[n] = buf[pad(bin_to_position<LOGF>(n))].x * (1.0f / F);
+    for (int n = lt; n < F; n += T) out[n] = buf[pad<LOGF>(bin_to_position<LOGF>(n))].x * (1.0f / F);
   }
 }
 
@@ -145,7 +143,7 @@ icf_half_kernel(const char2* __restrict__ in, float* __restrict__ ts, const floa
   constexpr int R0 = PL::R(0);
   constexpr int RL = PL::RL;
   static_assert(RL <= 16, "stride-1 groups must not cross a padding word");
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
   const int g = threadIdx.x / T;
   const int lt = threadIdx.x % T;
   float2* buf = smem + g * CF::SEG_F2;
@@ -170,9 +168,9 @@ icf_half_kernel(const char2* __restrict__ in, float* __restrict__ ts, const floa
     dft<R0, -1>(v);
 #pragma unroll
     for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], __ldg(&twc[kk * T + lt]));
-    float2* pb0 = buf + pad(lt);
+    float2* pb0 = buf + pad<LOGC>(lt);
 #pragma unroll
-    for (int kk = 0; kk < R0; ++kk) pb0[poff<T>(kk)] = v[kk];
+    for (int kk = 0; kk < R0; ++kk) pb0[poff<LOGC, T>(kk)] = v[kk];
   }
   __syncthreads();
   static_for<1, PL::P - 1>([&](auto P_) {
@@ -181,13 +179,11 @@ icf_half_kernel(const char2* __restrict__ in, float* __restrict__ ts, const floa
   });
   if (active) {                              // the last radix on stride-1 groups
     for (int q = lt; q < C / RL; q += T) {
-      float2* pb = buf + pad(q * RL);
+      float2* pb = buf + pad<LOGC>(q * RL);
       float2 x[RL];
-#pragma unroll
-      for (int j = 0; j < RL; ++j) x[j] = pb[j];
+      load_group<LOGC, RL>(pb, x);
       dft<RL, -1>(x);
-#pragma unroll
-      for (int j = 0; j < RL; ++j) pb[j] = x[j];
+      store_group<LOGC, RL>(pb, x);
     }
   }
   __syncthreads();
@@ -195,7 +191,7 @@ icf_half_kernel(const char2* __restrict__ in, float* __restrict__ ts, const floa
     float2* out2 = reinterpret_cast<float2*>(ts + t * F);
 #pragma unroll 4
     for (int n = lt; n < C; n += T) {
-      const float2 y = buf[pad(bin_to_position<LOGC>(n))];
+      const float2 y = buf[pad<LOGC>(bin_to_position<LOGC>(n))];
       out2[n] = make_float2(y.x * (1.0f / F), -y.y * (1.0f / F));
     }
   }
@@ -304,7 +300,7 @@ middle_kernel(float2* __restrict__ w, const float* __restrict__ ts, float* __res
   using PL = PassPlan<LOGS>;
   using CF = Cfg<LOGS>;
   constexpr int NS = PL::N;
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
   const int g = threadIdx.x / PL::T;
   const int lt = threadIdx.x % PL::T;
   float2* buf = smem + g * CF::SEG_F2;
@@ -318,7 +314,7 @@ middle_kernel(float2* __restrict__ w, const float* __restrict__ ts, float* __res
     for (int i = 0; i < PER; ++i)
       r[i] = ts ? make_float2(__ldg(&ts[qq * NS + lt + i * PL::T]), 0.f) : wq[lt + i * PL::T];
 #pragma unroll
-    for (int i = 0; i < PER; ++i) buf[pad(lt + i * PL::T)] = r[i];
+    for (int i = 0; i < PER; ++i) buf[pad<LOGS>(lt + i * PL::T)] = r[i];
   }
   __syncthreads();
   static_for<0, PL::P - 1>([&](auto P_) {
@@ -335,7 +331,7 @@ middle_kernel(float2* __restrict__ w, const float* __restrict__ ts, float* __res
   });
   if (active) {
     for (int i = lt; i < NS; i += PL::T) {
-      const float2 v = buf[pad(i)];
+      const float2 v = buf[pad<LOGS>(i)];
       if (pw) pw[qq * NS + i] = v.x * v.x;
       else wq[i] = v;
     }

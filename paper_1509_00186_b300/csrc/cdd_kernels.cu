@@ -51,7 +51,7 @@ __device__ __forceinline__ bool ols_segment(const OlsArgs& a, float2* buf, const
   constexpr int T = PL::T;
   constexpr int R0 = PL::R(0);
   // ---- pass 0, forward: unpack and gather x[lt + T*j] of this segment
-  float2* pb0 = buf + pad(lt);
+  float2* pb0 = buf + pad<LOGN>(lt);
   float2 v[R0];
   if (active) {
     const long long row0 = (long long)s * a.hop - a.n_ov;
@@ -86,7 +86,7 @@ __device__ __forceinline__ bool ols_segment(const OlsArgs& a, float2* buf, const
 #pragma unroll
     for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
 #pragma unroll
-    for (int kk = 0; kk < R0; ++kk) pb0[poff<T>(kk)] = v[kk];
+    for (int kk = 0; kk < R0; ++kk) pb0[poff<LOGN, T>(kk)] = v[kk];
   }
   sync();
 
@@ -118,7 +118,7 @@ __device__ __forceinline__ bool ols_segment(const OlsArgs& a, float2* buf, const
   // ---- pass 0, inverse: natural-order voltages v[j] = z[lt + T*j]
   if (active) {
 #pragma unroll
-    for (int kk = 0; kk < R0; ++kk) v[kk] = pb0[poff<T>(kk)];
+    for (int kk = 0; kk < R0; ++kk) v[kk] = pb0[poff<LOGN, T>(kk)];
 #pragma unroll
     for (int kk = 1; kk < R0; ++kk) v[kk] = cmulc(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
     dft<R0, 1>(v);
@@ -192,7 +192,7 @@ ols_kernel(const OlsArgs a) {
   using CF = Cfg<LOGN>;
   constexpr int T = PL::T;
   static_assert(PL::S(0) == T, "pass 0 stride must equal the threads per transform");
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
   const int g = threadIdx.x / T;
   const int lt = threadIdx.x % T;
   float2* buf = smem + g * CF::SEG_F2;
@@ -212,7 +212,7 @@ struct Persist {
   using PL = PassPlan<LOGN>;
   static constexpr int GROUPS = 2;
   static constexpr int THREADS = GROUPS * PL::T;
-  static constexpr size_t SMEM = (size_t(PL::TW_LEN) + size_t(GROUPS) * padded_len(PL::N)) * sizeof(float2);
+  static constexpr size_t SMEM = (size_t(PL::TW_LEN) + size_t(GROUPS) * padded_len<LOGN>()) * sizeof(float2);
 };
 
 #ifndef CDD_PREFETCH
@@ -255,13 +255,13 @@ ols_persistent_kernel(const OlsArgs a) {
   using PL = PassPlan<LOGN>;
   using PS = Persist<LOGN>;
   constexpr int T = PL::T;
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
   float2* tws = smem;
   for (int i = threadIdx.x; i < PL::TW_LEN; i += blockDim.x) tws[i] = __ldg(&a.tw[i]);
   __syncthreads();
   const int g = threadIdx.x / T;
   const int lt = threadIdx.x % T;
-  float2* buf = smem + PL::TW_LEN + g * padded_len(PL::N);
+  float2* buf = smem + PL::TW_LEN + g * padded_len<LOGN>();
   const int bar = g + 1;                       // named barriers 1, 2 (0 is __syncthreads)
   auto sync = [bar] { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(T) : "memory"); };
   const int work = a.n_chan * a.s_count;
@@ -310,7 +310,7 @@ ols_cluster_kernel(const OlsArgs a) {
   static_assert(PERX * T == NB, "cross pass must split evenly over the threads");
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
-  extern __shared__ float2 smem[];
+  extern __shared__ __align__(16) float2 smem[];
   float2* buf = smem;
   const int lt = threadIdx.x;
   // the cluster's buffers as 32-bit shared::cluster addresses (one register each)
@@ -393,7 +393,7 @@ ols_cluster_kernel(const OlsArgs a) {
 #pragma unroll
         for (int kk = 1; kk < CL; ++kk) v[kk] = cmul(v[kk], __ldg(&twx[(kk - 1) * NS + t]));
 #pragma unroll
-        for (int kk = 0; kk < CL; ++kk) dsm_st(rbuf[kk] + 8u * (uint32_t)pad(t), v[kk]);
+        for (int kk = 0; kk < CL; ++kk) dsm_st(rbuf[kk] + 8u * (uint32_t)pad<LOGS>(t), v[kk]);
       }
     }
     cluster.sync();
@@ -422,7 +422,7 @@ ols_cluster_kernel(const OlsArgs a) {
     for (int i = 0; i < PERX; ++i) {
       const int t = rank * NB + lt + i * T;
 #pragma unroll
-      for (int kk = 0; kk < CL; ++kk) z[i][kk] = dsm_ld(rbuf[kk] + 8u * (uint32_t)pad(t));
+      for (int kk = 0; kk < CL; ++kk) z[i][kk] = dsm_ld(rbuf[kk] + 8u * (uint32_t)pad<LOGS>(t));
 #pragma unroll
       for (int kk = 1; kk < CL; ++kk) z[i][kk] = cmulc(z[i][kk], __ldg(&twx[(kk - 1) * NS + t]));
       dft<CL, 1>(z[i]);
@@ -715,7 +715,7 @@ cudaError_t launch_ols_t(const OlsArgs& a, cudaStream_t s) {
 
 template <int LOGS, int CL>
 cudaError_t launch_cluster_t(const OlsArgs& a, cudaStream_t s) {
-  constexpr size_t SMEM = size_t(padded_len(PassPlan<LOGS>::N)) * sizeof(float2);
+  constexpr size_t SMEM = size_t(padded_len<LOGS>()) * sizeof(float2);
   static bool attr_set[128] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

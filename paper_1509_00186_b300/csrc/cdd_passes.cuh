@@ -33,14 +33,43 @@ struct Cfg {
 #else
   static constexpr int MINB = THREADS <= 256 ? (PL::R(0) <= 16 ? 3 : 2) : 1;
 #endif
-  static constexpr int SEG_F2 = padded_len(PL::N);                       // float2 per transform
+  static constexpr int SEG_F2 = padded_len<LOGN>();                       // float2 per transform
   static constexpr size_t SMEM = size_t(G) * SEG_F2 * sizeof(float2);
 };
 
-// pad(base + S*j) - pad(base) for the index sets the passes touch (S >= 16, or
-// base mod 16 < S with S dividing 16): a compile-time constant.
-template <int S>
-__device__ __forceinline__ constexpr int poff(int j) { return S * j + ((S * j) >> 4); }
+// pad<LOGN>(base + S*j) - pad<LOGN>(base) for the index sets the passes touch
+// (S >= 16, or base mod 16 < S with S dividing 16): a compile-time constant.
+template <int LOGN, int S>
+__device__ __forceinline__ constexpr int poff(int j) { return S * j + pad_words<LOGN>() * ((S * j) >> 4); }
+
+// A stride-1 group of R points at buf + pad<LOGN>(q * R) to and from
+// registers.  With two pad words per 16 points every group starts on a
+// 16-byte boundary (buffers start on one), so it moves as R/2 128-bit accesses.
+template <int LOGN, int R>
+__device__ __forceinline__ void load_group(const float2* pb, float2 (&v)[R]) {
+  if constexpr (pad_words<LOGN>() == 2 && R % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < R; j += 2) {
+      const float4 t = reinterpret_cast<const float4*>(pb)[j / 2];
+      v[j] = make_float2(t.x, t.y);
+      v[j + 1] = make_float2(t.z, t.w);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[j] = pb[j];
+  }
+}
+template <int LOGN, int R>
+__device__ __forceinline__ void store_group(float2* pb, const float2 (&v)[R]) {
+  if constexpr (pad_words<LOGN>() == 2 && R % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < R; j += 2)
+      reinterpret_cast<float4*>(pb)[j / 2] = make_float4(v[j].x, v[j].y, v[j + 1].x, v[j + 1].y);
+  } else {
+#pragma unroll
+    for (int j = 0; j < R; ++j) pb[j] = v[j];
+  }
+}
 
 // int8 pair (re, im) held in the low 16 bits -> float2 without I2F: bias each
 // byte to unsigned, drop it into the mantissa of 2^23 and subtract 2^23 + 128
@@ -77,10 +106,10 @@ __device__ __forceinline__ void fwd_pass(float2* buf, const float2* __restrict__
     const int b = lt + i * PL::T;
     const int t = b % S;
     const int base = (b / S) * M + t;
-    float2* pb = buf + pad(base);
+    float2* pb = buf + pad<LOGN>(base);
     float2 v[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) v[j] = pb[poff<S>(j)];
+    for (int j = 0; j < R; ++j) v[j] = pb[poff<LOGN, S>(j)];
     dft<R, -1>(v);
     if constexpr (S > 1) {
       const float2* twp = tw + PL::TwOff(p) + t;
@@ -88,7 +117,7 @@ __device__ __forceinline__ void fwd_pass(float2* buf, const float2* __restrict__
       for (int k = 1; k < R; ++k) v[k] = cmul(v[k], ld_tw<SH>(twp + k * S));
     }
 #pragma unroll
-    for (int k = 0; k < R; ++k) pb[poff<S>(k)] = v[k];
+    for (int k = 0; k < R; ++k) pb[poff<LOGN, S>(k)] = v[k];
   }
 }
 
@@ -103,10 +132,10 @@ __device__ __forceinline__ void inv_pass(float2* buf, const float2* __restrict__
     const int b = lt + i * PL::T;
     const int t = b % S;
     const int base = (b / S) * M + t;
-    float2* pb = buf + pad(base);
+    float2* pb = buf + pad<LOGN>(base);
     float2 v[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) v[k] = pb[poff<S>(k)];
+    for (int k = 0; k < R; ++k) v[k] = pb[poff<LOGN, S>(k)];
     if constexpr (S > 1) {
       const float2* twp = tw + PL::TwOff(p) + t;
 #pragma unroll
@@ -114,7 +143,7 @@ __device__ __forceinline__ void inv_pass(float2* buf, const float2* __restrict__
     }
     dft<R, 1>(v);
 #pragma unroll
-    for (int j = 0; j < R; ++j) pb[poff<S>(j)] = v[j];
+    for (int j = 0; j < R; ++j) pb[poff<LOGN, S>(j)] = v[j];
   }
 }
 
@@ -129,16 +158,14 @@ __device__ __forceinline__ void chirp_pass(float2* buf, const float2* __restrict
   for (int i = 0; i < PER; ++i) {
     const int q = lt + i * PL::T;
     static_assert(R <= 16, "stride-1 groups must not cross a padding word");
-    float2* pb = buf + pad(q * R);
+    float2* pb = buf + pad<LOGN>(q * R);
     float2 v[R];
-#pragma unroll
-    for (int j = 0; j < R; ++j) v[j] = pb[j];
+    load_group<LOGN, R>(pb, v);
     dft<R, -1>(v);
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = cmul(v[k], __ldg(&chirp_k[k * NG + q]));
     dft<R, 1>(v);
-#pragma unroll
-    for (int j = 0; j < R; ++j) pb[j] = v[j];
+    store_group<LOGN, R>(pb, v);
   }
 }
 
