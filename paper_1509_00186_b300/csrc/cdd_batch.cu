@@ -145,8 +145,12 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
 #pragma unroll
     for (int j = 0; j < R0; ++j) v[j] = unpack_i8x2(c[j]);
     dft<R0, -1>(v);
+    if constexpr (kRecPass0<LOGN, SH>) {
+      apply_twiddles_rec<R0, T, SH, false>(v, tw + lt);
+    } else {
 #pragma unroll
-    for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
+      for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
+    }
 #pragma unroll
     for (int kk = 0; kk < R0; ++kk) pb0[poff<LOGN, T>(kk)] = v[kk];
   }
@@ -238,8 +242,12 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
     if (active) {
 #pragma unroll
       for (int kk = 0; kk < R0; ++kk) v[kk] = pb0[poff<LOGN, T>(kk)];
+      if constexpr (kRecPass0<LOGN, SH>) {
+        apply_twiddles_rec<R0, T, SH, true>(v, tw + lt);
+      } else {
 #pragma unroll
-      for (int kk = 1; kk < R0; ++kk) v[kk] = cmulc(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
+        for (int kk = 1; kk < R0; ++kk) v[kk] = cmulc(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
+      }
       dft<R0, 1>(v);
     }
     sync();                                   // every thread has read buf

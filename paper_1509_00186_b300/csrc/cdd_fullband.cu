@@ -319,14 +319,14 @@ middle_kernel(float2* __restrict__ w, const float* __restrict__ ts, float* __res
   __syncthreads();
   static_for<0, PL::P - 1>([&](auto P_) {
     constexpr int pp = decltype(P_)::value;
-    if (active) fwd_pass<LOGS, pp>(buf, tw, lt);
+    if (active) fwd_pass<LOGS, pp, false, pp == 0 && kRecPass0<LOGS, false>>(buf, tw, lt);
     __syncthreads();
   });
   if (active) chirp_pass<LOGS>(buf, chirp + qq * NS, lt);
   __syncthreads();
   static_for<0, PL::P - 1>([&](auto I_) {
     constexpr int pp = PL::P - 2 - decltype(I_)::value;
-    if (active) inv_pass<LOGS, pp>(buf, tw, lt);
+    if (active) inv_pass<LOGS, pp, false, pp == 0 && kRecPass0<LOGS, false>>(buf, tw, lt);
     __syncthreads();
   });
   if (active) {

@@ -83,8 +83,12 @@ __device__ __forceinline__ bool ols_segment(const OlsArgs& a, float2* buf, const
 #pragma unroll
     for (int j = 0; j < R0; ++j) v[j] = unpack_i8x2(c[j]);
     dft<R0, -1>(v);
+    if constexpr (kRecPass0<LOGN, SH>) {
+      apply_twiddles_rec<R0, T, SH, false>(v, tw + lt);
+    } else {
 #pragma unroll
-    for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
+      for (int kk = 1; kk < R0; ++kk) v[kk] = cmul(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
+    }
 #pragma unroll
     for (int kk = 0; kk < R0; ++kk) pb0[poff<LOGN, T>(kk)] = v[kk];
   }
@@ -119,8 +123,12 @@ __device__ __forceinline__ bool ols_segment(const OlsArgs& a, float2* buf, const
   if (active) {
 #pragma unroll
     for (int kk = 0; kk < R0; ++kk) v[kk] = pb0[poff<LOGN, T>(kk)];
+    if constexpr (kRecPass0<LOGN, SH>) {
+      apply_twiddles_rec<R0, T, SH, true>(v, tw + lt);
+    } else {
 #pragma unroll
-    for (int kk = 1; kk < R0; ++kk) v[kk] = cmulc(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
+      for (int kk = 1; kk < R0; ++kk) v[kk] = cmulc(v[kk], ld_tw<SH>(&tw[kk * T + lt]));
+    }
     dft<R0, 1>(v);
     if (a.volt != nullptr) {
       const long long vbase = ((long long)k * a.q + s) * a.hop - a.n_ov;
@@ -403,7 +411,7 @@ ols_cluster_kernel(const OlsArgs a) {
     constexpr bool kWarpMid = PL::P >= 3 && PL::R(PL::P - 2) == PL::RL && PL::RL <= 32;
     static_for<0, PL::P - 1>([&](auto P_) {
       constexpr int p = decltype(P_)::value;
-      fwd_pass<LOGS, p>(buf, a.tw, lt);
+      fwd_pass<LOGS, p, false, p == 0 && kRecPass0<LOGS, false>>(buf, a.tw, lt);
       if constexpr (kWarpMid && p == PL::P - 2) __syncwarp();
       else __syncthreads();
     });
@@ -411,7 +419,8 @@ ols_cluster_kernel(const OlsArgs a) {
     if constexpr (kWarpMid) __syncwarp();
     else __syncthreads();
     static_for<0, PL::P - 1>([&](auto I_) {
-      inv_pass<LOGS, PL::P - 2 - decltype(I_)::value>(buf, a.tw, lt);
+      constexpr int pi = PL::P - 2 - decltype(I_)::value;
+      inv_pass<LOGS, pi, false, pi == 0 && kRecPass0<LOGS, false>>(buf, a.tw, lt);
       __syncthreads();
     });
     cluster.sync();

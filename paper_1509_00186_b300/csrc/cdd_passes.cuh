@@ -95,8 +95,28 @@ __device__ __forceinline__ float2 ld_tw(const float2* p) {
   else return __ldg(p);
 }
 
+// Twiddles k = 1 .. R-1 of slot t formed from four table loads (k = 1 and the
+// multiples of 8) and products with w^1 in between: at most 7 products deep.
+// Used where the table is too large for L1 and its loads wait on L2.
+template <int R, int S, bool SH, bool CONJ>
+__device__ __forceinline__ void apply_twiddles_rec(float2 (&v)[R], const float2* twp) {
+  const float2 w1 = ld_tw<SH>(twp + S);
+  float2 w = w1;
+#pragma unroll
+  for (int k = 1; k < R; ++k) {
+    if (k > 1) w = (k % 8 == 0) ? ld_tw<SH>(twp + k * S) : cmul(w, w1);
+    v[k] = CONJ ? cmulc(v[k], w) : cmul(v[k], w);
+  }
+}
+
+// Pass 0 of a radix-32 plan of N >= 8192 points read from global memory: its
+// table (31 twiddles per slot, 62 KB and more) does not stay in L1 beside the
+// transform buffers, so its twiddles are formed as products (apply_twiddles_rec).
+template <int LOGN, bool SH>
+constexpr bool kRecPass0 = !SH && LOGN >= 13 && PassPlan<LOGN>::R(0) == 32;
+
 // Forward (DIF) radix pass p, in place in shared memory; SH: tw is in shared memory.
-template <int LOGN, int p, bool SH = false>
+template <int LOGN, int p, bool SH = false, bool REC = false>
 __device__ __forceinline__ void fwd_pass(float2* buf, const float2* __restrict__ tw, int lt) {
   using PL = PassPlan<LOGN>;
   constexpr int R = PL::R(p), S = PL::S(p), M = PL::M(p);
@@ -111,7 +131,9 @@ __device__ __forceinline__ void fwd_pass(float2* buf, const float2* __restrict__
 #pragma unroll
     for (int j = 0; j < R; ++j) v[j] = pb[poff<LOGN, S>(j)];
     dft<R, -1>(v);
-    if constexpr (S > 1) {
+    if constexpr (S > 1 && REC) {
+      apply_twiddles_rec<R, S, SH, false>(v, tw + PL::TwOff(p) + t);
+    } else if constexpr (S > 1) {
       const float2* twp = tw + PL::TwOff(p) + t;
 #pragma unroll
       for (int k = 1; k < R; ++k) v[k] = cmul(v[k], ld_tw<SH>(twp + k * S));
@@ -122,7 +144,7 @@ __device__ __forceinline__ void fwd_pass(float2* buf, const float2* __restrict__
 }
 
 // Inverse (DIT) radix pass p, in place: conjugate twiddle, then butterfly.
-template <int LOGN, int p, bool SH = false>
+template <int LOGN, int p, bool SH = false, bool REC = false>
 __device__ __forceinline__ void inv_pass(float2* buf, const float2* __restrict__ tw, int lt) {
   using PL = PassPlan<LOGN>;
   constexpr int R = PL::R(p), S = PL::S(p), M = PL::M(p);
@@ -136,7 +158,9 @@ __device__ __forceinline__ void inv_pass(float2* buf, const float2* __restrict__
     float2 v[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = pb[poff<LOGN, S>(k)];
-    if constexpr (S > 1) {
+    if constexpr (S > 1 && REC) {
+      apply_twiddles_rec<R, S, SH, true>(v, tw + PL::TwOff(p) + t);
+    } else if constexpr (S > 1) {
       const float2* twp = tw + PL::TwOff(p) + t;
 #pragma unroll
       for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], ld_tw<SH>(twp + k * S));
