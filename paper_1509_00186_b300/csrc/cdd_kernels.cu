@@ -468,9 +468,10 @@ ols_cluster_kernel(const OlsArgs a) {
         }
       }
     }
-    // no CTA reads another's buffer after this; the release arrive also makes
-    // sure this CTA's loads from its neighbours are done before they exit
-    cluster.sync();
+    // the reads of the other CTAs' buffers are done: arrive (release orders
+    // them before it); wait only before this CTA's buffer is rewritten or the
+    // CTA exits, so the epilogue runs while the cluster catches up
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
 
     const int n_int = a.hop / a.n_avg;
     const int r = __ldg(&a.shift[k]);
@@ -514,6 +515,7 @@ ols_cluster_kernel(const OlsArgs a) {
       }
     } else {
       // ---- detect into this CTA's buffer: (j, tt) -> j*NB + tt, one spare word per 32
+      asm volatile("barrier.cluster.wait.aligned;" ::: "memory");   // nobody reads it any more
       float* pw = reinterpret_cast<float*>(buf);
 #pragma unroll
       for (int i = 0; i < PERX; ++i) {
@@ -545,6 +547,7 @@ ols_cluster_kernel(const OlsArgs a) {
     }
   };
   segment((int)(blockIdx.x / CL));
+  if (in_lanes) asm volatile("barrier.cluster.wait.aligned;" ::: "memory");   // then exit
 }
 
 // Chirp table for a transform of CL * 2^LOGS points held as CL sub-transforms
