@@ -307,7 +307,11 @@ middle_kernel(float2* __restrict__ w, const float* __restrict__ ts, float* __res
   const long long qq = (long long)blockIdx.x * CF::G + g;
   const bool active = qq < n_sub;
   float2* wq = w + qq * NS;
-  if (active) {                             // every load in flight before the first store
+  // with two pad words a pair of points (2m, 2m + 1) is 16-byte aligned in
+  // shared memory as in global memory: the working transform then moves as
+  // 128-bit accesses, half as many
+  constexpr bool kPairs = pad_words<LOGS>() == 2;
+  if (active && (!kPairs || ts)) {          // every load in flight before the first store
     constexpr int PER = NS / PL::T;
     float2 r[PER];
 #pragma unroll
@@ -315,6 +319,14 @@ middle_kernel(float2* __restrict__ w, const float* __restrict__ ts, float* __res
       r[i] = ts ? make_float2(__ldg(&ts[qq * NS + lt + i * PL::T]), 0.f) : wq[lt + i * PL::T];
 #pragma unroll
     for (int i = 0; i < PER; ++i) buf[pad<LOGS>(lt + i * PL::T)] = r[i];
+  } else if (active) {
+    constexpr int PER2 = NS / (2 * PL::T);
+    float4 r[PER2];
+#pragma unroll
+    for (int i = 0; i < PER2; ++i) r[i] = reinterpret_cast<const float4*>(wq)[lt + i * PL::T];
+#pragma unroll
+    for (int i = 0; i < PER2; ++i)
+      *reinterpret_cast<float4*>(&buf[pad<LOGS>(2 * (lt + i * PL::T))]) = r[i];
   }
   __syncthreads();
   static_for<0, PL::P - 1>([&](auto P_) {
@@ -329,12 +341,15 @@ middle_kernel(float2* __restrict__ w, const float* __restrict__ ts, float* __res
     if (active) inv_pass<LOGS, pp, false, pp == 0 && kRecPass0<LOGS, false>>(buf, tw, lt);
     __syncthreads();
   });
-  if (active) {
+  if (active && (!kPairs || pw)) {
     for (int i = lt; i < NS; i += PL::T) {
       const float2 v = buf[pad<LOGS>(i)];
       if (pw) pw[qq * NS + i] = v.x * v.x;
       else wq[i] = v;
     }
+  } else if (active) {
+    for (int m = lt; m < NS / 2; m += PL::T)
+      reinterpret_cast<float4*>(wq)[m] = *reinterpret_cast<const float4*>(&buf[pad<LOGS>(2 * m)]);
   }
 }
 
