@@ -15,8 +15,9 @@
  *
  * Conventions
  *   - Channel k (0 = lowest) covers [f_k, f_k + B/C) MHz with
- *     f_k = f_center - B/2 + k*B/C (upper sideband).  Its complex baseband
- *     sample rate is B/C MHz.
+ *     f_k = f_center - B/2 + k*B/C (upper sideband; a negative bandwidth
+ *     gives a lower sideband, channel 0 highest).  Its complex baseband
+ *     sample rate is |B|/C MHz.
  *   - Input layout (device or host, as the call says): int8 [T][C][2], time
  *     major, channel fastest, real then imaginary part (two's complement).
  *   - Output layout: float32 [C][n_out], channel major, intensities summed over
@@ -125,7 +126,11 @@ enum cdd_precision {
 typedef struct cdd_plan_s* cdd_plan;
 
 /* Create a plan for one polarisation of a C-channel band.
- *   f_center_mhz, bandwidth_mhz > 0: observing band (Sec. 2.1 f_o, Delta f).
+ *   f_center_mhz > 0, bandwidth_mhz != 0: observing band (Sec. 2.1 f_o,
+ *     Delta f).  bandwidth_mhz < 0: a lower sideband, channel 0 the highest;
+ *     each channel is the conjugate mirror of the upper-sideband one, so its
+ *     chirp is conjugated on mirrored bins, and shifts are taken against the
+ *     band's lowest channel.
  *   n_chan > 0: channels.  dm >= 0: dispersion measure in pc cm^-3 (Eq. 3).
  *   n_fft: FFT length N (power of two, 64..65536 in this build; above 16384
  *     a segment runs on a cluster of N/8192 CTAs and n_avg must be at most
