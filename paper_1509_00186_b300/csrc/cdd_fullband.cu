@@ -401,7 +401,7 @@ __global__ void fb_chirp_kernel(float2* chirp, long long n, int n_outer, const i
       const long long d = (qq / (stride_out[p] / NS)) % radix_out[p];
       b_out += d * rprod_out[p];
     }
-    const int pos = (idx % NG) * PL::RL + idx / NG;
+    const int pos = passes::chirp_pos<NG>(idx, PL::RL);
     const long long bin = b_out + l_out * position_to_bin<LOGS>(pos);
     const long long mb = bin <= n / 2 ? bin : n - bin;     // mirror for the upper half
     const double f_bb = (double)mb * (fs / (double)n);

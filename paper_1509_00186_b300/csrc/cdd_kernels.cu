@@ -553,7 +553,7 @@ ols_cluster_kernel(const OlsArgs a) {
 // Chirp table for a transform of CL * 2^LOGS points held as CL sub-transforms
 // of 2^LOGS (CL = 1: one CTA).  Entry (k, r, idx) multiplies the bin that
 // sub-transform r holds at table index idx after its forward passes:
-// bin = r + CL * position_to_bin(pos), pos = (idx % NG) * R_last + idx / NG.
+// bin = r + CL * position_to_bin(pos), pos = chirp_pos<NG>(idx, R_last).
 template <int LOGS, int CL>
 __global__ void chirp_table_kernel(float2* chirp, int n_chan, double f_base, double chan_bw,
                                    double dm, int taper, int sideband) {
@@ -567,7 +567,7 @@ __global__ void chirp_table_kernel(float2* chirp, int n_chan, double f_base, dou
     const int k = (int)(e / N);
     const int rem = (int)(e % N);
     const int r = rem / NS, idx = rem % NS;
-    const int pos = (idx % NG) * PL::RL + idx / NG;
+    const int pos = passes::chirp_pos<NG>(idx, PL::RL);
     const int bin = r + CL * position_to_bin<LOGS>(pos);
     // a lower-sideband channel is the conjugate mirror: bin j sits where the
     // upper-sideband bin -j does (the Nyquist bin is its own mirror)

@@ -171,6 +171,21 @@ __device__ __forceinline__ void inv_pass(float2* buf, const float2* __restrict__
   }
 }
 
+#ifndef CDD_CHIRP_PAIRS
+#define CDD_CHIRP_PAIRS 1
+#endif
+// Chirp-table index idx of a row -> (k, q): bin k of stride-1 group q.  With
+// CDD_CHIRP_PAIRS the bins k and k + 1 (k even) of a group are adjacent, so
+// the chirp pass loads them as one 16-byte value.
+template <int NG>
+__host__ __device__ constexpr int chirp_pos(int idx, int rl) {
+#if CDD_CHIRP_PAIRS
+  return ((idx >> 1) % NG) * rl + 2 * ((idx >> 1) / NG) + (idx & 1);
+#else
+  return (idx % NG) * rl + idx / NG;
+#endif
+}
+
 // Last forward radix, chirp multiply, first inverse radix (stride-1 groups).
 template <int LOGN>
 __device__ __forceinline__ void chirp_pass(float2* buf, const float2* __restrict__ chirp_k, int lt) {
@@ -186,8 +201,19 @@ __device__ __forceinline__ void chirp_pass(float2* buf, const float2* __restrict
     float2 v[R];
     load_group<LOGN, R>(pb, v);
     dft<R, -1>(v);
+#if CDD_CHIRP_PAIRS
+    // bins k and k + 1 (k even) of group q share one 16-byte table entry
+    static_assert(R % 2 == 0, "paired chirp entries need an even last radix");
+#pragma unroll
+    for (int k = 0; k < R; k += 2) {
+      const float4 c = __ldg(reinterpret_cast<const float4*>(chirp_k) + (k / 2) * NG + q);
+      v[k] = cmul(v[k], make_float2(c.x, c.y));
+      v[k + 1] = cmul(v[k + 1], make_float2(c.z, c.w));
+    }
+#else
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = cmul(v[k], __ldg(&chirp_k[k * NG + q]));
+#endif
     dft<R, 1>(v);
     store_group<LOGN, R>(pb, v);
   }
