@@ -98,6 +98,25 @@ __device__ __forceinline__ void dm_chirp1x2(float2 t1, float2 dmx, float2 ndm, f
 // spectrum to its scratch row, then every DM trial.  SH: tw is in shared
 // memory.  sync() is the group's barrier.  Returns true when buf (the power
 // samples) was read after the last barrier.
+#ifndef CDD_BATCH_PAIRS
+#define CDD_BATCH_PAIRS 1
+#endif
+// The per-bin rows of the batched form (the T1 and taper tables, a segment's
+// parked spectrum) hold bin kk of stride-1 group q at row index
+// row_index<NG>(kk, q): with CDD_BATCH_PAIRS the bins kk and kk + 1 (kk even)
+// sit side by side and the pairs run group-fastest, so one load brings two
+// bins.  row_position<NG, RL>(idx) is the inverse: the working-buffer position
+// q * RL + kk of the bin at row index idx.
+template <int NG>
+__host__ __device__ constexpr int row_index(int kk, int q) {
+  return CDD_BATCH_PAIRS ? ((kk >> 1) * NG + q) * 2 + (kk & 1) : kk * NG + q;
+}
+template <int NG, int RL>
+__host__ __device__ constexpr int row_position(int idx) {
+  return CDD_BATCH_PAIRS ? ((idx >> 1) % NG) * RL + 2 * ((idx >> 1) / NG) + (idx & 1)
+                         : (idx % NG) * RL + idx / NG;
+}
+
 template <int LOGN, bool SH, bool T1F, bool TAP, class Sync>
 __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, const float2* tw, int lt,
                                               bool active, int w, Sync sync) {
@@ -109,6 +128,7 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
   constexpr int NG = N / RL;
   constexpr int PERC = NG / T;
   static_assert(RL <= 16, "stride-1 groups must not cross a padding word");
+  static_assert(RL % 2 == 0, "bins are handled in pairs");
   // The last forward pass, the spectrum/chirp groups and the first inverse
   // pass stay within a warp when the last two radices are equal.
   constexpr bool kWarpMid = PL::P >= 3 && PL::R(PL::P - 2) == RL && RL <= 32;
@@ -178,6 +198,19 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
       // the taper (Sec. 2.2) depends on the bin only, so it is applied here
       // once for every DM trial, with the 1/N of the inverse transform (a
       // compile-time switch: the untapered kernels keep their own code)
+#if CDD_BATCH_PAIRS
+#pragma unroll
+      for (int kk = 0; kk < RL; kk += 2) {
+        float s0 = 1.0f / N, s1 = 1.0f / N;
+        if constexpr (TAP) {
+          const float2 t = __ldg(reinterpret_cast<const float2*>(a.taper) + (kk / 2) * NG + q);
+          s0 = t.x * (1.0f / N);
+          s1 = t.y * (1.0f / N);
+        }
+        reinterpret_cast<float4*>(xk)[(kk / 2) * NG + q] =
+            make_float4(x[kk].x * s0, x[kk].y * s0, x[kk + 1].x * s1, x[kk + 1].y * s1);
+      }
+#else
       if constexpr (TAP) {
 #pragma unroll
         for (int kk = 0; kk < RL; ++kk) {
@@ -189,6 +222,7 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
         for (int kk = 0; kk < RL; ++kk)
           xk[kk * NG + q] = make_float2(x[kk].x * (1.0f / N), x[kk].y * (1.0f / N));
       }
+#endif
     }
   }
 
@@ -211,6 +245,29 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
       for (int i = 0; i < PERC; ++i) {
         const int q = lt + i * T;
         float2 x[RL];
+#if CDD_BATCH_PAIRS
+        const float4* xk2 = reinterpret_cast<const float4*>(xk) + q;
+        if constexpr (T1F) {
+          const float2 dmx = make_float2(dm.x, dm.x), ndm = make_float2(-dm.x, -dm.x);
+          const float2 dmy = make_float2(dm.y, dm.y);
+#pragma unroll
+          for (int kk = 0; kk < RL; kk += 2) {
+            float2 c0, c1;
+            dm_chirp1x2(__ldg(reinterpret_cast<const float2*>(t1fk) + (kk / 2) * NG + q), dmx, ndm, dmy, c0, c1);
+            const float4 xx = xk2[(kk / 2) * NG];
+            x[kk] = cmul(make_float2(xx.x, xx.y), c0);
+            x[kk + 1] = cmul(make_float2(xx.z, xx.w), c1);
+          }
+        } else {
+#pragma unroll
+          for (int kk = 0; kk < RL; kk += 2) {
+            const float4 t = __ldg(reinterpret_cast<const float4*>(t1k) + (kk / 2) * NG + q);
+            const float4 xx = xk2[(kk / 2) * NG];
+            x[kk] = cmul(make_float2(xx.x, xx.y), dm_chirp(make_float2(t.x, t.y), dm));
+            x[kk + 1] = cmul(make_float2(xx.z, xx.w), dm_chirp(make_float2(t.z, t.w), dm));
+          }
+        }
+#else
         if constexpr (T1F && RL % 2 == 0) {
           const float2 dmx = make_float2(dm.x, dm.x), ndm = make_float2(-dm.x, -dm.x);
           const float2 dmy = make_float2(dm.y, dm.y);
@@ -228,6 +285,7 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
             x[kk] = cmul(xk[kk * NG + q], T1F ? dm_chirp1(__ldg(&t1fk[kk * NG + q]), dm)
                                               : dm_chirp(__ldg(&t1k[kk * NG + q]), dm));
         }
+#endif
         dft<RL, 1>(x);
         store_group<LOGN, RL>(buf + pad<LOGN>(q * RL), x);
       }
@@ -355,7 +413,7 @@ __global__ void t1_table_kernel(float2* t1, float* t1f, int n_tchan, int chan0, 
        e += (long long)gridDim.x * blockDim.x) {
     const int kt = (int)(e / N);
     const int idx = (int)(e % N);
-    const int pos = (idx % NG) * PL::RL + idx / NG;
+    const int pos = row_position<NG, PL::RL>(idx);
     const int bin = position_to_bin<LOGN>(pos);
     const int obin = sideband > 0 ? bin : (N - bin) % N;
     const int sbin = obin < N / 2 ? obin : obin - N;
@@ -440,7 +498,7 @@ __global__ void batch_taper_kernel(float* tap, int taper, int sideband) {
   constexpr int N = PL::N;
   constexpr int NG = N / PL::RL;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += gridDim.x * blockDim.x) {
-    const int pos = (idx % NG) * PL::RL + idx / NG;
+    const int pos = row_position<NG, PL::RL>(idx);
     const int bin = position_to_bin<LOGN>(pos);
     const int obin = sideband > 0 ? bin : (N - bin) % N;
     const int sbin = obin < N / 2 ? obin : obin - N;
