@@ -276,6 +276,23 @@ def test_batch_geometry_of_the_upgraded_gmrt_shape():
     assert abs(g.shift[-1, -1] - top) <= 0.5
 
 
+def test_batch_overlap_is_the_smear_of_each_tier_lowest_channel_at_the_largest_dm():
+    """325 MHz, 32 MHz, 512 channels, DMs 10 / 250 / 600, tiers N = 8192 and
+    4096: here the smear exceeds N/32, so each tier's overlap is the textbook
+    delay across its lowest channel at the largest DM, in that channel's
+    samples, rounded up to n_avg (Sec. 2.2).  Smaller DMs and the tier's
+    higher channels smear less and must not set it."""
+    dms = [10.0, 250.0, 600.0]
+    g = O.batch_geometry(325.0, 32.0, 512, dms, (8192, 4096), 16)
+    bw = 32.0 / 512
+    for t, n in enumerate((8192, 4096)):
+        nu = 309.0 + 256 * bw * t                 # lower edge of the tier's lowest channel
+        smear = (textbook_delay_s(nu, 600.0) - textbook_delay_s(nu + bw, 600.0)) * bw * 1e6
+        assert smear > n // 32
+        assert g.tier_nov[t] == -(-math.ceil(smear) // 16) * 16
+    assert g.tier_nov == (672, 576)
+
+
 def test_batch_with_one_dm_and_one_tier_is_the_single_dm_path():
     rng = np.random.default_rng(21)
     vin = rng.integers(-60, 60, size=(256 * 6, 4, 2)).astype(np.int8)
