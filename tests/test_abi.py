@@ -174,6 +174,10 @@ BATCH_GEOMS = [
     (325.0, 0.25, 4, [20.0], (256,), 4),
     (650.0, -6.25, 64, [5.0, 10.0, 15.0, 20.0], (2048, 1024, 512, 256), 4),   # lower sideband
     (325.0, -0.25, 4, [20.0], (256,), 4),
+    # overlap set by the smear (above N/32) at the largest DM, both sidebands
+    # (one tier: with two, these overlaps give hops that do not nest)
+    (325.0, 32.0, 512, [10.0, 250.0, 600.0], (8192,), 16),
+    (325.0, -32.0, 512, [10.0, 250.0, 600.0], (8192,), 16),
 ]
 
 
