@@ -67,6 +67,23 @@ def test_batch_lower_sideband_and_taper(cuda_device, bandwidth, taper):
         assert O.rel_rms(got[d], want[d]) <= TOL, d
 
 
+@pytest.mark.parametrize("bandwidth", [4.0, -4.0])
+def test_batch_overlap_set_by_the_smear(cuda_device, bandwidth):
+    """DM 300 at 325 MHz smears 288 samples across the lowest 62.5 kHz
+    channel, far above N/32 = 16: the overlap (292) comes from the smear, and
+    each block spans 82 hops to outlast a 4463-sample alignment shift.  Both
+    sidebands, every DM plane against the oracle."""
+    args = (325.0, bandwidth, 64, [10.0, 300.0], (512,), 4)
+    g = O.batch_geometry(*args)
+    assert g.tier_nov == (292,)
+    vin = complex_int8_voltages(29, g.hop(0) * 82 * 2, 64, 20.0)
+    want = O.dedisperse_batch(vin, g)
+    got = run_batch(vin, args, 82, 2)
+    assert got.shape == want.shape
+    for d in range(2):
+        assert O.rel_rms(got[d], want[d]) <= TOL, d
+
+
 def test_batch_checkpoint_resume_is_bit_identical(small):
     """Two blocks in one batch, its state exported; a new batch of the same
     geometry imports it and runs the next two: all four blocks equal the
