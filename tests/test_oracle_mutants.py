@@ -53,6 +53,24 @@ MUTANTS = {
     "batch_lsb_tier_order": ("else (n_chan - 1 - k) // per", "else k // per"),
     "dual_drops_second_pol": ("+ dedisperse(vin_b, geo, taper_kind)", "+ dedisperse(vin_a, geo, taper_kind)"),
     "band_sum_wrong_axis": ("return np.asarray(out).sum(axis=-2)", "return np.asarray(out).sum(axis=-1)"),
+    "welch_as_hann": ("return 1.0 - (2.0 * x - 1.0) ** 2", "return np.sin(np.pi * x) ** 2"),
+    "hann_cosine": ("return np.sin(np.pi * x) ** 2", "return np.cos(np.pi * x) ** 2"),
+    "lsb_edges_off_by_one": ("chan_bw * (k + 1.0)", "chan_bw * k"),
+    "unpack_conjugated": ("+ 1j * vin[:, k, 1]", "- 1j * vin[:, k, 1]"),
+    "unpack_re_im_swapped": ("vin[:, k, 0].astype(np.float64) + 1j * vin[:, k, 1].astype(np.float64)",
+                             "vin[:, k, 1].astype(np.float64) + 1j * vin[:, k, 0].astype(np.float64)"),
+    "align_advances": ("out[shift:] = intensity[: intensity.shape[-1] - shift]",
+                       "out[: intensity.shape[-1] - shift] = intensity[shift:]"),
+    "sec23_rule_not_doubled": ("_next_pow2_above(2.0 * n_d), _next_pow2_above(n_ov), 64)",
+                               "_next_pow2_above(n_d), _next_pow2_above(n_ov), 64)"),
+    "overlap_from_highest_channel": ("dispersion_samples(float(f_lo.min()), chan_bw, dm)",
+                                     "dispersion_samples(float(f_lo.max()), chan_bw, dm)"),
+    "delay_sign": ("(f ** -2 - float(f_ref_mhz) ** -2)", "(float(f_ref_mhz) ** -2 - f ** -2)"),
+    "chirp_pi_for_2pi": ("return 2.0 * np.pi * D_DISP_S_MHZ2", "return np.pi * D_DISP_S_MHZ2"),
+    "bin_offsets_reversed": ("return np.fft.fftfreq(n_fft, d=1.0 / chan_bw_mhz)",
+                             "return -np.fft.fftfreq(n_fft, d=1.0 / chan_bw_mhz)"),
+    "fullband_detect_magnitude": ("integrate(v * v, geo.n_avg)", "integrate(np.abs(v), geo.n_avg)"),
+    "fullband_overlap_not_frames": ("n_ov = -(-int(math.ceil(n_d)) // unit) * unit", "n_ov = int(math.ceil(n_d))"),
 }
 
 

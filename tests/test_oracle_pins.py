@@ -188,6 +188,20 @@ def test_geometry_of_the_named_shapes():
         O.plan_geometry(325.0, 32.0, 512, 50.0, 48, 16)
 
 
+def test_sec23_transform_length_is_the_power_of_two_above_twice_the_smear():
+    """Sec. 2.3 with n_avg = 1, where the rule binds (the overlap alone would
+    allow N = 64): the smear across the lowest channel from the textbook delay
+    law, 54.9 samples at DM 50, gives N = 128."""
+    bw = 32.0 / 512
+    n_d = (textbook_delay_s(309.0, 50.0) - textbook_delay_s(309.0 + bw, 50.0)) * bw * 1e6
+    want = 1
+    while want <= 2.0 * n_d:
+        want *= 2
+    g = O.plan_geometry(325.0, 32.0, 512, 50.0, 0, 1)
+    assert g.n_ov == math.ceil(n_d) == 55 and want == 128
+    assert g.n_fft == want
+
+
 # ---------------------------------------------------------------- physics, end to end
 
 def test_dispersed_impulse_aligns_across_channels():
@@ -409,6 +423,23 @@ def test_inverse_channelisation_round_trip():
     ref = np.fft.irfft(np.concatenate([vin8[..., 0] + 1j * vin8[..., 1], np.zeros((T, 1))], 1),
                        n=2 * C, axis=1).reshape(-1)
     assert np.allclose(got, ref, atol=1e-12)
+
+
+def test_fullband_dm_zero_is_the_integrated_power_of_the_series():
+    """At DM 0 the full-band correction is 1, so overlap-save returns the
+    inverse-channelised series itself; the output is its squares summed over
+    n_avg samples (Sec. 3.1), to rounding."""
+    rng = np.random.default_rng(5)
+    C, T, n_avg = 16, 64, 8
+    vin = rng.integers(-60, 61, size=(T, C, 2)).astype(np.int8)
+    geo = O.fullband_geometry(325.0, 32.0, C, 0.0, 256, n_avg)
+    assert geo.n_ov == 0 and geo.hop == 256
+    x = O.inverse_channelise(vin)
+    want = np.array([sum(float(x[i]) ** 2 for i in range(m * n_avg, (m + 1) * n_avg))
+                     for m in range(x.size // n_avg)])
+    got = O.dedisperse_fullband(vin, geo)
+    assert got.shape == want.shape
+    assert np.allclose(got, want, rtol=1e-9, atol=1e-9 * want.max())
 
 
 def test_fullband_geometry_and_the_paper_max_dm():
