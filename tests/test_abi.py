@@ -57,6 +57,8 @@ GEOMS = [
     (325.0, 0.4375, 7, 3.0, 256, 2),
     (325.0, 16.0, 8, 0.0, 64, 4),
     (1000.0, 1.0, 3, 1000.0, 0, 1),
+    (325.0, 32.0, 512, 50.0, 0, 1),            # Sec. 2.3 rule binds: N = 128, n_ov = 55
+    (325.0, -32.0, 512, 50.0, 0, 1),
     (325.0, -32.0, 512, 50.0, 8192, 16),       # lower sideband
     (610.0, -16.0, 256, 70.0, 0, 8),
     (150.0, -32.0, 512, 100.0, 65536, 16),
@@ -230,6 +232,7 @@ FULLBAND = [
     (610.0, 16.0, 256, 10.0, 0, 16),
     (610.0, 1.0, 32, 20.0, 0, 4),
     (325.0, 2.0, 64, 5.0, 1 << 20, 8),
+    (610.0, 1.0, 32, 0.0, 1 << 14, 4),      # DM 0: no overlap
 ]
 
 

@@ -31,6 +31,8 @@ def run_fullband(vin, args, q, n_blocks):
     (325.0, 8.0, 256, 30.0, 0, 32),          # N = 2^21: n_avg 32 > 16 keeps the integration kernel
     (610.0, -1.0, 32, 20.0, 0, 4),           # lower sideband, the shared-memory transform only
     (325.0, -2.0, 64, 5.0, 1 << 18, 1),      # lower sideband through the outer passes
+    (610.0, 1.0, 32, 0.0, 1 << 14, 4),       # DM 0: no overlap, the correction is 1
+    (325.0, 2.0, 64, 0.0, 1 << 18, 1),       # DM 0 through the outer passes
 ])
 def test_fullband_matches_oracle(cuda_device, args):
     g = O.fullband_geometry(*args)
