@@ -84,6 +84,20 @@ def test_batch_overlap_set_by_the_smear(cuda_device, bandwidth):
         assert O.rel_rms(got[d], want[d]) <= TOL, d
 
 
+def test_batch_with_a_dm_zero_trial(cuda_device):
+    """A DM-0 trial beside a dispersed one: its plane is every channel's
+    integrated power, unshifted; both planes against the oracle."""
+    args = (650.0, 6.25, 64, [0.0, 12.5], (2048, 1024, 512, 256), 4)
+    g = O.batch_geometry(*args)
+    assert np.all(g.shift[0] == 0)
+    vin = complex_int8_voltages(31, 1984 * 4, 64, 20.0)
+    want = O.dedisperse_batch(vin, g)
+    got = run_batch(vin, args, 2, 2)
+    assert got.shape == want.shape
+    for d in range(2):
+        assert O.rel_rms(got[d], want[d]) <= TOL, d
+
+
 def test_batch_checkpoint_resume_is_bit_identical(small):
     """Two blocks in one batch, its state exported; a new batch of the same
     geometry imports it and runs the next two: all four blocks equal the
