@@ -373,6 +373,29 @@ def test_checkpoint_resume_is_bit_identical(cuda_device, case):
         assert np.array_equal(g, w)
 
 
+@pytest.mark.parametrize("logn", [8, 13, 16])
+def test_overlap_longer_than_the_hop(cuda_device, logn):
+    """Overlap 0.7 N: each segment discards more samples than it keeps, and the
+    first segments of a block reach back into the previous block's tail.
+    N = 256 (ols_kernel), 8192 (persistent) and 65536 (clusters); each block
+    spans enough segments to outlast the largest shift."""
+    n = 1 << logn
+    n_chan, n_avg = 3, 4
+    chan_bw = 0.0625
+    dm = (0.7 * n) / O.dispersion_samples(317.0, chan_bw, 1.0)
+    args = (317.0 + n_chan * chan_bw / 2, n_chan * chan_bw, n_chan, dm, n, n_avg)
+    geo = O.plan_geometry(*args)
+    assert geo.n_ov > geo.hop
+    q = max(3, -(-int(geo.shift.max()) * n_avg // geo.hop))
+    rng = np.random.default_rng(100 + logn)
+    T = 2 * q * geo.hop
+    vin = np.clip(np.rint(rng.normal(0, 20, (T, n_chan, 2))), -127, 127).astype(np.int8)
+    out_o, v_o = oracle_run(vin, args, T)
+    out_g, v_g = gpu_run(vin, args, q, 2)
+    assert np.all(rel_rms_rows(v_g, v_o) <= TOL)
+    assert np.all(rel_rms_rows(out_g, out_o) <= TOL)
+
+
 def test_cluster_window_at_the_limit(cuda_device):
     """N = 65536 runs on clusters of eight 8192-point CTAs, each holding
     1024-sample runs of the segment: n_avg = 1024 (integration through shared
