@@ -71,6 +71,13 @@ MUTANTS = {
                              "return -np.fft.fftfreq(n_fft, d=1.0 / chan_bw_mhz)"),
     "fullband_detect_magnitude": ("integrate(v * v, geo.n_avg)", "integrate(np.abs(v), geo.n_avg)"),
     "fullband_overlap_not_frames": ("n_ov = -(-int(math.ceil(n_d)) // unit) * unit", "n_ov = int(math.ceil(n_d))"),
+    "history_ignored": ("xp = np.concatenate([np.asarray(history, dtype=np.complex128),",
+                        "xp = np.concatenate([np.zeros(n_ov, dtype=np.complex128),"),
+    "inverse_and_forward_swapped": ("y = idft(dft(segs) * filt)", "y = dft(idft(segs) * filt)"),
+    "every_channel_gets_channel_0_filter": ("dedispersion_filter(float(geo.f_lo_mhz[k]), geo.chan_bw_mhz, geo.dm,",
+                                            "dedispersion_filter(float(geo.f_lo_mhz[0]), geo.chan_bw_mhz, geo.dm,"),
+    "every_channel_gets_channel_0_shift": ("align(i_k, int(geo.shift[k]))", "align(i_k, int(geo.shift[0]))"),
+    "lsb_mirror_off_by_one": ("f_l = f_l[(-np.arange(n_fft)) % n_fft]", "f_l = f_l[::-1]"),
 }
 
 
