@@ -30,6 +30,28 @@ def test_reference_arm_line():
                         "d2h_bytes_per_step": 0}
 
 
+def test_traffic_capture_key_ignores_comments_only(tmp_path):
+    """The committed DRAM-traffic capture is keyed by a hash of the fused
+    kernel's code: comments and blank lines leave the key alone, a code change
+    moves it (and the bench line's traffic then reads null)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for f in bench.KERNEL_SOURCES:
+        dst = tmp_path / f
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            dst.write_text(fh.read(), encoding="utf-8")
+    key = bench.kernel_source_hash(str(tmp_path))
+    assert key == bench.kernel_source_hash(ROOT)
+    first = tmp_path / bench.KERNEL_SOURCES[0]
+    first.write_text(first.read_text(encoding="utf-8") + "\n// a note\n/* a block\n   note */\n\n",
+                     encoding="utf-8")
+    assert bench.kernel_source_hash(str(tmp_path)) == key
+    first.write_text(first.read_text(encoding="utf-8") + "static int cdd_probe_value = 1;\n",
+                     encoding="utf-8")
+    assert bench.kernel_source_hash(str(tmp_path)) != key
+
+
 @pytest.mark.gpu
 @pytest.mark.slow
 def test_gpu_line(cuda_device):
