@@ -27,5 +27,5 @@ def test_stream_transform_length_is_the_smallest_fit_and_a_valid_plan():
         finally:
             cdd.cdd_destroy(p)
         seen.add(n)
-    assert len(seen) >= 2                 # the mix spans more than one transform length
+    assert len(seen) >= 2                 # the cases span more than one transform length
     assert np.all([sp.dm >= 5.0 and sp.dm <= 150.0 for sp in specs[:40]])
