@@ -255,6 +255,14 @@ def run_reference(args, world, rank):
     return 0
 
 
+# the arithmetic the block computes in, by --precision
+DTYPE_OF = {"fp32": "f32", "fp16x2": "f16x2 (hi+lo f16 tensor-core products, f32 accumulate)",
+            "bf16x2": "bf16x2 (hi+lo bf16 tensor-core products, f32 accumulate)",
+            "fp16": "f16 (tensor-core products, f32 accumulate)",
+            "bf16": "bf16 (tensor-core products, f32 accumulate)"}
+PRECISION_CODE = {"fp32": 0, "fp16": 1, "fp16x2": 2, "bf16x2": 3, "bf16": 4}
+
+
 def config_dict(w, q, hop):
     return {"workload": f"gsb-{w.bandwidth_mhz:g}MHz@{w.f_center_mhz:g}MHz-{w.n_chan}ch-DM{w.dm:g}"
                         f"-N{w.n_fft}-x{w.n_avg}",
@@ -280,7 +288,7 @@ def run_gpu(args, world, rank, local):
 
     w, q = workload_info(args.channels)
     plan = Plan(w.f_center_mhz, w.bandwidth_mhz, w.n_chan, w.dm, w.n_fft, w.n_avg,
-                segments_per_block=q, stage_timing=True)
+                segments_per_block=q, stage_timing=True, precision=args.precision)
     hop = plan.get("hop")
     assert hop * q == plan.block_samples and q == w.n_samp // hop
     rows, n_out, C = plan.block_samples, plan.n_out, w.n_chan
@@ -366,7 +374,8 @@ def run_gpu(args, world, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": "Msamples/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": total_ms_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE_OF[args.precision],
         "data": "synthetic: seeded complex int8 N(0,20) noise plus a pulse train "
                 "(period 33 ms, 3% duty) at each channel's dispersion delay",
         "config": {**config_dict(w, q, hop), "parallelism": f"replicas x{world} (channels independent)"},
@@ -380,7 +389,9 @@ def run_gpu(args, world, rank, local):
                      "traffic": traffic,
                      "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x "
                                     f"{peaks['sm_max_mhz']:.0f} MHz ({peaks['_source']} max clock)",
-                     "kernel": (f"ols_persistent_kernel<{int(math.log2(n_fft))}>"
+                     "kernel": (f"ols_tc_kernel<{PRECISION_CODE[args.precision]}>"
+                                if args.precision != "fp32" else
+                                f"ols_persistent_kernel<{int(math.log2(n_fft))}>"
                                 if n_fft in (4096, 8192) else f"ols_kernel<{int(math.log2(n_fft))}>"),
                      "kernel_ms": kernel_ms,
                      "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
@@ -679,27 +690,41 @@ def row_fullband(args, dev, peaks):
 
 def row_serving(args, dev, peaks):
     """Serving pool: 8 mixed streams (GSB 16/32 MHz at 325/610 MHz, upgraded-GMRT
-    200 MHz / 2048 channels at 650 MHz; DM 5..150), 8 blocks each, submitted as
-    fast as possible; each stream's first block (its plan commit) is served
-    before the timed region; the value is the aggregate rate of the other 7
-    blocks of every stream, latency per block.  Blocks of the small streams
-    take about 40 us on the GPU, as long as a submit call through Python, so
-    the aggregate measures the submit loop more than the GPU."""
-    from paper_1509_00186_b300 import serving
+    200 MHz / 2048 channels at 650 MHz; DM 5..150), 8 blocks of 0.5 s each,
+    ingested from pinned host memory (copy-in, dedispersion, copy-out inside
+    each block's latency).  Two runs: arrivals paced at 20x real time, for the
+    latency of each block from its arrival against its paced deadline (block
+    duration / 20); then every block at once (submitted in batched library
+    calls), for the aggregate rate.  An HBM budget of half the streams' total
+    needs makes the later streams wait in the pool's queue and enter mid-run."""
+    from paper_1509_00186_b300 import cdd, serving
     specs = serving.mixed_scenario(8)
-    summary, _ = serving.run_mix(specs, 8, speedup=1e9)
-    clocks = None
-    cfg = {"workload": "serving:8-mixed-streams-x8-blocks", "timed_blocks_per_stream": 7,
-           "streams": [s.__dict__ for s in specs]}
-    line = {"path": "serving", "metric": "served Msamples/s (8 streams, back to back)",
-            "value": summary["msamples_per_s"], "unit": "Msamples/s", "n_gpus": 1,
-            "steps": summary["blocks"], "warmup": 0, "higher_is_better": True, "scaling": "weak",
+    need = 0
+    for sp in specs:
+        n = sp.n_fft()
+        with cdd.Plan(sp.f_center_mhz, sp.bandwidth_mhz, sp.n_chan, sp.dm, n, sp.n_avg,
+                      segments_per_block=sp.segments_per_block(n)) as p:
+            need += p.get("bytes_needed") + p.get("host_staging_bytes")
+    budget = need // 2
+    clocks = ClockSampler(dev.index or 0)
+    time.sleep(0.3)
+    paced, _ = serving.run_mix(specs, 8, speedup=20.0, budget_bytes=budget)
+    full, _ = serving.run_mix(specs, 8, speedup=1e9, budget_bytes=64 << 30)
+    clock_info = clocks.stop()
+    cfg = {"workload": "serving:8-mixed-streams-x8-blocks-0.5s-host-ingest",
+           "streams": [s.__dict__ for s in specs], "paced_budget_bytes": budget,
+           "streams_total_need_bytes": need}
+    line = {"path": "serving", "metric": "served Msamples/s (8 streams from host buffers)",
+            "value": full["msamples_per_s"], "unit": "Msamples/s", "n_gpus": 1,
+            "steps": full["blocks"], "warmup": 0, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
-            "x_realtime": summary["x_realtime"], "latency_ms": summary["latency_ms"],
-            "deadline_ms": summary["deadline_ms"], "missed_deadlines": summary["missed_deadlines"],
+            "x_realtime": full["x_realtime"],
+            "latency_ms": paced["latency_ms"], "deadline_ms": paced["deadline_ms"],
+            "missed_deadlines": paced["missed_deadlines"],
+            "paced_run": paced, "unpaced_run": full,
             "roofline": None, "roofline_note": "the same per-channel kernels as the block path; "
-                                               "this row measures latency and admission",
-            "clocks": clocks}
+                                               "this row measures ingest, admission and latency",
+            "clocks": clock_info}
     return line
 
 
@@ -730,6 +755,9 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--impl", choices=("cdd", "reference"), default="cdd")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=("fp32", "fp16x2", "bf16x2", "fp16", "bf16"), default="fp32",
+                    help="arithmetic of the block's transforms: fp32 on the CUDA cores, the others as "
+                         "tensor-core (tcgen05) DFT products with FP32 accumulation")
     ap.add_argument("--path", choices=ROWS, default="block",
                     help="block: the headline line; others: one more row of the path (one GPU)")
     ap.add_argument("--dm", type=float, default=None,

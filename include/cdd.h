@@ -104,23 +104,38 @@ enum cdd_attr {
   CDD_ATTR_PHASE_FLOATS = 22,      /* batch only: 1 when the DM = 1 chirp phase
                                       table is single floats (no chirp phase
                                       above 16 turns), else 2 (two floats)     */
-  CDD_ATTR_PRECISION = 23          /* enum cdd_precision, settable: FP32 only;
-                                      the other forms return CDD_EUNSUPPORTED  */
+  CDD_ATTR_PRECISION = 23,         /* enum cdd_precision, settable (see below) */
+  CDD_ATTR_DEVICE_ERRORS = 24,     /* tensor-core forms: nonzero once a kernel
+                                      gave up waiting for its tensor-core
+                                      products (it then stopped early and its
+                                      outputs are invalid); reading waits for
+                                      the device                               */
+  CDD_ATTR_HOST_STAGING_BYTES = 25 /* device bytes the host-buffer path adds
+                                      (two chunks in, two out)                 */
 };
 
 enum cdd_taper { CDD_TAPER_NONE = 0, CDD_TAPER_HANN = 1, CDD_TAPER_WELCH = 2 };
 
-/* Arithmetic of the transforms.  This build computes in FP32, with every chirp
- * phase formed in FP64 and reduced modulo one turn before rounding.  FP16 or
- * BF16 transforms (alone or as hi/lo pairs on the tensor cores) are not built:
- * FP16 and BF16 alone miss the 1e-5 relative RMS bound against the FP64
- * reference, and the split forms are not implemented.  Setting any of them
- * returns CDD_EUNSUPPORTED and leaves the plan at FP32. */
+/* Arithmetic of the transforms (the precision question of Sec. 3 and
+ * Sec. 4.1: single precision versus double over long transforms).  The chirp
+ * phase is always formed in FP64 and reduced modulo one turn before
+ * rounding, and the chirp, twiddle and DFT-matrix tables are built in FP64.
+ *   FP32: every step in FP32 on the CUDA cores (any N).
+ *   FP16, BF16, FP16X2, BF16X2 (N = 8192 only, else CDD_EUNSUPPORTED): the
+ *     radix passes (32, 16, 16) run as matrix products on the tensor cores
+ *     (tcgen05) with FP32 accumulation; the operands are rounded to FP16 or
+ *     BF16 (one product per pass), or split into a rounded value plus its
+ *     rounded residual, for both the data and the DFT matrix (the X2 forms:
+ *     three products, about 22 significant bits for FP16, 16 for BF16).
+ *     Twiddles, the chirp, detection and integration stay in FP32.  Relative
+ *     RMS error against an FP64 evaluation: about 1e-6 (FP16X2), 7e-6
+ *     (BF16X2), 6e-4 (FP16), 5e-3 (BF16). */
 enum cdd_precision {
   CDD_PRECISION_FP32 = 0,
   CDD_PRECISION_FP16 = 1,
   CDD_PRECISION_FP16X2 = 2,
-  CDD_PRECISION_BF16X2 = 3
+  CDD_PRECISION_BF16X2 = 3,
+  CDD_PRECISION_BF16 = 4
 };
 
 typedef struct cdd_plan_s* cdd_plan;
@@ -199,6 +214,18 @@ int cdd_band_sum(const float* d_out, int64_t n_planes, int n_chan, int64_t n_out
  * `stream` orders the call after earlier work on it. */
 int cdd_execute_host(cdd_plan plan, const int8_t* h_in, float* h_out, cudaStream_t stream);
 
+/* cdd_execute_host without the final wait: returns once everything is
+ * queued; `stream` reaches the end of the call's last copy-out (so an event or
+ * host callback enqueued on `stream` afterwards marks the block's result in
+ * h_out).  h_in and h_out must stay valid until then; the next call on the
+ * same plan is ordered after this one. */
+int cdd_execute_host_async(cdd_plan plan, const int8_t* h_in, float* h_out, cudaStream_t stream);
+
+/* Allocate the host-buffer path's staging now (CDD_ATTR_HOST_STAGING_BYTES;
+ * commits the plan if needed), so that later host-buffer calls allocate
+ * nothing.  Synchronous. */
+int cdd_plan_prepare_host(cdd_plan plan);
+
 /* No-allocation form.  The paper has no counterpart: this entry point exists
  * for callers that must not allocate device memory -- code running where
  * cudaMalloc is unavailable or forbidden, such as real-time loops that may only
@@ -216,8 +243,11 @@ int cdd_execute_host(cdd_plan plan, const int8_t* h_in, float* h_out, cudaStream
  *
  * It calls no cudaMalloc, cudaFree or other allocating routine.  Its chirp
  * and twiddle tables, shifts, zero history and alignment spill all live in one
- * file-scope device array of CDD_STATIC_SCRATCH_BYTES (64 MiB) that every GPU
- * which loads the library holds until the process exits.  The tables are
+ * file-scope device array of CDD_STATIC_SCRATCH_BYTES (64 MiB).  A GPU holds
+ * the array from the moment the library's device code is loaded on it until
+ * the process exits; CUDA may load that code lazily, at the first call that
+ * needs it, so the first cdd_execute_static on a device can be the moment the
+ * array is reserved.  Make that first call at start-up.  The tables are
  * rebuilt on every call; the zero history is cleared on every call.  A request
  * whose tables need more than the array returns CDD_ETOOBIG (the 512-channel,
  * N = 8192 shape needs about 36 MB).
@@ -317,28 +347,70 @@ int cdd_fullband_reset(cdd_fullband plan);
 int cdd_fullband_destroy(cdd_fullband plan);
 
 /* ------------------------------------------------------------------------
- * Serving pool: concurrent observation streams on one GPU.  A stream is
- * admitted when its plan's device bytes (CDD_ATTR_BYTES_NEEDED) fit the pool's
- * remaining HBM budget and a slot is free, otherwise CDD_EBUSY; admission
- * allocates at once, so an admitted stream cannot fail later for memory.  Each
- * stream has its own plan (overlap tail, alignment ring and integration state
- * stay on the device between blocks, as in Sec. 4.3) and its own CUDA stream:
- * a block submitted while others are on the GPU is launched at once and
- * overlaps with them.  Submissions carry a sequence number; missing numbers are
- * counted (CDD_ATTR_SEQ_GAPS) and a repeated or older number is refused
- * (CDD_EINVAL).  A block's latency runs from its submit call to the
- * completion of its kernels on the GPU (stamped on the host by a stream
- * callback).  The pool is thread-safe. */
+ * Serving pool: concurrent observation streams on one GPU (the real-time
+ * loop of Sec. 4.2 and 4.3, for many streams at once).  Each stream has its
+ * own plan -- overlap tail, alignment ring and integration state stay on the
+ * device between blocks -- and its own CUDA stream, so a block submitted while
+ * others are on the GPU is launched at once and overlaps with them.
+ *
+ * Admission.  A stream needs its plan's device bytes (CDD_ATTR_BYTES_NEEDED,
+ * plus CDD_ATTR_HOST_STAGING_BYTES when admitted with CDD_POOL_HOST_INGEST)
+ * out of the pool's HBM budget, and a free slot.  cdd_pool_admit[_ex] admits
+ * at once or returns CDD_EBUSY; cdd_pool_request queues the stream instead:
+ * queued requests are admitted first come, first served, whenever memory and
+ * a slot are free (at the request, at every release, and at every status
+ * query), and an immediate admission never overtakes a queued one.  Admission
+ * allocates and builds the stream's tables at once (synchronously), so an
+ * admitted stream cannot fail later for memory.
+ *
+ * Blocks.  Every submission carries the block's sequence number, which must
+ * be the stream's next one: an older or repeated number is refused, and so
+ * is a later one while an earlier block is missing (CDD_EINVAL, nothing
+ * enqueued).  After a loss the caller moves the stream past it with
+ * cdd_pool_stream_resync, which restarts the stream from zero history (as a
+ * fresh stream: Sec. 4.3's overlap carry and the alignment ring need the
+ * missing block) and counts the skipped blocks (CDD_ATTR_SEQ_GAPS).  A block's
+ * latency runs from its arrival time (cdd_pool_clock_ms units; the submit
+ * call's own time for cdd_pool_submit) to the completion of its work on the
+ * GPU, including the copies of a host-buffer block (stamped on the host by a
+ * stream callback).  The pool is thread-safe. */
 typedef struct cdd_pool_s* cdd_pool;
 
-enum cdd_pool_attr { CDD_POOL_BUDGET = 100, CDD_POOL_USED_BYTES = 101, CDD_POOL_STREAMS = 102 };
+enum cdd_pool_attr {
+  CDD_POOL_BUDGET = 100,       /* HBM budget, bytes                             */
+  CDD_POOL_USED_BYTES = 101,   /* bytes held by admitted streams                */
+  CDD_POOL_STREAMS = 102,      /* admitted streams                              */
+  CDD_POOL_QUEUED = 103        /* admission requests still waiting              */
+};
+/* cdd_pool_admit_ex / cdd_pool_request flags */
+#define CDD_POOL_HOST_INGEST 1  /* also reserve host-buffer staging, so the
+                                   stream's cdd_pool_submit_host calls allocate
+                                   nothing */
+
+/* Milliseconds on the steady clock the pool stamps completions with: the
+ * unit of the arrival times passed to the submit calls. */
+double cdd_pool_clock_ms(void);
 
 int cdd_pool_create(cdd_pool* pool, int64_t hbm_budget_bytes, int max_streams);
-/* Admit a stream (arguments as cdd_plan_create plus segments per block and
- * taper); *stream_id receives its slot. */
+/* Admit a stream now (arguments as cdd_plan_create plus segments per block
+ * and taper); *stream_id receives its slot.  CDD_EBUSY if it does not fit now
+ * or a queued request is waiting. */
 int cdd_pool_admit(cdd_pool pool, double f_center_mhz, double bandwidth_mhz, int n_chan,
                    double dm, int n_fft, int n_avg, int segments_per_block, int taper,
                    int* stream_id);
+/* cdd_pool_admit with flags (CDD_POOL_HOST_INGEST). */
+int cdd_pool_admit_ex(cdd_pool pool, double f_center_mhz, double bandwidth_mhz, int n_chan,
+                      double dm, int n_fft, int n_avg, int segments_per_block, int taper, int flags,
+                      int* stream_id);
+/* Queue a stream for admission; *request identifies it.  It may be admitted
+ * before this returns.  CDD_EBUSY if it needs more than the whole budget. */
+int cdd_pool_request(cdd_pool pool, double f_center_mhz, double bandwidth_mhz, int n_chan,
+                     double dm, int n_fft, int n_avg, int segments_per_block, int taper, int flags,
+                     int64_t* request);
+/* CDD_EBUSY while the request waits; CDD_OK with *stream_id once admitted
+ * (reported once; the request is then forgotten); the admission's error if it
+ * failed; CDD_EINVAL for an unknown request. */
+int cdd_pool_request_status(cdd_pool pool, int64_t request, int* stream_id);
 /* Plan attributes of a stream, plus CDD_ATTR_SEQ_GAPS. */
 int cdd_pool_stream_get(cdd_pool pool, int stream_id, int attr, int64_t* value);
 
@@ -349,15 +421,43 @@ int cdd_pool_stream_get(cdd_pool pool, int stream_id, int attr, int64_t* value);
  * continue from; the stream then resumes bit for bit. */
 int cdd_pool_stream_state_bytes(cdd_pool pool, int stream_id, int64_t* bytes);
 int cdd_pool_stream_export(cdd_pool pool, int stream_id, void* state, int64_t bytes, int64_t* next_seq);
-int cdd_pool_stream_import(cdd_pool pool, int stream_id, const void* state, int64_t bytes, int64_t next_seq);/* Enqueue block `seq` of a stream: d_in, d_out as for cdd_execute.  Returns at
- * once with a ticket for cdd_pool_wait. */
+int cdd_pool_stream_import(cdd_pool pool, int stream_id, const void* state, int64_t bytes, int64_t next_seq);
+/* Restart a stream at sequence number seq (>= the next expected one) after
+ * lost blocks: waits for its work, zeroes its history (cdd_reset) and adds
+ * the skipped numbers to CDD_ATTR_SEQ_GAPS. */
+int cdd_pool_stream_resync(cdd_pool pool, int stream_id, int64_t seq);
+
+/* Enqueue block `seq` of a stream from device buffers (d_in, d_out as for
+ * cdd_execute).  Returns at once with a ticket for cdd_pool_wait; latency is
+ * counted from the call. */
 int cdd_pool_submit(cdd_pool pool, int stream_id, int64_t seq, const int8_t* d_in, float* d_out,
                     int64_t* ticket);
-/* Wait for a ticket; *latency_ms (may be NULL) receives submit-to-done time. */
+/* cdd_pool_submit with the block's arrival time (cdd_pool_clock_ms units):
+ * latency is counted from the arrival, so time spent waiting for admission or
+ * in the caller's queue counts. */
+int cdd_pool_submit_at(cdd_pool pool, int stream_id, int64_t seq, const int8_t* d_in, float* d_out,
+                       double t_arrival_ms, int64_t* ticket);
+/* Block from HOST buffers (h_in, h_out as for cdd_execute_host; pinned memory
+ * for asynchronous copies) of a stream admitted with CDD_POOL_HOST_INGEST
+ * (else CDD_ESTATE): copy-in, dedispersion and copy-out are enqueued on the
+ * stream's CUDA stream, overlapping within the block (Sec. 4.2) and with other
+ * streams; the ticket completes when h_out holds the result. */
+int cdd_pool_submit_host(cdd_pool pool, int stream_id, int64_t seq, const int8_t* h_in, float* h_out,
+                         double t_arrival_ms, int64_t* ticket);
+/* n submissions in one call (host != 0: host buffers): blocks i of streams
+ * ids[i] with seqs[i], ins[i], outs[i], arrival times t_arrival_ms[i] (NULL:
+ * now).  Stops at the first refusal and returns its code; *submitted counts
+ * the blocks enqueued, whose tickets are in tickets[0..*submitted). */
+int cdd_pool_submit_many(cdd_pool pool, int n, const int* stream_ids, const int64_t* seqs,
+                         const int8_t* const* ins, float* const* outs, const double* t_arrival_ms,
+                         int host, int64_t* tickets, int* submitted);
+/* Wait for a ticket; *latency_ms (may be NULL) receives arrival-to-done time. */
 int cdd_pool_wait(cdd_pool pool, int64_t ticket, double* latency_ms);
-/* Wait for the stream's blocks, free its plan and return its bytes to the budget. */
+/* Wait for the stream's blocks, free its plan and return its bytes to the
+ * budget; queued requests that now fit are admitted. */
 int cdd_pool_release(cdd_pool pool, int stream_id);
 int cdd_pool_get(cdd_pool pool, int attr, int64_t* value);
+/* Release every stream and drop the queued requests. */
 int cdd_pool_destroy(cdd_pool pool);
 
 /* Restart the stream: zero the overlap tails and the alignment ring and the

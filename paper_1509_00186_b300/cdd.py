@@ -31,10 +31,12 @@ ATTR = {
     "blocks_done": 11, "pipeline_chunks": 12, "kernel_launches": 13, "bytes_needed": 14,
     "seq_gaps": 15, "polarisations": 16, "stage_timing": 17, "timed_blocks": 18,
     "corner_turn_ns": 19, "ols_ns": 20, "phase_floats": 22, "precision": 23,
+    "device_errors": 24, "host_staging_bytes": 25,
 }
-POOL_ATTR = {"budget": 100, "used_bytes": 101, "streams": 102}
+POOL_ATTR = {"budget": 100, "used_bytes": 101, "streams": 102, "queued": 103}
+POOL_HOST_INGEST = 1
 TAPER = {"none": 0, "hann": 1, "welch": 2}
-PRECISION = {"fp32": 0, "fp16": 1, "fp16x2": 2, "bf16x2": 3}
+PRECISION = {"fp32": 0, "fp16": 1, "fp16x2": 2, "bf16x2": 3, "bf16": 4}
 
 # every symbol include/cdd.h declares
 EXPORTS = ("cdd_plan_create", "cdd_plan_set", "cdd_plan_get", "cdd_plan_shifts", "cdd_execute",
@@ -48,7 +50,10 @@ EXPORTS = ("cdd_plan_create", "cdd_plan_set", "cdd_plan_get", "cdd_plan_shifts",
            "cdd_fullband_execute", "cdd_fullband_reset", "cdd_fullband_destroy",
            "cdd_plan_state_bytes", "cdd_plan_export_state", "cdd_plan_import_state",
            "cdd_pool_stream_state_bytes", "cdd_pool_stream_export", "cdd_pool_stream_import",
-           "cdd_batch_state_bytes", "cdd_batch_export_state", "cdd_batch_import_state")
+           "cdd_batch_state_bytes", "cdd_batch_export_state", "cdd_batch_import_state",
+           "cdd_execute_host_async", "cdd_plan_prepare_host", "cdd_pool_clock_ms", "cdd_pool_admit_ex",
+           "cdd_pool_request", "cdd_pool_request_status", "cdd_pool_submit_at", "cdd_pool_submit_host",
+           "cdd_pool_submit_many", "cdd_pool_stream_resync")
 
 
 class CddError(RuntimeError):
@@ -113,14 +118,32 @@ def _load() -> ctypes.CDLL:
     lib.cdd_pool_release.argtypes = [vp, ctypes.c_int]
     lib.cdd_pool_get.argtypes = [vp, ctypes.c_int, i64p]
     lib.cdd_pool_destroy.argtypes = [vp]
+    lib.cdd_execute_host_async.argtypes = [vp, vp, vp, vp]
+    lib.cdd_plan_prepare_host.argtypes = [vp]
+    lib.cdd_pool_clock_ms.argtypes = []
+    lib.cdd_pool_admit_ex.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.cdd_pool_request.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, i64p]
+    lib.cdd_pool_request_status.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]
+    lib.cdd_pool_submit_at.argtypes = [vp, ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_double, i64p]
+    lib.cdd_pool_submit_host.argtypes = [vp, ctypes.c_int, ctypes.c_int64, vp, vp, ctypes.c_double, i64p]
+    lib.cdd_pool_submit_many.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), i64p,
+                                         ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int, i64p,
+                                         ctypes.POINTER(ctypes.c_int)]
+    lib.cdd_pool_stream_resync.argtypes = [vp, ctypes.c_int, ctypes.c_int64]
     lib.cdd_reset.argtypes = [vp]
     lib.cdd_destroy.argtypes = [vp]
     lib.cdd_strerror.argtypes = [ctypes.c_int]
     lib.cdd_strerror.restype = ctypes.c_char_p
     lib.cdd_version.argtypes = []
     for name in EXPORTS:
-        if name not in ("cdd_strerror",):
+        if name not in ("cdd_strerror", "cdd_pool_clock_ms"):
             getattr(lib, name).restype = ctypes.c_int
+    lib.cdd_pool_clock_ms.restype = ctypes.c_double
     return lib
 
 
@@ -428,6 +451,86 @@ def cdd_pool_destroy(pool: int) -> None:
     _check(_lib.cdd_pool_destroy(ctypes.c_void_p(pool)), "cdd_pool_destroy")
 
 
+def cdd_execute_host_async(plan: int, h_in: int, h_out: int, stream: int = 0) -> None:
+    _check(_lib.cdd_execute_host_async(ctypes.c_void_p(plan), ctypes.c_void_p(h_in),
+                                       ctypes.c_void_p(h_out), ctypes.c_void_p(stream)),
+           "cdd_execute_host_async")
+
+
+def cdd_plan_prepare_host(plan: int) -> None:
+    _check(_lib.cdd_plan_prepare_host(ctypes.c_void_p(plan)), "cdd_plan_prepare_host")
+
+
+def cdd_pool_clock_ms() -> float:
+    return float(_lib.cdd_pool_clock_ms())
+
+
+def cdd_pool_admit_ex(pool: int, f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft, n_avg,
+                      segments_per_block, taper, flags) -> int:
+    sid = ctypes.c_int(-1)
+    _check(_lib.cdd_pool_admit_ex(ctypes.c_void_p(pool), f_center_mhz, bandwidth_mhz, n_chan, dm,
+                                  n_fft, n_avg, segments_per_block, taper, flags, ctypes.byref(sid)),
+           "cdd_pool_admit_ex")
+    return sid.value
+
+
+def cdd_pool_request(pool: int, f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft, n_avg,
+                     segments_per_block, taper, flags) -> int:
+    req = ctypes.c_int64(0)
+    _check(_lib.cdd_pool_request(ctypes.c_void_p(pool), f_center_mhz, bandwidth_mhz, n_chan, dm,
+                                 n_fft, n_avg, segments_per_block, taper, flags, ctypes.byref(req)),
+           "cdd_pool_request")
+    return req.value
+
+
+def cdd_pool_request_status(pool: int, request: int):
+    """The admitted stream's id, or None while the request waits."""
+    sid = ctypes.c_int(-1)
+    rc = _lib.cdd_pool_request_status(ctypes.c_void_p(pool), request, ctypes.byref(sid))
+    if rc == CDD_EBUSY:
+        return None
+    _check(rc, "cdd_pool_request_status")
+    return sid.value
+
+
+def cdd_pool_submit_at(pool: int, stream_id: int, seq: int, d_in: int, d_out: int,
+                       t_arrival_ms: float) -> int:
+    t = ctypes.c_int64(0)
+    _check(_lib.cdd_pool_submit_at(ctypes.c_void_p(pool), stream_id, seq, ctypes.c_void_p(d_in),
+                                   ctypes.c_void_p(d_out), t_arrival_ms, ctypes.byref(t)),
+           "cdd_pool_submit_at")
+    return t.value
+
+
+def cdd_pool_submit_host(pool: int, stream_id: int, seq: int, h_in: int, h_out: int,
+                         t_arrival_ms: float) -> int:
+    t = ctypes.c_int64(0)
+    _check(_lib.cdd_pool_submit_host(ctypes.c_void_p(pool), stream_id, seq, ctypes.c_void_p(h_in),
+                                     ctypes.c_void_p(h_out), t_arrival_ms, ctypes.byref(t)),
+           "cdd_pool_submit_host")
+    return t.value
+
+
+def cdd_pool_submit_many(pool: int, ids, seqs, ins, outs, arrivals=None, host=False):
+    """Submit len(ids) blocks in one call; returns their tickets."""
+    n = len(ids)
+    c_ids = (ctypes.c_int * n)(*ids)
+    c_seqs = (ctypes.c_int64 * n)(*seqs)
+    c_ins = (ctypes.c_void_p * n)(*ins)
+    c_outs = (ctypes.c_void_p * n)(*outs)
+    c_arr = (ctypes.c_double * n)(*arrivals) if arrivals is not None else None
+    tickets = (ctypes.c_int64 * n)()
+    done = ctypes.c_int(0)
+    rc = _lib.cdd_pool_submit_many(ctypes.c_void_p(pool), n, c_ids, c_seqs, c_ins, c_outs, c_arr,
+                                   1 if host else 0, tickets, ctypes.byref(done))
+    _check(rc, f"cdd_pool_submit_many (after {done.value} blocks)")
+    return list(tickets)
+
+
+def cdd_pool_stream_resync(pool: int, stream_id: int, seq: int) -> None:
+    _check(_lib.cdd_pool_stream_resync(ctypes.c_void_p(pool), stream_id, seq), "cdd_pool_stream_resync")
+
+
 # ------------------------------------------------------------------ convenience
 
 class Plan:
@@ -435,11 +538,13 @@ class Plan:
 
     def __init__(self, f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft=0, n_avg=1,
                  segments_per_block=1, taper="none", pipeline_chunks=None, polarisations=1,
-                 stage_timing=False):
+                 stage_timing=False, precision="fp32"):
         self.handle = cdd_plan_create(f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft, n_avg)
         try:
             cdd_plan_set(self.handle, "segments_per_block", segments_per_block)
             cdd_plan_set(self.handle, "taper", TAPER[taper])
+            if precision != "fp32":
+                cdd_plan_set(self.handle, "precision", PRECISION[precision])
             if stage_timing:
                 cdd_plan_set(self.handle, "stage_timing", 1)
             if polarisations != 1:

@@ -32,6 +32,7 @@ struct cdd_plan_s {
   // settable before the first execute
   int q = 1;
   int taper = CDD_TAPER_NONE;
+  int precision = CDD_PRECISION_FP32;
   int chunks = 1;
   bool chunks_set = false;
   // device state
@@ -43,6 +44,7 @@ struct cdd_plan_s {
   char2* d_tail[2] = {nullptr, nullptr};
   float* d_ring = nullptr;
   int* d_shift = nullptr;
+  int* d_err = nullptr;      // tensor-core forms: the kernels' wait-timeout flag
   char2* d_in_cm = nullptr;  // channel-major copy of the block (corner-turn path)
   long long ring_len = 0;
   size_t bytes_device = 0;
@@ -180,6 +182,7 @@ int64_t bytes_needed(const cdd_plan p) {
   b += C * (p->r_max + n_out_per_block(p)) * (int64_t)sizeof(float);
   b += C * (int64_t)sizeof(int);
   b += C * p->q * p->hop * (int64_t)sizeof(char2);
+  if (p->precision != CDD_PRECISION_FP32) b += (int64_t)sizeof(int);
   if (p->pols == 2) {
     if (p->n_ov > 0) b += 2 * C * p->n_ov * (int64_t)sizeof(char2);
     b += C * (p->r_max + n_out_per_block(p)) * (int64_t)sizeof(float);
@@ -216,6 +219,7 @@ void free_device(cdd_plan p) {
   cudaFree(p->d_tail[1]);
   cudaFree(p->d_ring);
   cudaFree(p->d_shift);
+  cudaFree(p->d_err);
   cudaFree(p->d_in_cm);
   cudaFree(p->d_tail_b[0]);
   cudaFree(p->d_tail_b[1]);
@@ -287,6 +291,11 @@ int commit_once(cdd_plan p) {
   if ((rc = dalloc(p, &p->d_shift, (size_t)p->n_chan * sizeof(int)))) return rc;
   // channel-major copy of a block: the fused kernel then reads each segment contiguously
   if ((rc = dalloc(p, &p->d_in_cm, (size_t)p->n_chan * p->q * p->hop * sizeof(char2)))) return rc;
+  const bool tc = p->precision != CDD_PRECISION_FP32;
+  if (tc) {
+    if ((rc = dalloc(p, &p->d_err, sizeof(int)))) return rc;
+    CDD_TRY(p, cudaMemset(p->d_err, 0, sizeof(int)));
+  }
   if (p->pols == 2) {
     if (p->n_ov > 0)
       for (int i = 0; i < 2; ++i)
@@ -306,7 +315,7 @@ int commit_once(cdd_plan p) {
   cudaError_t e = cdd::launch_twiddle_table(p->logn, p->d_tw, s);
   if (e == cudaSuccess)
     e = cdd::launch_chirp_table(p->logn, p->d_chirp, p->n_chan, p->f_base, p->chan_bw, p->dm,
-                                p->taper, p->sideband, s);
+                                p->taper, p->sideband, s, tc ? cdd::tc_chirp_scale() : 0.0);
   if (e == cudaSuccess && (rc = zero_state(p, s)) != CDD_OK) {
     cudaStreamDestroy(s);
     return rc;
@@ -396,7 +405,8 @@ int run_block(cdd_plan p, const int8_t* d_in, float* d_out, float* d_volt, int q
   if (te) CDD_TRY(p, cudaEventRecord(te[1], s));
   a.s_begin = 0;
   a.s_count = q;
-  CDD_TRY(p, cdd::launch_ols(p->logn, a, s));
+  if (p->precision == CDD_PRECISION_FP32) CDD_TRY(p, cdd::launch_ols(p->logn, a, s));
+  else CDD_TRY(p, cdd::launch_ols_tc(p->logn, p->precision, a, p->d_err, s));
   if (te) CDD_TRY(p, cudaEventRecord(te[2], s));
   const int launches = 2;
   p->last_launches = launches;
@@ -412,6 +422,13 @@ int prepare(cdd_plan p) {
   int rc = commit(p);
   if (rc) return rc;
   return check_device(p);
+}
+
+// Device bytes of the host-buffer path's staging: two chunks of input and
+// two of output (copy-in, compute and copy-out overlap, Sec. 4.2).
+int64_t host_staging_bytes(const cdd_plan p) {
+  const int64_t q_c = p->q / p->chunks;
+  return 2 * (q_c * p->hop * p->n_chan * 2 + (int64_t)p->n_chan * (q_c * p->hop / p->n_avg) * (int64_t)sizeof(float));
 }
 
 int setup_host_path(cdd_plan p) {
@@ -504,8 +521,10 @@ int cdd_plan_set(cdd_plan p, int attr, int64_t value) {
       p->timing = value == 1;
       return CDD_OK;
     case CDD_ATTR_PRECISION:
-      if (value == CDD_PRECISION_FP32) return CDD_OK;
-      return value >= CDD_PRECISION_FP16 && value <= CDD_PRECISION_BF16X2 ? CDD_EUNSUPPORTED : CDD_EINVAL;
+      if (value < CDD_PRECISION_FP32 || value > CDD_PRECISION_BF16) return CDD_EINVAL;
+      if (value != CDD_PRECISION_FP32 && !cdd::tc_supported(p->logn, (int)value)) return CDD_EUNSUPPORTED;
+      p->precision = (int)value;
+      return CDD_OK;
     default:
       return CDD_EINVAL;
   }
@@ -529,9 +548,19 @@ int cdd_plan_get(cdd_plan p, int attr, int64_t* v) {
     case CDD_ATTR_PIPELINE_CHUNKS: *v = p->chunks; break;
     case CDD_ATTR_KERNEL_LAUNCHES: *v = p->last_launches; break;
     case CDD_ATTR_BYTES_NEEDED: *v = bytes_needed(p); break;
+    case CDD_ATTR_HOST_STAGING_BYTES: *v = host_staging_bytes(p); break;
     case CDD_ATTR_POLARISATIONS: *v = p->pols; break;
     case CDD_ATTR_STAGE_TIMING: *v = p->timing ? 1 : 0; break;
-    case CDD_ATTR_PRECISION: *v = CDD_PRECISION_FP32; break;
+    case CDD_ATTR_PRECISION: *v = p->precision; break;
+    case CDD_ATTR_DEVICE_ERRORS: {
+      int e = 0;
+      if (p->d_err) {
+        if (p->sticky) return p->sticky;
+        CDD_TRY(p, cudaMemcpy(&e, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+      }
+      *v = e;
+      break;
+    }
     case CDD_ATTR_TIMED_BLOCKS:
     case CDD_ATTR_CORNER_TURN_NS:
     case CDD_ATTR_OLS_NS: {
@@ -592,7 +621,7 @@ int cdd_band_sum(const float* d_out, int64_t n_planes, int n_chan, int64_t n_out
              ? CDD_OK : CDD_ECUDA;
 }
 
-int cdd_execute_host(cdd_plan p, const int8_t* h_in, float* h_out, cudaStream_t stream) {
+int cdd_execute_host_async(cdd_plan p, const int8_t* h_in, float* h_out, cudaStream_t stream) {
   if (!p || !h_in || !h_out) return CDD_EINVAL;
   int rc = prepare(p);
   if (rc) return rc;
@@ -626,11 +655,24 @@ int cdd_execute_host(cdd_plan p, const int8_t* h_in, float* h_out, cudaStream_t 
                                  cudaMemcpyDeviceToHost, p->st_d2h));
     CDD_TRY(p, cudaEventRecord(p->ev_out[slot], p->st_d2h));
   }
-  // the caller's stream continues after the last copy-out
+  // the caller's stream continues after the last copy-out, which completes
+  // every earlier copy and kernel of this call
   CDD_TRY(p, cudaStreamWaitEvent(stream, p->ev_out[(nc - 1) & 1], 0));
-  CDD_TRY(p, cudaStreamSynchronize(p->st_d2h));
   p->last_launches *= nc;
   return CDD_OK;
+}
+
+int cdd_execute_host(cdd_plan p, const int8_t* h_in, float* h_out, cudaStream_t stream) {
+  const int rc = cdd_execute_host_async(p, h_in, h_out, stream);
+  if (rc) return rc;
+  CDD_TRY(p, cudaStreamSynchronize(p->st_d2h));
+  return CDD_OK;
+}
+
+int cdd_plan_prepare_host(cdd_plan p) {
+  const int rc = prepare(p);
+  if (rc) return rc;
+  return setup_host_path(p);
 }
 
 }  // extern "C"

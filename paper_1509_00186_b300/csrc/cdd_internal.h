@@ -55,11 +55,19 @@ cudaError_t launch_corner_turn(const char2* in, char2* out, long long r_begin, l
                                long long stride, int n_chan, cudaStream_t s);
 
 // Build the chirp table (FP64 phase, reduced mod 1 turn, then rounded to
-// float): chirp[k][idx] = exp(-i Phi_k(f_l)) * w(f_l) / N in the layout the
-// fused kernel reads.
+// float): chirp[k][idx] = exp(-i Phi_k(f_l)) * w(f_l) * scale in the layout
+// the fused kernel reads; scale 0 means 1/N (the FP32 kernels).
 cudaError_t launch_chirp_table(int logn, float2* chirp, int n_chan, double f_base_mhz,
                                double chan_bw_mhz, double dm, int taper, int sideband,
-                               cudaStream_t s);
+                               cudaStream_t s, double scale = 0.0);
+
+// Tensor-core form of the fused kernel (cdd_tc.cu): the reduced precisions
+// of enum cdd_precision, N = 8192 only.  `err` is a device int that the
+// kernel ORs with 1 if a wait for its tensor-core products gives up.
+bool tc_supported(int logn, int precision);
+cudaError_t launch_ols_tc(int logn, int precision, const OlsArgs& a, int* err, cudaStream_t s);
+// The chirp table's scale for the tensor-core form.
+double tc_chirp_scale();
 
 // Twiddle factors of every radix pass in the kernel's thread-major layout
 // (FP64, then rounded); twiddle_table_len entries.

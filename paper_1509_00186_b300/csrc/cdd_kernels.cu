@@ -556,7 +556,7 @@ ols_cluster_kernel(const OlsArgs a) {
 // bin = r + CL * position_to_bin(pos), pos = chirp_pos<NG>(idx, R_last).
 template <int LOGS, int CL>
 __global__ void chirp_table_kernel(float2* chirp, int n_chan, double f_base, double chan_bw,
-                                   double dm, int taper, int sideband) {
+                                   double dm, int taper, int sideband, double scale) {
   using PL = PassPlan<LOGS>;
   constexpr int NS = PL::N;
   constexpr int N = NS * CL;
@@ -589,8 +589,8 @@ __global__ void chirp_table_kernel(float2* chirp, int n_chan, double f_base, dou
       const double y = 2.0 * x - 1.0;
       wt = 1.0 - y * y;
     }
-    const double sc = wt / N;
-    // exp(-i Phi) w / N; its conjugate for a lower-sideband channel
+    const double sc = wt * (scale > 0 ? scale : 1.0 / N);
+    // exp(-i Phi) w / N (FP32 kernels); its conjugate for a lower-sideband channel
     chirp[e] = make_float2((float)(cs * sc), (float)((sideband > 0 ? -sn : sn) * sc));
   }
 }
@@ -772,11 +772,11 @@ cudaError_t launch_cluster_t(const OlsArgs& a, cudaStream_t s) {
 
 template <int LOGS, int CL>
 cudaError_t launch_chirp_t(float2* chirp, int n_chan, double f_base, double chan_bw, double dm,
-                           int taper, int sideband, cudaStream_t s) {
+                           int taper, int sideband, cudaStream_t s, double scale) {
   const long long total = (long long)n_chan * (CL << LOGS);
   const unsigned grid = (unsigned)((total + 255) / 256 < 65535 ? (total + 255) / 256 : 65535);
   chirp_table_kernel<LOGS, CL><<<grid, 256, 0, s>>>(chirp, n_chan, f_base, chan_bw, dm, taper,
-                                                     sideband);
+                                                     sideband, scale);
   return cudaGetLastError();
 }
 
@@ -797,13 +797,13 @@ cudaError_t launch_ols(int logn, const OlsArgs& a, cudaStream_t s) {
 
 cudaError_t launch_chirp_table(int logn, float2* chirp, int n_chan, double f_base_mhz,
                                double chan_bw_mhz, double dm, int taper, int sideband,
-                               cudaStream_t s) {
+                               cudaStream_t s, double scale) {
   switch (logn) {
-#define X(L) case L: return launch_chirp_t<L, 1>(chirp, n_chan, f_base_mhz, chan_bw_mhz, dm, taper, sideband, s);
+#define X(L) case L: return launch_chirp_t<L, 1>(chirp, n_chan, f_base_mhz, chan_bw_mhz, dm, taper, sideband, s, scale);
     CDD_LOGN_CASES(X)
 #undef X
-    case 15: return launch_chirp_t<kClusterLogS, 4>(chirp, n_chan, f_base_mhz, chan_bw_mhz, dm, taper, sideband, s);
-    case 16: return launch_chirp_t<kClusterLogS, 8>(chirp, n_chan, f_base_mhz, chan_bw_mhz, dm, taper, sideband, s);
+    case 15: return launch_chirp_t<kClusterLogS, 4>(chirp, n_chan, f_base_mhz, chan_bw_mhz, dm, taper, sideband, s, scale);
+    case 16: return launch_chirp_t<kClusterLogS, 8>(chirp, n_chan, f_base_mhz, chan_bw_mhz, dm, taper, sideband, s, scale);
     default: return cudaErrorInvalidValue;
   }
 }

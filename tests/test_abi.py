@@ -126,15 +126,25 @@ def test_setters(cdd):
         assert cdd.cdd_plan_get(p, "pipeline_chunks") == 2
         cdd.cdd_plan_set(p, "taper", cdd.TAPER["welch"])
         assert cdd.cdd_plan_get(p, "taper") == 2
-        # precision: FP32 only; the FP16 / BF16 forms are refused as unsupported
-        cdd.cdd_plan_set(p, "precision", cdd.PRECISION["fp32"])
-        for name in ("fp16", "fp16x2", "bf16x2"):
-            with pytest.raises(cdd.CddError) as ei:
-                cdd.cdd_plan_set(p, "precision", cdd.PRECISION[name])
-            assert ei.value.code == cdd.CDD_EUNSUPPORTED
+        # precision: every form at N = 8192 (the tensor-core forms exist for it)
+        for name in ("fp16", "fp16x2", "bf16x2", "bf16", "fp32"):
+            cdd.cdd_plan_set(p, "precision", cdd.PRECISION[name])
+            assert cdd.cdd_plan_get(p, "precision") == cdd.PRECISION[name]
         with pytest.raises(cdd.CddError) as ei:
             cdd.cdd_plan_set(p, "precision", 9)
         assert ei.value.code == cdd.CDD_EINVAL
+        assert cdd.cdd_plan_get(p, "precision") == cdd.PRECISION["fp32"]
+        # nothing allocated yet: no error flag to read
+        assert cdd.cdd_plan_get(p, "device_errors") == 0
+    finally:
+        cdd.cdd_destroy(p)
+    # other transform lengths run FP32 only: the reduced forms are refused
+    p = cdd.cdd_plan_create(325.0, 32.0, 512, 50.0, 4096, 16)
+    try:
+        for name in ("fp16", "fp16x2", "bf16x2", "bf16"):
+            with pytest.raises(cdd.CddError) as ei:
+                cdd.cdd_plan_set(p, "precision", cdd.PRECISION[name])
+            assert ei.value.code == cdd.CDD_EUNSUPPORTED
         assert cdd.cdd_plan_get(p, "precision") == cdd.PRECISION["fp32"]
     finally:
         cdd.cdd_destroy(p)
