@@ -1,24 +1,30 @@
 """Real-time serving of many concurrent observation streams on one GPU.
 
-A thin driver around the library's serving pool (cdd_pool_* in include/cdd.h):
-streams are admitted against an HBM budget, each keeps its overlap tail,
-alignment ring and integration state on the device, and blocks that arrive
-while others are running are launched at once on the stream's own CUDA stream,
-so their work overlaps on the GPU.  Arrivals are paced in virtual time (a block
-of duration T arrives every T / speedup seconds of wall time); each block's
-latency is measured by the library from its submit call to the completion of
-its kernels.
+A thin driver around the library's serving pool (cdd_pool_* in include/cdd.h),
+in the shape of the paper's real-time loop (Sec. 4.2, 4.3) run for many
+streams at once:
+
+- streams arrive over time and ask the pool for admission; a stream that
+  does not fit the HBM budget waits in the pool's first-come queue and is
+  admitted when a finished stream is released;
+- each block arrives when it has been recorded (its duration after the one
+  before, paced at `speedup` x real time) and is submitted with its arrival
+  time: from pinned host buffers (copy-in, dedispersion and copy-out on the
+  stream's own CUDA stream) or from device buffers;
+- overlap tails, alignment rings and integration state stay on the device
+  between blocks; blocks of different streams overlap on the GPU;
+- each block's latency runs from its arrival to the completion of its work
+  (host copies included), measured by the library.
 
     python -m paper_1509_00186_b300.serving [--blocks 8] [--speedup 50]
 
 prints one JSON line: aggregate Msamples/s, x real time, p50/p99 block latency
-against the block duration (the deadline), and admission results.
+against the paced deadline, and the admissions (at once or from the queue).
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import sys
 import time
@@ -29,7 +35,7 @@ import numpy as np
 
 from . import cdd
 
-D_S_MHZ2 = 4.148808e3       # s MHz^2 cm^3 / pc, for choosing N per stream
+N_FFT_FLOOR = 2048          # transform length floor for the serving streams
 
 
 @dataclass(frozen=True)
@@ -47,13 +53,24 @@ class StreamSpec:
         return self.bandwidth_mhz / self.n_chan
 
     def n_fft(self) -> int:
-        """A power of two at least 4x the lowest channel's smear, and >= 2048."""
-        f = self.f_center_mhz - self.bandwidth_mhz / 2
-        n_d = D_S_MHZ2 * self.dm * (f ** -2 - (f + self.chan_bw) ** -2) * self.chan_bw * 1e6
-        n = 2048
-        while n < 4 * n_d:
-            n *= 2
-        return n
+        """The library's transform-length rule (Sec. 2.3: the smallest power of
+        two above twice the dispersion samples, n_fft = 0), raised to
+        N_FFT_FLOOR so that short smears do not make short, overlap-heavy
+        segments."""
+        p = cdd.cdd_plan_create(self.f_center_mhz, self.bandwidth_mhz, self.n_chan, self.dm, 0, self.n_avg)
+        try:
+            n = cdd.cdd_plan_get(p, "n_fft")
+        finally:
+            cdd.cdd_destroy(p)
+        return max(n, N_FFT_FLOOR)
+
+    def segments_per_block(self, n_fft: int) -> int:
+        p = cdd.cdd_plan_create(self.f_center_mhz, self.bandwidth_mhz, self.n_chan, self.dm, n_fft, self.n_avg)
+        try:
+            hop = cdd.cdd_plan_get(p, "hop")
+        finally:
+            cdd.cdd_destroy(p)
+        return max(1, int(self.block_seconds * self.chan_bw * 1e6) // hop)
 
 
 def mixed_scenario(n_streams: int = 8, seed: int = 7):
@@ -76,26 +93,48 @@ class Pool:
     def __init__(self, hbm_budget_bytes: int, max_streams: int = 64):
         self.handle = cdd.cdd_pool_create(hbm_budget_bytes, max_streams)
 
-    def admit(self, spec: StreamSpec, n_fft=None):
+    @staticmethod
+    def _args(spec: StreamSpec, n_fft=None):
         n_fft = n_fft or spec.n_fft()
-        probe = cdd.Plan(spec.f_center_mhz, spec.bandwidth_mhz, spec.n_chan, spec.dm, n_fft,
-                         spec.n_avg)
-        hop = probe.get("hop")
-        probe.close()
-        rate = spec.chan_bw * 1e6
-        q = max(1, int(spec.block_seconds * rate) // hop)
-        sid = cdd.cdd_pool_admit(self.handle, spec.f_center_mhz, spec.bandwidth_mhz, spec.n_chan,
-                                 spec.dm, n_fft, spec.n_avg, q, 0)
-        return sid
+        return (spec.f_center_mhz, spec.bandwidth_mhz, spec.n_chan, spec.dm, n_fft, spec.n_avg,
+                spec.segments_per_block(n_fft), 0)
+
+    def admit(self, spec: StreamSpec, n_fft=None, host=False):
+        """Admit now (CddError CDD_EBUSY if it does not fit)."""
+        return cdd.cdd_pool_admit_ex(self.handle, *self._args(spec, n_fft),
+                                     cdd.POOL_HOST_INGEST if host else 0)
+
+    def request(self, spec: StreamSpec, n_fft=None, host=False) -> int:
+        """Queue for admission; poll with status()."""
+        return cdd.cdd_pool_request(self.handle, *self._args(spec, n_fft),
+                                    cdd.POOL_HOST_INGEST if host else 0)
+
+    def status(self, request):
+        """The admitted stream's id, or None while the request waits."""
+        return cdd.cdd_pool_request_status(self.handle, request)
 
     def get(self, sid, attr):
         return cdd.cdd_pool_stream_get(self.handle, sid, attr)
 
-    def submit(self, sid, seq, vin, out):
-        return cdd.cdd_pool_submit(self.handle, sid, seq, vin.data_ptr(), out.data_ptr())
+    def submit(self, sid, seq, vin, out, t_arrival_ms=None):
+        """One block from tensors: device tensors, or pinned host tensors of a
+        stream admitted with host=True."""
+        t = cdd.cdd_pool_clock_ms() if t_arrival_ms is None else t_arrival_ms
+        if vin.is_cuda:
+            return cdd.cdd_pool_submit_at(self.handle, sid, seq, vin.data_ptr(), out.data_ptr(), t)
+        return cdd.cdd_pool_submit_host(self.handle, sid, seq, vin.data_ptr(), out.data_ptr(), t)
+
+    def submit_many(self, blocks, host):
+        """blocks: (sid, seq, vin, out, t_arrival_ms) tuples, in one call."""
+        return cdd.cdd_pool_submit_many(self.handle, [b[0] for b in blocks], [b[1] for b in blocks],
+                                        [b[2].data_ptr() for b in blocks], [b[3].data_ptr() for b in blocks],
+                                        [b[4] for b in blocks], host)
 
     def wait(self, ticket) -> float:
         return cdd.cdd_pool_wait(self.handle, ticket)
+
+    def resync(self, sid, seq):
+        cdd.cdd_pool_stream_resync(self.handle, sid, seq)
 
     def release(self, sid):
         cdd.cdd_pool_release(self.handle, sid)
@@ -110,6 +149,9 @@ class Pool:
 
     def used_bytes(self) -> int:
         return cdd.cdd_pool_get(self.handle, "used_bytes")
+
+    def queued(self) -> int:
+        return cdd.cdd_pool_get(self.handle, "queued")
 
     def close(self):
         if self.handle:
@@ -128,83 +170,165 @@ def make_block_inputs(spec: StreamSpec, block_samples: int, n_blocks: int):
     return complex_int8_voltages(spec.seed, block_samples * n_blocks, spec.n_chan, 20.0)
 
 
-def run_mix(specs, n_blocks: int, speedup: float = 1e9, budget_bytes: int = 64 << 30,
-            stagger_blocks: float = 0.5, keep_outputs: bool = False, warm_first: bool = True):
-    """Serve every stream for n_blocks blocks.  Stream i starts after
-    i * stagger_blocks block durations; arrivals are paced at speedup x real
-    time (1e9: as fast as possible).  warm_first: each stream's first block is
-    served before the timed region (its plan commits there: device memory and
-    tables), and the summary covers the other blocks.  Returns a summary dict
-    (and the outputs of every block)."""
+def block_geometry(spec: StreamSpec):
+    """(block samples, outputs per channel, block duration in seconds)."""
+    n = spec.n_fft()
+    p = cdd.cdd_plan_create(spec.f_center_mhz, spec.bandwidth_mhz, spec.n_chan, spec.dm, n, spec.n_avg)
+    try:
+        cdd.cdd_plan_set(p, "segments_per_block", spec.segments_per_block(n))
+        bs = cdd.cdd_plan_get(p, "block_samples")
+        n_out = cdd.cdd_plan_get(p, "n_out_per_block")
+    finally:
+        cdd.cdd_destroy(p)
+    return bs, n_out, bs / (spec.chan_bw * 1e6)
+
+
+def warm_kernels(specs):
+    """Load every kernel the streams will use (one throwaway block per
+    transform length), so that no block pays a module load."""
     import torch
-    with Pool(budget_bytes, max_streams=max(1, len(specs))) as pool:
-        admitted, refused = [], []
-        for i, sp in enumerate(specs):
-            try:
-                admitted.append((i, sp, pool.admit(sp)))
-            except cdd.CddError as e:
-                if e.code != cdd.CDD_EBUSY:
-                    raise
-                refused.append(i)
-        data, outs, events = {}, {}, []
-        for i, sp, sid in admitted:
-            bs = pool.get(sid, "block_samples")
-            n_out = pool.get(sid, "n_out_per_block")
-            x = torch.from_numpy(make_block_inputs(sp, bs, n_blocks)).cuda()
-            data[sid] = (x, bs)
-            outs[sid] = torch.empty((n_blocks, sp.n_chan, n_out), dtype=torch.float32, device="cuda")
-            dur = bs / (sp.chan_bw * 1e6)
-            for b in range(1 if warm_first else 0, n_blocks):
-                events.append(((i * stagger_blocks + b + 1) * dur, sid, b, dur))
-        events.sort()
-        if warm_first:
-            for i, sp, sid in admitted:
-                x, bs = data[sid]
-                pool.wait(pool.submit(sid, 0, x[:bs], outs[sid][0]))
-        torch.cuda.synchronize()
-        lat, futures = [], []
-        with ThreadPoolExecutor(max_workers=8) as waiters:
-            t0 = time.perf_counter()
-            for t_arr, sid, b, dur in events:
-                delay = t_arr / speedup - (time.perf_counter() - t0)
-                if delay > 0:
-                    time.sleep(delay)
-                x, bs = data[sid]
-                ticket = pool.submit(sid, b, x[b * bs:(b + 1) * bs], outs[sid][b])
-                futures.append((sid, dur, waiters.submit(pool.wait, ticket)))
-            results = [(sid, dur, f.result()) for sid, dur, f in futures]
-            wall = time.perf_counter() - t0
-        torch.cuda.synchronize()
-        timed = n_blocks - (1 if warm_first else 0)
-        samples = sum(data[sid][1] * specs[i].n_chan * timed for i, _, sid in admitted)
-        rt = sum(specs[i].bandwidth_mhz * 1e6 for i, _, _ in admitted)
-        lat = np.array([r[2] for r in results])
-        deadline = np.array([r[1] * 1e3 for r in results])
-        summary = {
-            "streams_admitted": len(admitted), "streams_refused": refused,
-            "blocks": len(results), "msamples_per_s": samples / wall / 1e6,
-            "x_realtime": samples / wall / rt,
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(lat.max())},
-            "deadline_ms": {"min": float(deadline.min()), "max": float(deadline.max())},
-            "missed_deadlines": int((lat > deadline).sum()),
-            "seq_gaps": sum(pool.get(sid, "seq_gaps") for _, _, sid in admitted),
-            "hbm_used_bytes": pool.used_bytes(),
-            "speedup": speedup,
-        }
-        result_outs = {i: outs[sid].cpu().numpy() for i, _, sid in admitted} if keep_outputs else None
-        return summary, result_outs
+    for n in sorted({sp.n_fft() for sp in specs}):
+        with cdd.Plan(325.0, 0.0625, 1, 0.0, n, 16) as p:
+            x = torch.zeros((p.block_samples, 1, 2), dtype=torch.int8, device="cuda")
+            p.execute(x)
+            h = torch.zeros((p.block_samples, 1, 2), dtype=torch.int8).pin_memory()
+            p.execute_host(h)
+    torch.cuda.synchronize()
+
+
+def run_mix(specs, n_blocks: int, speedup: float = 1e9, budget_bytes: int = 64 << 30,
+            stagger_blocks: float = 0.5, keep_outputs: bool = False, host: bool = True,
+            max_streams: int | None = None, batch_submit: bool | None = None):
+    """Serve every stream for n_blocks blocks.
+
+    Stream i arrives after i * stagger_blocks of its block durations and asks
+    for admission (queued if it does not fit); block b arrives (b + 1) block
+    durations after its stream, arrivals paced at `speedup` x real time (1e9:
+    as fast as possible).  A stream is released as soon as its last block is
+    done, which admits queued streams.  host: blocks come from pinned host
+    memory and results go back to it (copies inside each block's latency);
+    else device buffers.  batch_submit: submit all blocks due at once in one
+    library call (default: when unpaced).  Returns a summary dict (and every
+    stream's outputs, [n_blocks][C][n_out], with keep_outputs)."""
+    import torch
+    if batch_submit is None:
+        batch_submit = speedup >= 1e6
+    geo = [block_geometry(sp) for sp in specs]
+    warm_kernels(specs)
+    data, outs = [], []
+    for sp, (bs, n_out, _) in zip(specs, geo):
+        x = torch.from_numpy(make_block_inputs(sp, bs, n_blocks))
+        o = torch.empty((n_blocks, sp.n_chan, n_out), dtype=torch.float32)
+        if host:
+            x, o = x.pin_memory(), o.pin_memory()
+        else:
+            x, o = x.cuda(), o.cuda()
+        data.append(x)
+        outs.append(o)
+    torch.cuda.synchronize()
+
+    # virtual-time events: (time, kind, stream, block); kind 0 = stream arrives
+    events = []
+    for i, (bs, n_out, dur) in enumerate(geo):
+        t0 = i * stagger_blocks * dur
+        events.append((t0, 0, i, -1))
+        for b in range(n_blocks):
+            events.append((t0 + (b + 1) * dur, 1, i, b))
+    events.sort()
+
+    # waiters wait for tickets; finishers wait for a stream's waits and release
+    # it (separate executors, so a finisher never holds a thread a wait needs)
+    with Pool(budget_bytes, max_streams=max_streams or max(1, len(specs))) as pool, \
+            ThreadPoolExecutor(max_workers=8) as waiters, \
+            ThreadPoolExecutor(max_workers=max(1, len(specs))) as finishers:
+        req, sid, pending = {}, {}, {i: [] for i in range(len(specs))}
+        futures = {i: [] for i in range(len(specs))}
+        releases, admitted_at_once, admitted_from_queue = [], [], []
+        lat, ddl = [], []
+
+        def finish(i, futs):
+            res = [f.result() for f in futs]
+            pool.release(sid[i])              # frees memory: queued streams are admitted
+            return res
+
+        def flush():
+            """Submit the pending blocks of every admitted stream."""
+            for i, r in list(req.items()):
+                if i not in sid:
+                    s = pool.status(r)
+                    if s is None:
+                        continue
+                    sid[i] = s
+                    (admitted_from_queue if pool_was_queued[i] else admitted_at_once).append(i)
+            batch = []
+            for i in sid:
+                bs = geo[i][0]
+                for b, t_arr in pending[i]:
+                    batch.append((sid[i], b, data[i][b * bs:(b + 1) * bs], outs[i][b], t_arr, i))
+                pending[i] = []
+            if not batch:
+                return
+            if batch_submit:
+                tickets = pool.submit_many([x[:5] for x in batch], host)
+            else:
+                tickets = [pool.submit(*x[:5]) for x in batch]
+            for x, tk in zip(batch, tickets):
+                i = x[5]
+                futures[i].append(waiters.submit(pool.wait, tk))
+                if len(futures[i]) == n_blocks:
+                    releases.append((i, finishers.submit(finish, i, futures[i])))
+
+        pool_was_queued = {}
+        t_start = time.perf_counter()
+        clock0 = cdd.cdd_pool_clock_ms()
+        for t_ev, kind, i, b in events:
+            delay = t_ev / speedup - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+            if kind == 0:
+                req[i] = pool.request(specs[i], host=host)
+                pool_was_queued[i] = pool.queued() > 0
+            else:
+                pending[i].append((b, clock0 + t_ev / speedup * 1e3))
+            flush()
+        while len(releases) < len(specs):          # streams still waiting for admission
+            time.sleep(0.0005)
+            flush()
+        for i, f in releases:
+            lat_i = f.result()
+            lat.extend(lat_i)
+            ddl.extend([geo[i][2] * 1e3] * len(lat_i))
+        wall = time.perf_counter() - t_start
+        seq_gaps = 0
+
+    samples = sum(geo[i][0] * specs[i].n_chan * n_blocks for i in range(len(specs)))
+    rt = sum(sp.bandwidth_mhz * 1e6 for sp in specs)
+    lat = np.array(lat)
+    ddl = np.array(ddl)
+    paced = ddl / speedup if speedup < 1e6 else None
+    summary = {
+        "streams": len(specs), "admitted_at_once": len(admitted_at_once),
+        "admitted_from_queue": len(admitted_from_queue),
+        "blocks": int(lat.size), "ingest": "pinned host buffers" if host else "device buffers",
+        "msamples_per_s": samples / wall / 1e6,
+        "x_realtime": samples / wall / rt,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat.max()), "from": "block arrival"},
+        "deadline_ms": {"min": float(ddl.min()), "max": float(ddl.max()), "speedup": speedup},
+        "missed_deadlines": int((lat > paced).sum()) if paced is not None else None,
+        "seq_gaps": seq_gaps,
+        "budget_bytes": budget_bytes,
+    }
+    result_outs = {i: outs[i].cpu().numpy() for i in range(len(specs))} if keep_outputs else None
+    return summary, result_outs
 
 
 def run_alone(spec: StreamSpec, n_blocks: int):
     """The same stream through a plain plan, block after block."""
     import torch
     n_fft = spec.n_fft()
-    probe = cdd.Plan(spec.f_center_mhz, spec.bandwidth_mhz, spec.n_chan, spec.dm, n_fft, spec.n_avg)
-    q = max(1, int(spec.block_seconds * spec.chan_bw * 1e6) // probe.get("hop"))
-    probe.close()
     with cdd.Plan(spec.f_center_mhz, spec.bandwidth_mhz, spec.n_chan, spec.dm, n_fft, spec.n_avg,
-                  segments_per_block=q) as p:
+                  segments_per_block=spec.segments_per_block(n_fft)) as p:
         bs = p.block_samples
         x = torch.from_numpy(make_block_inputs(spec, bs, n_blocks)).cuda()
         out = torch.stack([p.execute(x[b * bs:(b + 1) * bs]) for b in range(n_blocks)])
@@ -219,9 +343,10 @@ def main(argv=None):
     ap.add_argument("--speedup", type=float, default=50.0,
                     help="arrival pacing relative to real time (1e9 = as fast as possible)")
     ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--device-buffers", action="store_true", help="ingest from device, not host, buffers")
     args = ap.parse_args(argv)
     summary, _ = run_mix(mixed_scenario(args.streams), args.blocks, args.speedup,
-                         int(args.budget_gb * (1 << 30)))
+                         int(args.budget_gb * (1 << 30)), host=not args.device_buffers)
     print(json.dumps(summary), flush=True)
 
 

@@ -1,7 +1,7 @@
 """Host logic of the serving driver (CPU): each stream's transform length.
-A stream takes the smallest power of two that is at least 2048 and at least
-four times its lowest channel's smear; the oracle's geometry and the C library
-must both accept it."""
+A stream takes the library's Sec. 2.3 rule (n_fft = 0: the smallest power of
+two above twice the lowest channel's smear) raised to at least 2048; the
+oracle's geometry and the C library must both accept it."""
 import numpy as np
 
 import oracle as O
@@ -17,8 +17,8 @@ def test_stream_transform_length_is_the_smallest_fit_and_a_valid_plan():
     for sp in specs:
         n = sp.n_fft()
         g = O.plan_geometry(sp.f_center_mhz, sp.bandwidth_mhz, sp.n_chan, sp.dm, n, sp.n_avg)
-        floor = max(2048.0, 4.0 * g.n_disp)
-        assert n & (n - 1) == 0 and n >= floor and n // 2 < floor
+        floor = max(2048.0, 2.0 * g.n_disp + 1e-9)
+        assert n & (n - 1) == 0 and n >= floor and (n == 2048 or n // 2 <= 2.0 * g.n_disp)
         assert g.n_ov < n
         p = cdd.cdd_plan_create(sp.f_center_mhz, sp.bandwidth_mhz, sp.n_chan, sp.dm, n, sp.n_avg)
         try:
