@@ -5,8 +5,10 @@ start-up, processes whose device memory belongs to another allocator or to a
 fixed budget).  For them the library offers cdd_execute_static, which keeps all
 of its scratch in one fixed device array compiled into the library.  This file
 checks it through the C ABI against the plan-based entry point (cdd_plan_create
-+ cdd_execute on a fresh plan), on consecutive calls that leave different
-tables in the shared array.  The file name makes pytest collect it last.
++ cdd_execute on a fresh plan) and against the FP64 oracle, on consecutive
+calls that leave different tables in the shared array, and checks that calls
+after the first on a device take no device memory.  The file name makes
+pytest collect it last.
 """
 import numpy as np
 import pytest
@@ -58,3 +60,31 @@ def test_static_entry_matches_plan_entry_on_consecutive_calls(cuda_device):
         got, want = got.cpu().numpy(), want.cpu().numpy()
         assert np.all(np.isfinite(got)), i
         assert O.rel_rms(got, want) <= TOL, i
+        # the oracle: one block of a fresh stream (zero history)
+        oracle_out = O.dedisperse(x.cpu().numpy(), geo, taper)
+        assert oracle_out.shape == got.shape
+        assert O.rel_rms(got, oracle_out) <= TOL, i
+
+
+def test_static_entry_takes_no_device_memory_after_the_first_call(cuda_device):
+    """After one call on the device (which may load the library's device code
+    and with it the fixed array), further calls leave the device's free memory
+    and torch's allocations unchanged."""
+    import torch
+    args, n_seg, taper = (309.0 + 2.0, 4.0, 64, 50.0, 8192, 16), 3, "none"
+    geo = O.plan_geometry(*args)
+    x = torch.from_numpy(_input(7, n_seg * geo.hop, args[2])).to(cuda_device)
+    first = _static_output(x, args, n_seg, taper)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    outs = [_static_output(x, args, n_seg, taper) for _ in range(2)]
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    del outs                            # the outputs were torch's own, made before each call
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert free1 >= free0 - 2 * first.numel() * 4 - (4 << 20)   # no new device memory but the outputs
+    again = _static_output(x, args, n_seg, taper)
+    torch.cuda.synchronize()
+    assert torch.equal(again, first)
