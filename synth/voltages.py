@@ -2,7 +2,9 @@
 
 Shared by the tests and the benchmark as the single source of inputs.  It holds
 none of the dedispersion arithmetic: it draws Gaussian noise, adds pulses at the
-per-channel sample offsets the caller passes in, rounds and clips to int8.
+per-channel sample offsets the caller passes in -- optionally filtered by a
+per-channel frequency response the caller also passes in (to disperse them
+inside each channel) -- rounds and clips to int8.
 
 Layout is the voltage-beam layout: int8 [T][C][2], time-major, channel fastest,
 real part then imaginary part of each complex sample.
@@ -22,12 +24,21 @@ class PulseTrain:
 
     ``start`` and ``period`` are in samples of channel 0; pulse p occupies
     [start + p*period + offset_k, ... + width) in channel k, where offset_k comes
-    from the caller (e.g. the cold-plasma delay of channel k, rounded)."""
+    from the caller (e.g. the cold-plasma delay of channel k, rounded).
+
+    ``response`` (optional): a callable L -> complex [C][L] array, the caller's
+    frequency response of every channel in numpy FFT bin order.  Each pulse is
+    then filtered by it before it is added: the pulse sits at the centre of a
+    zero-padded window of ``window`` samples (a power of two, with room on
+    both sides for the response's spread), which is transformed, multiplied
+    by the response and transformed back."""
     start: float
     period: float
     width: int
     sigma: float
     offsets: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    response: object = None
+    window: int = 0
 
 
 def complex_int8_voltages(seed: int, n_samp: int, n_chan: int, sigma: float = 20.0,
@@ -57,9 +68,15 @@ def _add_pulses(blk: np.ndarray, r0: int, pulses: PulseTrain, seed: int) -> None
     if offs.shape != (n_chan,):
         raise ValueError("pulse offsets must have one entry per channel")
     lo_off, hi_off = float(offs.min()), float(offs.max())
-    # pulses that can touch rows [r0, r0 + n_rows)
-    p_first = int(np.floor((r0 - pulses.width - hi_off - pulses.start) / pulses.period))
-    p_last = int(np.ceil((r0 + n_rows - lo_off - pulses.start) / pulses.period))
+    filt = pulses.response is not None
+    L = int(pulses.window) if filt else 0
+    if filt and (L < 2 * pulses.width or L & (L - 1)):
+        raise ValueError("the filter window must be a power of two of at least twice the width")
+    # rows a pulse can touch: its boxcar, or its filter window [t0 - L/2, t0 + L/2)
+    before, after = (L // 2, L // 2) if filt else (0, pulses.width)
+    p_first = int(np.floor((r0 - after - hi_off - pulses.start) / pulses.period))
+    p_last = int(np.ceil((r0 + n_rows + before - lo_off - pulses.start) / pulses.period))
+    gain = None
     for p in range(max(p_first, 0), p_last + 1):
         # the pulse's own samples are drawn from a generator keyed on (seed, p),
         # so they do not depend on how the record is chunked
@@ -67,9 +84,23 @@ def _add_pulses(blk: np.ndarray, r0: int, pulses: PulseTrain, seed: int) -> None
         amp = prng.standard_normal((pulses.width, n_chan, 2), dtype=np.float32)
         amp *= np.float32(pulses.sigma)
         t0 = np.rint(pulses.start + p * pulses.period + offs).astype(np.int64)  # [C]
-        rows = t0[None, :] + np.arange(pulses.width)[:, None]                 # [W][C]
+        if filt:
+            if gain is None:
+                gain = np.asarray(pulses.response(L), dtype=np.complex128)
+                if gain.shape != (n_chan, L):
+                    raise ValueError("the response must be complex [C][window]")
+            if not np.any((t0 + after > r0) & (t0 - before < r0 + n_rows)):
+                continue
+            z = np.zeros((n_chan, L), dtype=np.complex128)
+            z[:, L // 2:L // 2 + pulses.width] = (amp[..., 0] + 1j * amp[..., 1]).T
+            z = np.fft.ifft(np.fft.fft(z, axis=1) * gain, axis=1)
+            rows = t0[None, :] - L // 2 + np.arange(L)[:, None]              # [L][C]
+            vals = np.stack([z.real.T, z.imag.T], axis=-1).astype(np.float32)   # [L][C][2]
+        else:
+            rows = t0[None, :] + np.arange(pulses.width)[:, None]             # [W][C]
+            vals = amp
         inside = (rows >= r0) & (rows < r0 + n_rows)
         if not inside.any():
             continue
         w_idx, k_idx = np.nonzero(inside)
-        blk[rows[w_idx, k_idx] - r0, k_idx, :] += amp[w_idx, k_idx, :]
+        blk[rows[w_idx, k_idx] - r0, k_idx, :] += vals[w_idx, k_idx, :]
