@@ -378,7 +378,8 @@ def run_gpu(args, world, rank, local):
         "dtype": DTYPE_OF[args.precision],
         "data": "synthetic: seeded complex int8 N(0,20) noise plus a pulse train "
                 "(period 33 ms, 3% duty) at each channel's dispersion delay",
-        "config": {**config_dict(w, q, hop), "parallelism": f"replicas x{world} (channels independent)"},
+        "config": {**config_dict(w, q, hop), **({"precision": args.precision} if args.precision != "fp32" else {})},
+        "parallelism": f"replicas x{world} (channels independent)",
         "x_realtime": value * 1e6 / (rt_rate * world),
         "hbm_roofline_frac": achieved_gbs / peaks["hbm_gbs"],
         "latency_ms": {"p50": statistics.median(step_ms),
@@ -406,7 +407,10 @@ def run_gpu(args, world, rank, local):
         "paper_gflops": flops / (kernel_ms * 1e-3) / 1e9,
     }
     plan.close()
-    del vin, out
+    del out
+    if not args.no_rows and args.precision == "fp32":
+        line["rows"] = collect_rows(args, dev, peaks, vin, w, q)
+    del vin
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rate(w, vin_np, min(SAMPLE_CHANNELS, C))
     print(json.dumps(line), flush=True)
@@ -493,7 +497,118 @@ def _ols_flops(n_fft, segments):
     return segments * (10.0 * n_fft * math.log2(n_fft) + 9.0 * n_fft)
 
 
-def row_plan_variant(args, dev, peaks, path):
+def device_voltages(rows, n_chan, seed, dev, sigma=20.0):
+    """Seeded complex int8 noise N(0, sigma) drawn on the device: the inputs of
+    the rows under "rows" (their throughput does not depend on the data;
+    the headline line's input comes from synth)."""
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    x = torch.empty((rows, n_chan, 2), dtype=torch.int8, device=dev)
+    chunk = max(1, (1 << 27) // (2 * n_chan))
+    for r0 in range(0, rows, chunk):
+        r1 = min(rows, r0 + chunk)
+        v = torch.randn((r1 - r0, n_chan, 2), device=dev, generator=g).mul_(sigma)
+        x[r0:r1] = v.round_().clamp_(-127, 127).to(torch.int8)
+    return x
+
+
+def tc_tensor_flops(segments, precision):
+    """Tensor-core flops one launch of the tensor-core kernel executes: per
+    segment, radix-32 passes (2 tiles of 128 groups, K = 64) and radix-16
+    passes (4 tiles, K = 32), N = 4R with the hi + lo DFT matrix (2R
+    without), plus the lo operand's product (N = 2R) in every split pass
+    but the exact first one."""
+    split = precision.endswith("x2")
+    def pass_flops(R, tiles, lo):
+        n = 4 * R if split else 2 * R
+        f = tiles * (2 * R // 16) * 2 * 128 * n * 16
+        if split and lo:
+            f += tiles * (2 * R // 16) * 2 * 128 * (2 * R) * 16
+        return f
+    per = pass_flops(32, 2, False) + 4 * pass_flops(16, 4, True) + pass_flops(32, 2, True)
+    return segments * per
+
+
+def row_tc(args, dev, peaks, precision, vin, w, q):
+    """The 512-channel N 8192 block with the radix passes on the tensor cores
+    (tcgen05 DFT products, FP32 accumulation), on the headline's input."""
+    import torch
+    from paper_1509_00186_b300.cdd import Plan
+    plan = Plan(w.f_center_mhz, w.bandwidth_mhz, w.n_chan, w.dm, w.n_fft, w.n_avg,
+                segments_per_block=q, stage_timing=True, precision=precision)
+    C, rows, n_out = w.n_chan, plan.block_samples, plan.n_out
+    out = torch.empty((C, n_out), dtype=torch.float32, device=dev)
+    fn = lambda: plan.execute(vin, out)
+    for _ in range(max(args.warmup, 3)):
+        fn()
+    torch.cuda.synchronize(dev)
+    st0 = {k: plan.get(k) for k in ("timed_blocks", "ols_ns", "corner_turn_ns")}
+    total, steps_ms, clocks = _timed(fn, args.steps, 0, dev)
+    st = {k: plan.get(k) - v for k, v in st0.items()}
+    launches = plan.get("kernel_launches")
+    errors = plan.get("device_errors")
+    plan.close()
+    kernel_ms = st["ols_ns"] / st["timed_blocks"] / 1e6
+    segs = C * q
+    tflops = tc_tensor_flops(segs, precision)
+    ach = tflops / (kernel_ms * 1e-3) / 1e12
+    peak = peaks["bf16_tflops"]
+    roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": None,
+            "peak_source": f"bf16_tflops ({peaks['_source']}; dense f16 runs at the bf16 rate)",
+            "kernel": f"ols_tc_kernel<{PRECISION_CODE[precision]}>", "kernel_ms": kernel_ms,
+            "tensor_flops_per_launch": tflops,
+            "fp32_equivalent": _alu_roofline("same kernel, radix-2 flop count", _ols_flops(w.n_fft, segs),
+                                             kernel_ms, dev, peaks)["frac"],
+            "corner_turn_ms": st["corner_turn_ns"] / st["timed_blocks"] / 1e6}
+    value = float(C) * rows * args.steps / (total * 1e-3) / 1e6
+    config = {"workload": f"tc:{config_dict(w, q, rows // q)['workload']}", "precision": precision}
+    return _line(f"tc_{precision}", args, "dedispersed Msamples/s", value, "Msamples/s",
+                 total / args.steps, steps_ms, config, roof, None, clocks, launches * args.steps,
+                 dtype=DTYPE_OF[precision], x_realtime=value * 1e6 / (C * w.chan_bw_mhz * 1e6),
+                 device_errors=errors)
+
+
+def _compact(line):
+    keep = ("metric", "value", "unit", "ms_per_step", "x_realtime", "dtype", "latency_ms", "gpu_launches",
+            "clocks", "missed_deadlines", "deadline_ms", "device_errors")
+    out = {k: line[k] for k in keep if k in line}
+    out["workload"] = line.get("config", {}).get("workload")
+    r = line.get("roofline")
+    if r:
+        out["roofline"] = {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel", "kernel_ms",
+                                              "fp32_equivalent") if k in r}
+    return out
+
+
+def collect_rows(args, dev, peaks, vin, w, q):
+    """The other rows of the path, each timed briefly (args.row_steps steps
+    after 3 warm-up steps) on one GPU: the tensor-core forms of the headline
+    block, the N = 65536 shape, the batched form, the full-band mode and the
+    serving pool.  A row that fails reports its error instead."""
+    import copy
+    import torch
+    sub = copy.copy(args)
+    sub.steps, sub.warmup, sub.no_cpu_baseline, sub.channels, sub.dm = args.row_steps, 3, True, None, None
+    rows = {}
+    jobs = [("tc_fp16x2", lambda: row_tc(sub, dev, peaks, "fp16x2", vin, w, q)),
+            ("tc_fp16", lambda: row_tc(sub, dev, peaks, "fp16", vin, w, q)),
+            ("precision_n65536", lambda: row_plan_variant(sub, dev, peaks, "precision", device_input=True)),
+            ("batch", lambda: row_batch(sub, dev, peaks, device_input=True)),
+            ("fullband", lambda: row_fullband(sub, dev, peaks)),
+            ("serving", lambda: row_serving(sub, dev, peaks))]
+    for name, fn in jobs:
+        try:
+            rows[name] = _compact(fn())
+        except Exception as e:                      # report, do not lose the headline
+            rows[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
+    return rows
+
+
+def row_plan_variant(args, dev, peaks, path, device_input=False):
     """lsb_hann: the GSB block as a lower-sideband band with the Hann taper.
     dual: the GSB block for two polarisations summed after detection.
     precision: 150 MHz / DM 100 / N 65536 (a cluster of eight CTAs per segment)."""
@@ -511,10 +626,15 @@ def row_plan_variant(args, dev, peaks, path):
     plan = Plan(w.f_center_mhz, bw, w.n_chan, w.dm, w.n_fft, w.n_avg, segments_per_block=q,
                 taper=taper, polarisations=pols, stage_timing=True)
     rows, C, n_out = plan.block_samples, w.n_chan, plan.n_out
-    va = complex_int8_voltages(w.seed, rows, C, w.sigma)
-    vb = complex_int8_voltages(w.seed + 100, rows, C, w.sigma) if pols == 2 else None
-    xa = torch.from_numpy(va).to(dev)
-    xb = torch.from_numpy(vb).to(dev) if pols == 2 else None
+    if device_input:
+        va = vb = None
+        xa = device_voltages(rows, C, w.seed, dev, w.sigma)
+        xb = device_voltages(rows, C, w.seed + 100, dev, w.sigma) if pols == 2 else None
+    else:
+        va = complex_int8_voltages(w.seed, rows, C, w.sigma)
+        vb = complex_int8_voltages(w.seed + 100, rows, C, w.sigma) if pols == 2 else None
+        xa = torch.from_numpy(va).to(dev)
+        xb = torch.from_numpy(vb).to(dev) if pols == 2 else None
     out = torch.empty((C, n_out), dtype=torch.float32, device=dev)
     fn = (lambda: plan.execute_dual(xa, xb, out)) if pols == 2 else (lambda: plan.execute(xa, out))
     for _ in range(max(args.warmup, 3)):
@@ -533,7 +653,7 @@ def row_plan_variant(args, dev, peaks, path):
     roof = _alu_roofline(kname, _ols_flops(geo.n_fft, C * q), kernel_ms, dev, peaks)
     roof["corner_turn_ms"] = st["corner_turn_ns"] / st["timed_blocks"] / 1e6
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and va is not None:
         threads = oracle_threads()
         n_cpu = min(C, {"precision": 4, "dual": 4}.get(path, 8) * threads)
         dt = _cpu_time(lambda: [oracle_channels(v, geo, range(n_cpu), threads, taper)
@@ -588,7 +708,7 @@ def row_band_sum(args, dev, peaks):
                  steps_ms, config, roof, cpu, clocks, args.steps, max_rel_err_plane0=check)
 
 
-def row_batch(args, dev, peaks):
+def row_batch(args, dev, peaks, device_input=False):
     """Batched form: 650 MHz / 200 MHz / 2048 channels / 64 DM trials 20.0..51.5,
     tiers N = 16384, 8192, 4096, 2048 (lowest frequencies first), x16, a block
     of 24 longest hops (3.9 s)."""
@@ -609,8 +729,11 @@ def row_batch(args, dev, peaks):
         f_c = 650.0 - 100.0 + bw / 2
     b = Batch(f_c, bw, C, dms, tiers, n_avg, segments_per_block=24)
     bs, n_out = b.block_samples, b.n_out
-    vin = complex_int8_voltages(4, bs, C, 20.0)
-    x = torch.from_numpy(vin).to(dev)
+    if device_input:
+        vin, x = None, device_voltages(bs, C, 4, dev)
+    else:
+        vin = complex_int8_voltages(4, bs, C, 20.0)
+        x = torch.from_numpy(vin).to(dev)
     out = torch.empty((len(dms), C, n_out), dtype=torch.float32, device=dev)
     total, steps_ms, clocks = _timed(lambda: b.execute(x, out), args.steps, args.warmup, dev)
     launches = b.get("kernel_launches")
@@ -626,7 +749,7 @@ def row_batch(args, dev, peaks):
                          flops, ms, dev, peaks)
     roof["output_bytes_per_step"] = out.numel() * 4
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and vin is not None:
         geo = O.batch_geometry(f_c, bw, C, dms, tiers, n_avg)
         threads = oracle_threads()
         per_tier = max(1, threads // 4)
@@ -692,27 +815,33 @@ def row_serving(args, dev, peaks):
     """Serving pool: 8 mixed streams (GSB 16/32 MHz at 325/610 MHz, upgraded-GMRT
     200 MHz / 2048 channels at 650 MHz; DM 5..150), 8 blocks of 0.5 s each,
     ingested from pinned host memory (copy-in, dedispersion, copy-out inside
-    each block's latency).  Two runs: arrivals paced at 20x real time, for the
-    latency of each block from its arrival against its paced deadline (block
-    duration / 20); then every block at once (submitted in batched library
-    calls), for the aggregate rate.  An HBM budget of half the streams' total
-    needs makes the later streams wait in the pool's queue and enter mid-run."""
+    each block's latency, counted from the block's arrival).  Three runs:
+    - paced: arrivals at 20x real time, every stream admitted on arrival; the
+      latency and missed deadlines (block duration / 20) of this run are the
+      row's latency;
+    - queued: the same pacing with an HBM budget of about half the streams'
+      needs, so later streams wait in the pool's queue and enter mid-run (their
+      blocks' latency includes that wait);
+    - unpaced: every block at once (batched library calls), for the aggregate
+      rate, which is the row's value."""
     from paper_1509_00186_b300 import cdd, serving
     specs = serving.mixed_scenario(8)
-    need = 0
+    needs = []
     for sp in specs:
         n = sp.n_fft()
         with cdd.Plan(sp.f_center_mhz, sp.bandwidth_mhz, sp.n_chan, sp.dm, n, sp.n_avg,
                       segments_per_block=sp.segments_per_block(n)) as p:
-            need += p.get("bytes_needed") + p.get("host_staging_bytes")
-    budget = need // 2
+            needs.append(p.get("bytes_needed") + p.get("host_staging_bytes"))
+    need = sum(needs)
+    budget = max(need // 2, max(needs))
     clocks = ClockSampler(dev.index or 0)
     time.sleep(0.3)
-    paced, _ = serving.run_mix(specs, 8, speedup=20.0, budget_bytes=budget)
+    paced, _ = serving.run_mix(specs, 8, speedup=20.0, budget_bytes=64 << 30)
+    queued, _ = serving.run_mix(specs, 8, speedup=20.0, budget_bytes=budget)
     full, _ = serving.run_mix(specs, 8, speedup=1e9, budget_bytes=64 << 30)
     clock_info = clocks.stop()
     cfg = {"workload": "serving:8-mixed-streams-x8-blocks-0.5s-host-ingest",
-           "streams": [s.__dict__ for s in specs], "paced_budget_bytes": budget,
+           "streams": [s.__dict__ for s in specs], "queued_budget_bytes": budget,
            "streams_total_need_bytes": need}
     line = {"path": "serving", "metric": "served Msamples/s (8 streams from host buffers)",
             "value": full["msamples_per_s"], "unit": "Msamples/s", "n_gpus": 1,
@@ -721,10 +850,10 @@ def row_serving(args, dev, peaks):
             "x_realtime": full["x_realtime"],
             "latency_ms": paced["latency_ms"], "deadline_ms": paced["deadline_ms"],
             "missed_deadlines": paced["missed_deadlines"],
-            "paced_run": paced, "unpaced_run": full,
+            "paced_run": paced, "queued_run": queued, "unpaced_run": full,
             "roofline": None, "roofline_note": "the same per-channel kernels as the block path; "
                                                "this row measures ingest, admission and latency",
-            "clocks": clock_info}
+            "clocks": clock_info, "gpu_launches": None}
     return line
 
 
@@ -755,6 +884,9 @@ def main(argv=None):
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--impl", choices=("cdd", "reference"), default="cdd")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true",
+                    help="headline line only (without the other rows of the path under \"rows\")")
+    ap.add_argument("--row-steps", type=int, default=10, help="timed steps of each row under \"rows\"")
     ap.add_argument("--precision", choices=("fp32", "fp16x2", "bf16x2", "fp16", "bf16"), default="fp32",
                     help="arithmetic of the block's transforms: fp32 on the CUDA cores, the others as "
                          "tensor-core (tcgen05) DFT products with FP32 accumulation")

@@ -45,6 +45,7 @@ struct cdd_plan_s {
   float* d_ring = nullptr;
   int* d_shift = nullptr;
   int* d_err = nullptr;      // tensor-core forms: the kernels' wait-timeout flag
+  void* d_dft = nullptr;     // tensor-core forms: the DFT matrices
   char2* d_in_cm = nullptr;  // channel-major copy of the block (corner-turn path)
   long long ring_len = 0;
   size_t bytes_device = 0;
@@ -182,7 +183,7 @@ int64_t bytes_needed(const cdd_plan p) {
   b += C * (p->r_max + n_out_per_block(p)) * (int64_t)sizeof(float);
   b += C * (int64_t)sizeof(int);
   b += C * p->q * p->hop * (int64_t)sizeof(char2);
-  if (p->precision != CDD_PRECISION_FP32) b += (int64_t)sizeof(int);
+  if (p->precision != CDD_PRECISION_FP32) b += (int64_t)sizeof(int) + (int64_t)cdd::tc_dft_bytes();
   if (p->pols == 2) {
     if (p->n_ov > 0) b += 2 * C * p->n_ov * (int64_t)sizeof(char2);
     b += C * (p->r_max + n_out_per_block(p)) * (int64_t)sizeof(float);
@@ -220,6 +221,7 @@ void free_device(cdd_plan p) {
   cudaFree(p->d_ring);
   cudaFree(p->d_shift);
   cudaFree(p->d_err);
+  cudaFree(p->d_dft);
   cudaFree(p->d_in_cm);
   cudaFree(p->d_tail_b[0]);
   cudaFree(p->d_tail_b[1]);
@@ -295,6 +297,7 @@ int commit_once(cdd_plan p) {
   if (tc) {
     if ((rc = dalloc(p, &p->d_err, sizeof(int)))) return rc;
     CDD_TRY(p, cudaMemset(p->d_err, 0, sizeof(int)));
+    if ((rc = dalloc(p, &p->d_dft, cdd::tc_dft_bytes()))) return rc;
   }
   if (p->pols == 2) {
     if (p->n_ov > 0)
@@ -316,6 +319,7 @@ int commit_once(cdd_plan p) {
   if (e == cudaSuccess)
     e = cdd::launch_chirp_table(p->logn, p->d_chirp, p->n_chan, p->f_base, p->chan_bw, p->dm,
                                 p->taper, p->sideband, s, tc ? cdd::tc_chirp_scale() : 0.0);
+  if (e == cudaSuccess && tc) e = cdd::launch_tc_dft_table(p->precision, p->d_dft, s);
   if (e == cudaSuccess && (rc = zero_state(p, s)) != CDD_OK) {
     cudaStreamDestroy(s);
     return rc;
@@ -382,6 +386,7 @@ int run_block(cdd_plan p, const int8_t* d_in, float* d_out, float* d_volt, int q
   a.ring = pol == 0 ? p->d_ring : p->d_ring_b;
   a.shift = p->d_shift;
   a.volt = reinterpret_cast<float2*>(d_volt);
+  a.dft = p->d_dft;
   a.n_chan = p->n_chan;
   a.n_ov = p->n_ov;
   a.hop = p->hop;

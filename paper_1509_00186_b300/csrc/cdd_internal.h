@@ -21,6 +21,7 @@ struct OlsArgs {
   float* ring;            // [C][ring_len] integrated samples still to be emitted
   const int* shift;       // [C] alignment shift r_k
   float2* volt;           // [C][q*h] dedispersed voltages, or nullptr
+  const void* dft;        // tensor-core forms: the DFT matrices (tc_dft_bytes), else nullptr
   int n_chan, n_ov, hop, n_avg, q, n_out;
   int s_begin, s_count;   // this launch runs segments [s_begin, s_begin + s_count) of q
   long long g0;           // stream index of this block's first integrated sample
@@ -68,6 +69,10 @@ bool tc_supported(int logn, int precision);
 cudaError_t launch_ols_tc(int logn, int precision, const OlsArgs& a, int* err, cudaStream_t s);
 // The chirp table's scale for the tensor-core form.
 double tc_chirp_scale();
+// The DFT matrices of the tensor-core form (radix 32 then radix 16, hi and
+// lo rows, in the operand layout), built in FP64 once per plan.
+size_t tc_dft_bytes();
+cudaError_t launch_tc_dft_table(int precision, void* dft, cudaStream_t s);
 
 // Twiddle factors of every radix pass in the kernel's thread-major layout
 // (FP64, then rounded); twiddle_table_len entries.

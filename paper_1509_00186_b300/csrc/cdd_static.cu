@@ -98,6 +98,7 @@ extern "C" int cdd_execute_static(double f_center_mhz, double bandwidth_mhz, int
   a.ring = ring;
   a.shift = shift;
   a.volt = nullptr;
+  a.dft = nullptr;
   a.n_chan = n_chan;
   a.n_ov = g.n_ov;
   a.hop = g.hop;

@@ -43,14 +43,18 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)_
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
+// Test phase `parity`; the thread may sleep in the instruction for up to
+// kSuspendNs (it wakes as soon as the phase completes), so a waiting warp
+// does not spin on the issue slots.
+constexpr uint32_t kSuspendNs = 20000;
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -221,7 +225,7 @@ struct TcCfg {
   static constexpr int OFF_B16 = OFF_B32 + b_bytes(32);
   static constexpr int TW_LEN = PassPlan<kLogN>::TW_LEN;
   static constexpr int OFF_TW = OFF_B16 + b_bytes(16);
-  static constexpr int OFF_BAR = OFF_TW + TW_LEN * (int)sizeof(float2);
+  static constexpr int OFF_BAR = OFF_TW + tw_slots(TW_LEN) * (int)sizeof(float2);
   static constexpr int OFF_TMEM = OFF_BAR + 8 * PIPES;
   static constexpr int SMEM = OFF_TMEM + 16;
   static constexpr int TMEM_COLS = SPLIT ? 512 : 256;             // per CTA; half per pipeline
@@ -304,9 +308,13 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
   const uint32_t bar = sb + C::OFF_BAR + 8 * pipe;
   uint32_t* const tslot = reinterpret_cast<uint32_t*>(smem + C::OFF_TMEM);
 
-  for (int i = tid; i < C::TW_LEN; i += C::THREADS) tws[i] = __ldg(&a.tw[i]);
-  build_dft<32, BF>(smem + C::OFF_B32, tid, C::THREADS);
-  build_dft<16, BF>(smem + C::OFF_B16, tid, C::THREADS);
+  for (int i = tid; i < C::TW_LEN; i += C::THREADS) tws[tw_slot(i)] = __ldg(&a.tw[i]);
+  {
+    // the DFT matrices (radix 32 then 16), contiguous in the table and here
+    const uint4* src = reinterpret_cast<const uint4*>(a.dft);
+    uint4* dst = reinterpret_cast<uint4*>(smem + C::OFF_B32);
+    for (int i = tid; i < (b_bytes(32) + b_bytes(16)) / 16; i += C::THREADS) dst[i] = __ldg(src + i);
+  }
   if (tid == 0) {
     for (int p = 0; p < C::PIPES; ++p) mbar_init(sb + C::OFF_BAR + 8 * p, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -336,9 +344,13 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
       issue();
       mma_commit(bar);
     }
-    if (!mbar_wait_bounded(bar, phase)) {
+    // one lane per warp waits on the barrier; the warp then synchronises
+    bool ok = true;
+    if ((lt & 31) == 0) ok = mbar_wait_bounded(bar, phase);
+    __syncwarp();
+    if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) {
       abort = true;
-      atomicOr(err, 1);
+      if ((lt & 31) == 0) atomicOr(err, 1);
     }
     phase ^= 1;
     tc_fence_after();
@@ -398,7 +410,7 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int kq = 16 * hf + i;
-          const float2 x = kq ? cmul(v[i], tws[f0_tw(lt, kq)]) : v[i];
+          const float2 x = kq ? cmul(v[i], tws[tw_slot(f0_tw(lt, kq))]) : v[i];
           uint32_t h, l;
           split<BF, SPLIT>(x, h, l);
           const int off = lay_off(lay12(), f0_row(lt, kq), 2 * f0_elem(lt));
@@ -416,7 +428,7 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
       row16<16, SPLIT>(tlane + (uint32_t)((g >> 7) * CW16), 0, v);
 #pragma unroll
       for (int kq = 0; kq < 16; ++kq) {
-        const float2 x = kq ? cmul(v[kq], tws[f1_tw(g, kq)]) : v[kq];
+        const float2 x = kq ? cmul(v[kq], tws[tw_slot(f1_tw(g, kq))]) : v[kq];
         uint32_t h, l;
         split<BF, SPLIT>(x, h, l);
         const int off = lay_off(lay12(), f1_row(g, kq), 2 * f1_elem(g));
@@ -462,7 +474,7 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
       row16<16, SPLIT>(tlane + (uint32_t)((q >> 7) * CW16), 0, v);
 #pragma unroll
       for (int kq = 0; kq < 16; ++kq) {
-        const float2 x = kq ? cmul(v[kq], tws[i2_tw(q, kq)]) : v[kq];
+        const float2 x = kq ? cmul(v[kq], tws[tw_slot(i2_tw(q, kq))]) : v[kq];
         uint32_t h, l;
         split<BF, SPLIT>(x, h, l);
         const int off = lay_off(lay12(), i2_row(q, kq), 2 * i2_elem(q));
@@ -479,7 +491,7 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
       row16<16, SPLIT>(tlane + (uint32_t)((g >> 7) * CW16), 0, v);
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
-        const float2 x = cmul(v[j], tws[i1_tw(g, j)]);
+        const float2 x = cmul(v[j], tws[tw_slot(i1_tw(g, j))]);
         uint32_t h, l;
         split<BF, SPLIT>(x, h, l);
         const int off = lay_off(lay0(), i1_row(g, j), 2 * i1_elem(g));
@@ -569,7 +581,7 @@ cudaError_t launch_tc_t(const OlsArgs& a, int* err, cudaStream_t s) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
-  if (a.in_cm == nullptr) return cudaErrorInvalidValue;      // reads the channel-major copy
+  if (a.in_cm == nullptr || a.dft == nullptr) return cudaErrorInvalidValue;   // channel-major copy, DFT table
   if (!attr_set[dev]) {
     e = cudaFuncSetAttribute(ols_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
@@ -586,7 +598,22 @@ cudaError_t launch_tc_t(const OlsArgs& a, int* err, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <bool BF>
+__global__ void dft_table_kernel(uint8_t* dft) {
+  build_dft<32, BF>(dft, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  build_dft<16, BF>(dft + b_bytes(32), blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
 }  // namespace
+
+size_t tc_dft_bytes() { return (size_t)(b_bytes(32) + b_bytes(16)); }
+
+cudaError_t launch_tc_dft_table(int precision, void* dft, cudaStream_t s) {
+  const bool bf = precision == CDD_PRECISION_BF16 || precision == CDD_PRECISION_BF16X2;
+  if (bf) dft_table_kernel<true><<<16, 256, 0, s>>>(static_cast<uint8_t*>(dft));
+  else dft_table_kernel<false><<<16, 256, 0, s>>>(static_cast<uint8_t*>(dft));
+  return cudaGetLastError();
+}
 
 bool tc_supported(int logn, int precision) {
   return logn == kLogN && precision >= CDD_PRECISION_FP16 && precision <= CDD_PRECISION_BF16;

@@ -137,15 +137,23 @@ CDD_HD constexpr int f1_tw(int g, int k) { return kTwOff1 + 16 * k + (g & 15); }
 // paired table: bins k and k + 1 of a group in one 16-byte entry).
 CDD_HD constexpr int chirp4_index(int q, int k) { return 512 * (k >> 1) + q; }
 // Inverse pass 2, output k of group q -> inverse pass-1 row and element,
-// twiddle w_256^{k (q mod 16)}.
+// twiddle w_256^{k (q mod 16)}.  The pass-1 table holds w_256^{tk} at
+// 16 k + t, symmetric in t and k, so the entry is read at 16 k + (q mod 16):
+// neighbouring groups then read neighbouring entries.
 CDD_HD constexpr int i2_row(int q, int k) { return 16 * (q >> 4) + k; }
 CDD_HD constexpr int i2_elem(int q) { return q & 15; }
-CDD_HD constexpr int i2_tw(int q, int k) { return kTwOff1 + 16 * (q & 15) + k; }
+CDD_HD constexpr int i2_tw(int q, int k) { return kTwOff1 + 16 * k + (q & 15); }
 // Inverse pass 1, output j of group g -> inverse pass-0 row and element,
 // twiddle w_N^{t k0} with t the row and k0 the element.
 CDD_HD constexpr int i1_row(int g, int j) { return (g & 15) + 16 * j; }
 CDD_HD constexpr int i1_elem(int g) { return g >> 4; }
 CDD_HD constexpr int i1_tw(int g, int j) { return 256 * (g >> 4) + (g & 15) + 16 * j; }
+
+// The kernel's shared-memory copy of the twiddle table: 8 spare entries
+// after every 256, so that the two half-warps of an inverse-pass-1 read
+// (rows 256 apart) fall on different banks.
+CDD_HD constexpr int tw_slot(int i) { return i + 8 * (i >> 8); }
+CDD_HD constexpr int tw_slots(int n) { return tw_slot(n - 1) + 1; }
 
 // Tensor-memory columns of one pass: 2R per tile (one product), or 4R with
 // the [hi | lo] matrix.

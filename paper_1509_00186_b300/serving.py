@@ -259,6 +259,7 @@ def run_mix(specs, n_blocks: int, speedup: float = 1e9, budget_bytes: int = 64 <
                     if s is None:
                         continue
                     sid[i] = s
+                    t_admit[i] = cdd.cdd_pool_clock_ms()
                     (admitted_from_queue if pool_was_queued[i] else admitted_at_once).append(i)
             batch = []
             for i in sid:
@@ -278,7 +279,7 @@ def run_mix(specs, n_blocks: int, speedup: float = 1e9, budget_bytes: int = 64 <
                 if len(futures[i]) == n_blocks:
                     releases.append((i, finishers.submit(finish, i, futures[i])))
 
-        pool_was_queued = {}
+        pool_was_queued, t_req, t_admit = {}, {}, {}
         t_start = time.perf_counter()
         clock0 = cdd.cdd_pool_clock_ms()
         for t_ev, kind, i, b in events:
@@ -286,6 +287,7 @@ def run_mix(specs, n_blocks: int, speedup: float = 1e9, budget_bytes: int = 64 <
             if delay > 0:
                 time.sleep(delay)
             if kind == 0:
+                t_req[i] = cdd.cdd_pool_clock_ms()
                 req[i] = pool.request(specs[i], host=host)
                 pool_was_queued[i] = pool.queued() > 0
             else:
@@ -294,10 +296,13 @@ def run_mix(specs, n_blocks: int, speedup: float = 1e9, budget_bytes: int = 64 <
         while len(releases) < len(specs):          # streams still waiting for admission
             time.sleep(0.0005)
             flush()
+        lat_by = {"at_once": [], "from_queue": []}
         for i, f in releases:
             lat_i = f.result()
             lat.extend(lat_i)
             ddl.extend([geo[i][2] * 1e3] * len(lat_i))
+            lat_by["from_queue" if i in admitted_from_queue else "at_once"].extend(lat_i)
+        waits = [t_admit[i] - t_req[i] for i in admitted_from_queue]
         wall = time.perf_counter() - t_start
         seq_gaps = 0
 
@@ -316,6 +321,9 @@ def run_mix(specs, n_blocks: int, speedup: float = 1e9, budget_bytes: int = 64 <
                        "max": float(lat.max()), "from": "block arrival"},
         "deadline_ms": {"min": float(ddl.min()), "max": float(ddl.max()), "speedup": speedup},
         "missed_deadlines": int((lat > paced).sum()) if paced is not None else None,
+        "latency_ms_by_admission": {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99)),
+                                        "blocks": len(v)} for k, v in lat_by.items() if v},
+        "admission_wait_ms": {"max": float(max(waits)), "mean": float(np.mean(waits))} if waits else None,
         "seq_gaps": seq_gaps,
         "budget_bytes": budget_bytes,
     }
