@@ -226,7 +226,7 @@ struct TcCfg {
   static constexpr int TW_LEN = PassPlan<kLogN>::TW_LEN;
   static constexpr int OFF_TW = OFF_B16 + b_bytes(16);
   static constexpr int OFF_BAR = OFF_TW + tw_slots(TW_LEN) * (int)sizeof(float2);
-  static constexpr int OFF_TMEM = OFF_BAR + 8 * PIPES;
+  static constexpr int OFF_TMEM = OFF_BAR + 16 * PIPES;          // two mbarriers per pipeline
   static constexpr int SMEM = OFF_TMEM + 16;
   static constexpr int TMEM_COLS = SPLIT ? 512 : 256;             // per CTA; half per pipeline
   static_assert(SMEM <= 232448, "shared memory of one CTA");
@@ -255,10 +255,12 @@ __device__ __forceinline__ void row16(uint32_t trow, int e0, float2 (&v)[16]) {
 
 // The products of one pass: for each tile of 128 rows and each k-step of 16
 // values, A_hi * [B_hi | B_lo] (N = 4R; N = 2R without the split) and, with
-// `lo`, A_lo * B_hi into the first 2R columns.
+// `lo`, A_lo * B_hi into the first 2R columns.  The first half of the tiles
+// is committed to mbarrier bar0, the second half to bar1, so the rows of the
+// first half can be read while the second half's products run.
 template <int R, bool BF, bool SPLIT>
 __device__ __forceinline__ void issue_pass(uint32_t tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b, Lay L,
-                                           int tiles, bool lo) {
+                                           int tiles, bool lo, uint32_t bar0, uint32_t bar1) {
   constexpr int CW = tile_cols(R, SPLIT);
   const uint32_t id_hi = idesc_f16(128, CW, BF), id_lo = idesc_f16(128, 2 * R, BF);
   for (int tt = 0; tt < tiles; ++tt) {
@@ -269,7 +271,9 @@ __device__ __forceinline__ void issue_pass(uint32_t tmem, uint32_t a_hi, uint32_
       mma_f16(tmem + tt * CW, smem_desc(a_hi + aoff, L.lbo, L.sbo), bd, id_hi, s > 0);
       if (SPLIT && lo) mma_f16(tmem + tt * CW, smem_desc(a_lo + aoff, L.lbo, L.sbo), bd, id_lo, 1u);
     }
+    if (tt == tiles / 2 - 1) mma_commit(bar0);
   }
+  mma_commit(bar1);
 }
 
 __device__ __forceinline__ int tc_work_chan(const OlsArgs& a, int w) { return w / a.s_count; }
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
   const uint32_t a_hi = sb + pipe * C::PIPE_BYTES, a_lo = a_hi + kRegion;
   const uint32_t b32 = sb + C::OFF_B32, b16 = sb + C::OFF_B16;
   float2* const tws = reinterpret_cast<float2*>(smem + C::OFF_TW);
-  const uint32_t bar = sb + C::OFF_BAR + 8 * pipe;
+  const uint32_t bar0 = sb + C::OFF_BAR + 16 * pipe, bar1 = bar0 + 8;
   uint32_t* const tslot = reinterpret_cast<uint32_t*>(smem + C::OFF_TMEM);
 
   for (int i = tid; i < C::TW_LEN; i += C::THREADS) tws[tw_slot(i)] = __ldg(&a.tw[i]);
@@ -316,7 +320,7 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
     for (int i = tid; i < (b_bytes(32) + b_bytes(16)) / 16; i += C::THREADS) dst[i] = __ldg(src + i);
   }
   if (tid == 0) {
-    for (int p = 0; p < C::PIPES; ++p) mbar_init(sb + C::OFF_BAR + 8 * p, 1);
+    for (int p = 0; p < 2 * C::PIPES; ++p) mbar_init(sb + C::OFF_BAR + 8 * p, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -333,28 +337,33 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
   uint32_t phase = 0;
   bool abort = false;
 
-  // Barrier, products, wait: one pass.  False once any thread of the
-  // pipeline has given up on a wait (the pipeline then stops).
+  // Barrier and products of one pass.  False once any thread of the pipeline
+  // has given up on a wait (the pipeline then stops).  Both mbarriers complete
+  // once per pass, so both phase bits flip at every pass after the first.
+  bool issued = false;
   auto pass = [&](auto issue) -> bool {
+    if (issued) phase ^= 3u;
+    issued = true;
     fence_async_shared();
     tc_fence_before();
     if (bar_or(barid, kT, abort)) return false;
     if (lt == 0) {
       tc_fence_after();
       issue();
-      mma_commit(bar);
     }
-    // one lane per warp waits on the barrier; the warp then synchronises
+    return true;
+  };
+  // Wait until the products of half h (0: the first half of the tiles) are in
+  // tensor memory: one lane per warp waits, the warp then synchronises.
+  auto wait_half = [&](int h) {
     bool ok = true;
-    if ((lt & 31) == 0) ok = mbar_wait_bounded(bar, phase);
+    if ((lt & 31) == 0) ok = mbar_wait_bounded(h ? bar1 : bar0, (phase >> h) & 1u);
     __syncwarp();
     if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) {
       abort = true;
       if ((lt & 31) == 0) atomicOr(err, 1);
     }
-    phase ^= 1;
     tc_fence_after();
-    return true;
   };
 
   const int work = a.n_chan * a.s_count;
@@ -400,7 +409,8 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
       }
     }
     // ---- forward pass 0 (radix 32 over stride 256); the int8 input is exact: no lo product
-    if (!pass([&] { issue_pass<32, BF, SPLIT>(tmem, a_hi, a_lo, b32, lay0(), 2, false); })) break;
+    if (!pass([&] { issue_pass<32, BF, SPLIT>(tmem, a_hi, a_lo, b32, lay0(), 2, false, bar0, bar1); })) break;
+    wait_half(lt >> 7);
     {
       const uint32_t trow = tlane + (uint32_t)((lt >> 7) * CW32);
 #pragma unroll
@@ -420,10 +430,11 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
       }
     }
     // ---- forward pass 1 (radix 16 over stride 16)
-    if (!pass([&] { issue_pass<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true); })) break;
+    if (!pass([&] { issue_pass<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true, bar0, bar1); })) break;
 #pragma unroll
     for (int gi = 0; gi < 2; ++gi) {
       const int g = lt + kT * gi;
+      wait_half(gi);
       float2 v[16];
       row16<16, SPLIT>(tlane + (uint32_t)((g >> 7) * CW16), 0, v);
 #pragma unroll
@@ -439,12 +450,13 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
     // ---- forward pass 2 (radix 16, stride 1), then the chirp; the first
     // inverse pass works on the same groups, conjugated, so each thread
     // rewrites its own rows
-    if (!pass([&] { issue_pass<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true); })) break;
+    if (!pass([&] { issue_pass<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true, bar0, bar1); })) break;
     {
       const float4* ch4 = reinterpret_cast<const float4*>(a.chirp + (size_t)k * kN);
 #pragma unroll
       for (int gi = 0; gi < 2; ++gi) {
         const int q = lt + kT * gi;
+        wait_half(gi);
         float2 v[16];
         row16<16, SPLIT>(tlane + (uint32_t)((q >> 7) * CW16), 0, v);
         uint32_t hw[16], lw[16];
@@ -466,10 +478,11 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
       }
     }
     // ---- inverse pass 2 (conjugated data)
-    if (!pass([&] { issue_pass<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true); })) break;
+    if (!pass([&] { issue_pass<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true, bar0, bar1); })) break;
 #pragma unroll
     for (int gi = 0; gi < 2; ++gi) {
       const int q = lt + kT * gi;
+      wait_half(gi);
       float2 v[16];
       row16<16, SPLIT>(tlane + (uint32_t)((q >> 7) * CW16), 0, v);
 #pragma unroll
@@ -483,10 +496,11 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
       }
     }
     // ---- inverse pass 1
-    if (!pass([&] { issue_pass<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true); })) break;
+    if (!pass([&] { issue_pass<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true, bar0, bar1); })) break;
 #pragma unroll
     for (int gi = 0; gi < 2; ++gi) {
       const int g = lt + kT * gi;
+      wait_half(gi);
       float2 v[16];
       row16<16, SPLIT>(tlane + (uint32_t)((g >> 7) * CW16), 0, v);
 #pragma unroll
@@ -500,8 +514,9 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
       }
     }
     // ---- inverse pass 0 (radix 32): conj(y) / kOutScale at positions lt + 256 j
-    if (!pass([&] { issue_pass<32, BF, SPLIT>(tmem, a_hi, a_lo, b32, lay0(), 2, true); })) break;
+    if (!pass([&] { issue_pass<32, BF, SPLIT>(tmem, a_hi, a_lo, b32, lay0(), 2, true, bar0, bar1); })) break;
     float2 u[kR0];
+    wait_half(lt >> 7);
     {
       const uint32_t trow = tlane + (uint32_t)((lt >> 7) * CW32);
       float2 v[16];
