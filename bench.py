@@ -575,6 +575,9 @@ def _compact(line):
             "clocks", "missed_deadlines", "deadline_ms", "device_errors")
     out = {k: line[k] for k in keep if k in line}
     out["workload"] = line.get("config", {}).get("workload")
+    for k in ("launch_form", "tuning_ms"):
+        if k in line.get("config", {}):
+            out[k] = line["config"][k]
     r = line.get("roofline")
     if r:
         out["roofline"] = {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel", "kernel_ms",
@@ -737,6 +740,8 @@ def row_batch(args, dev, peaks, device_input=False):
     out = torch.empty((len(dms), C, n_out), dtype=torch.float32, device=dev)
     total, steps_ms, clocks = _timed(lambda: b.execute(x, out), args.steps, args.warmup, dev)
     launches = b.get("kernel_launches")
+    form = {0: "tiers", 1: "tiers_np", 2: "multi"}.get(b.get("batch_form"), "?")
+    tune_ms = {"tiers": b.get("tune_ns_tiers") / 1e6, "multi": b.get("tune_ns_multi") / 1e6}
     flops = 0.0
     for t in range(len(tiers)):
         n, nov, _, ct = b.tier(t)
@@ -765,7 +770,8 @@ def row_batch(args, dev, peaks, device_input=False):
                "seconds": dt, "sample": f"{len(chans)} channels ({per_tier} per tier) x {bs} samples x "
                                         f"{len(dms)} DMs, {threads} threads over channels"}
     config = {"workload": f"batch:{f_c:g}MHz-{bw:g}MHz-{C}ch-{len(dms)}DM-N16384/8192/4096/2048-x{n_avg}",
-              "block_samples_per_channel": bs, "dm_trials": len(dms)}
+              "block_samples_per_channel": bs, "dm_trials": len(dms),
+              "launch_form": form, "tuning_ms": tune_ms}
     return _line("batch", args, "input Msamples/s through all DM trials", value, "Msamples/s", ms,
                  steps_ms, config, roof, cpu, clocks, launches * args.steps,
                  x_realtime=value * 1e6 / (bw * 1e6))

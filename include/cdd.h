@@ -110,9 +110,37 @@ enum cdd_attr {
                                       products (it then stopped early and its
                                       outputs are invalid); reading waits for
                                       the device                               */
-  CDD_ATTR_HOST_STAGING_BYTES = 25 /* device bytes the host-buffer path adds
+  CDD_ATTR_HOST_STAGING_BYTES = 25,/* device bytes the host-buffer path adds
                                       (two chunks in, two out)                 */
+  CDD_ATTR_BATCH_FORM = 26,        /* batch only, settable: the launch form
+                                      (enum cdd_batch_form), or -1 (default):
+                                      chosen by timing at the first execute   */
+  CDD_ATTR_TUNE_NS_TIERS = 27,     /* batch only: device time of each form in
+                                      the first execute's tuning, ns (0: not
+                                      run)                                     */
+  CDD_ATTR_TUNE_NS_TIERS_NP = 28,
+  CDD_ATTR_TUNE_NS_MULTI = 29
 };
+
+/* Launch forms of a batch; they differ in how the (tier, channel, segment)
+ * work items reach the SMs.  TIERS and MULTI give the same outputs bit for
+ * bit; TIERS_NP forms the N = 8192 tier's first-pass twiddles as products (as
+ * the one-CTA-per-item kernels of 16384 points do), so its outputs differ from
+ * theirs in the last bits, within the same accuracy.
+ *   TIERS: one launch per tier, the N = 8192 tier as a persistent kernel
+ *     (one CTA per SM, twiddles in shared memory), the others one CTA per
+ *     work item (several CTAs per SM);
+ *   TIERS_NP: one launch per tier, every tier one CTA per work item;
+ *   MULTI: one persistent launch for every tier (tiers of 2048..16384
+ *     points, at most four): one 512-thread CTA per SM takes the tiers
+ *     longest-first, its groups claiming work items from each tier's counter,
+ *     so CTAs move to the next tier without waiting for a launch boundary.
+ * With CDD_ATTR_BATCH_FORM = -1 the first execute runs TIERS and (where it
+ * applies) MULTI once each on its block, times them with CUDA events
+ * (synchronously) and keeps the faster for this and later executes; the choice is remembered per device
+ * and batch shape for the process, so later batches of that shape skip the
+ * timing.  Make the first execute before capturing a stream into a graph. */
+enum cdd_batch_form { CDD_BATCH_FORM_TIERS = 0, CDD_BATCH_FORM_TIERS_NP = 1, CDD_BATCH_FORM_MULTI = 2 };
 
 enum cdd_taper { CDD_TAPER_NONE = 0, CDD_TAPER_HANN = 1, CDD_TAPER_WELCH = 2 };
 
@@ -282,12 +310,14 @@ typedef struct cdd_batch_s* cdd_batch;
 
 int cdd_batch_create(cdd_batch* batch, double f_center_mhz, double bandwidth_mhz, int n_chan,
                      const double* dms, int n_dm, const int* tier_nfft, int n_tiers, int n_avg);
-/* CDD_ATTR_SEGMENTS_PER_BLOCK and CDD_ATTR_TAPER (applied to every DM trial),
- * before the first execute. */
+/* CDD_ATTR_SEGMENTS_PER_BLOCK, CDD_ATTR_TAPER (applied to every DM trial) and
+ * CDD_ATTR_BATCH_FORM, before the first execute.  MULTI for a shape it does
+ * not cover makes the first execute return CDD_EUNSUPPORTED. */
 int cdd_batch_set(cdd_batch batch, int attr, int64_t value);
 /* SEGMENTS_PER_BLOCK, BLOCK_SAMPLES, N_OUT_PER_BLOCK, R_MAX, BYTES_DEVICE,
  * BLOCKS_DONE, KERNEL_LAUNCHES, N_CHAN, N_AVG, HOP (the longest hop),
- * PHASE_FLOATS, TAPER. */
+ * PHASE_FLOATS, TAPER, BATCH_FORM (the form in use once one ran),
+ * TUNE_NS_*. */
 int cdd_batch_get(cdd_batch batch, int attr, int64_t* value);
 /* Geometry of tier t (any output pointer may be NULL). */
 int cdd_batch_tier(cdd_batch batch, int t, int64_t* n_fft, int64_t* n_ov, int64_t* first_chan,

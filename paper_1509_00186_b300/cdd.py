@@ -31,8 +31,10 @@ ATTR = {
     "blocks_done": 11, "pipeline_chunks": 12, "kernel_launches": 13, "bytes_needed": 14,
     "seq_gaps": 15, "polarisations": 16, "stage_timing": 17, "timed_blocks": 18,
     "corner_turn_ns": 19, "ols_ns": 20, "phase_floats": 22, "precision": 23,
-    "device_errors": 24, "host_staging_bytes": 25,
+    "device_errors": 24, "host_staging_bytes": 25, "batch_form": 26, "tune_ns_tiers": 27,
+    "tune_ns_tiers_np": 28, "tune_ns_multi": 29,
 }
+BATCH_FORM = {"tune": -1, "tiers": 0, "tiers_np": 1, "multi": 2}
 POOL_ATTR = {"budget": 100, "used_bytes": 101, "streams": 102, "queued": 103}
 POOL_HOST_INGEST = 1
 TAPER = {"none": 0, "hann": 1, "welch": 2}
@@ -654,13 +656,15 @@ class Batch:
     """Owning wrapper of a batched (many-DM, tiered-N) plan."""
 
     def __init__(self, f_center_mhz, bandwidth_mhz, n_chan, dms, tier_nfft, n_avg,
-                 segments_per_block=None, taper="none"):
+                 segments_per_block=None, taper="none", form="tune"):
         self.handle = cdd_batch_create(f_center_mhz, bandwidth_mhz, n_chan, dms, tier_nfft, n_avg)
         try:
             if segments_per_block is not None:
                 cdd_batch_set(self.handle, "segments_per_block", segments_per_block)
             if taper != "none":
                 cdd_batch_set(self.handle, "taper", TAPER[taper])
+            if form != "tune":
+                cdd_batch_set(self.handle, "batch_form", BATCH_FORM[form])
         except Exception:
             cdd_batch_destroy(self.handle)
             raise

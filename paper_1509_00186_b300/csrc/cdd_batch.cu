@@ -15,6 +15,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -49,6 +52,7 @@ struct BatchArgs {
   const float2* dms;        // [n_dm] DM as (hi, lo)
   float2* xs;               // [n_tchan * q][N] spectra
   int n_chan, chan0, n_tchan, n_ov, hop, n_avg, q, n_out, n_dm, r_max, tail_stride;
+  int persistent;           // N = 8192 per-tier launch: the persistent kernel (1) or one CTA per item (0)
 };
 
 // exp(-2 pi i * DM * T1): the product and its reduction modulo one turn in
@@ -119,7 +123,7 @@ __host__ __device__ constexpr int row_position(int idx) {
 
 template <int LOGN, bool SH, bool T1F, bool TAP, class Sync>
 __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, const float2* tw, int lt,
-                                              bool active, int w, Sync sync) {
+                                              bool active, int w, float2* xk, Sync sync) {
   using PL = PassPlan<LOGN>;
   constexpr int N = PL::N;
   constexpr int T = PL::T;
@@ -186,7 +190,6 @@ __device__ __forceinline__ bool batch_segment(const BatchArgs& a, float2* buf, c
   // ---- last forward radix: the spectrum, scaled by 1/N, to this segment's
   // scratch row.  A thread later chirps and writes back exactly the groups it
   // reads here, so no barrier separates the two.
-  float2* xk = a.xs + (size_t)w * N;
   if (active) {
 #pragma unroll 1
     for (int i = 0; i < PERC; ++i) {
@@ -360,7 +363,8 @@ batch_kernel(const BatchArgs a) {
   float2* buf = smem + g * CF::SEG_F2;
   const int w = blockIdx.x * CF::G + g;
   const bool active = w < a.n_tchan * a.q;
-  batch_segment<LOGN, false, T1F, TAP>(a, buf, a.tw, lt, active, w, [] { __syncthreads(); });
+  batch_segment<LOGN, false, T1F, TAP>(a, buf, a.tw, lt, active, w, a.xs + (size_t)w * PL::N,
+                                       [] { __syncthreads(); });
 }
 
 // Persistent form for N = 8192: one CTA per SM, two groups of 256
@@ -392,9 +396,118 @@ batch_persistent_kernel(const BatchArgs a) {
   auto sync = [bar] { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(T) : "memory"); };
   const int work = a.n_tchan * a.q;
   for (int w = blockIdx.x * BP::GROUPS + g; w < work; w += gridDim.x * BP::GROUPS) {
-    if (batch_segment<LOGN, true, T1F, TAP>(a, buf, tws, lt, true, w, sync))
+    if (batch_segment<LOGN, true, T1F, TAP>(a, buf, tws, lt, true, w, a.xs + (size_t)w * PL::N, sync))
       sync();                                  // buf is rewritten by the next work item
   }
+}
+
+// ------------------------------------------------------------------ one launch
+//
+// Every tier of a batch in one persistent launch: one 512-thread CTA per SM
+// takes the tiers in order (the longest transforms first), and within a tier
+// its groups (one per N / R_0 threads: 1 x 512 for N = 16384, 2 x 256 for
+// 8192 and 4096, 4 x 128 for 2048) claim (channel, segment) work items from
+// the tier's counter until it is exhausted; a CTA that runs out moves on to
+// the next tier while others finish theirs, so no launch boundary idles the
+// GPU between tiers.  Each group parks its spectrum in its own scratch row
+// (slots: 16384 points per CTA, L2-resident) instead of one row per item.
+constexpr int kMultiThreads = 512;
+constexpr int kMultiTiers = 4;
+
+struct MultiArgs {
+  BatchArgs tier[kMultiTiers];
+  int logn[kMultiTiers];
+  int n_tiers;
+  int* counters;       // [kMultiTiers] work items claimed (zero at launch)
+  float2* slots;       // [gridDim.x][16384] scratch rows
+};
+
+template <int LOGN>
+struct MultiCfg {
+  using PL = PassPlan<LOGN>;
+  static constexpr int T = PL::T;
+  static constexpr int G = kMultiThreads / T;
+  static constexpr bool SH = LOGN == 13;        // N = 8192 stages its twiddles, as its persistent kernel
+  static constexpr size_t SMEM = (size_t(SH ? PL::TW_LEN : 0) + size_t(G) * padded_len<LOGN>()) * sizeof(float2);
+  static_assert(G * T == kMultiThreads, "a tier's groups fill the CTA");
+};
+
+// The multi-tier launch handles tiers of 2048 to 16384 points.
+__host__ __device__ constexpr bool multi_logn_ok(int logn) { return logn >= 11 && logn <= 14; }
+
+template <int LOGN, bool T1F, bool TAP>
+__device__ __forceinline__ void multi_tier(const BatchArgs& a, int* counter, float2* smem, float2* slot,
+                                           volatile int* claim) {
+  using MC = MultiCfg<LOGN>;
+  using PL = PassPlan<LOGN>;
+  constexpr int T = MC::T;
+  const int g = threadIdx.x / T, lt = threadIdx.x % T;
+  float2* buf = smem + (MC::SH ? PL::TW_LEN : 0) + g * padded_len<LOGN>();
+  const float2* tw = a.tw;
+  if constexpr (MC::SH) {
+    for (int i = threadIdx.x; i < PL::TW_LEN; i += kMultiThreads) smem[i] = __ldg(&a.tw[i]);
+    __syncthreads();
+    tw = smem;
+  }
+  const int bar = 1 + g;
+  auto sync = [bar] { asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(T) : "memory"); };
+  float2* xk = slot + (size_t)g * PL::N;
+  const int work = a.n_tchan * a.q;
+  for (;;) {
+    if (lt == 0) claim[g] = atomicAdd(counter, 1);
+    sync();
+    const int w = claim[g];              // read by the group before its next barrier
+    if (w >= work) break;
+    if (batch_segment<LOGN, MC::SH, T1F, TAP>(a, buf, tw, lt, true, w, xk, sync)) sync();
+  }
+}
+
+template <bool T1F, bool TAP>
+__global__ void __launch_bounds__(kMultiThreads, 1) batch_multi_kernel(const MultiArgs m) {
+  extern __shared__ __align__(16) float2 smem[];
+  __shared__ int claim[kMultiThreads / 128];
+  float2* slot = m.slots + (size_t)blockIdx.x * 16384;
+  for (int t = 0; t < m.n_tiers; ++t) {
+    switch (m.logn[t]) {
+      case 14: multi_tier<14, T1F, TAP>(m.tier[t], m.counters + t, smem, slot, claim); break;
+      case 13: multi_tier<13, T1F, TAP>(m.tier[t], m.counters + t, smem, slot, claim); break;
+      case 12: multi_tier<12, T1F, TAP>(m.tier[t], m.counters + t, smem, slot, claim); break;
+      case 11: multi_tier<11, T1F, TAP>(m.tier[t], m.counters + t, smem, slot, claim); break;
+      default: break;
+    }
+    __syncthreads();                     // the shared memory is laid out anew for the next tier
+  }
+}
+
+size_t multi_smem() {
+  size_t b = MultiCfg<14>::SMEM;
+  b = b > MultiCfg<13>::SMEM ? b : MultiCfg<13>::SMEM;
+  b = b > MultiCfg<12>::SMEM ? b : MultiCfg<12>::SMEM;
+  return b > MultiCfg<11>::SMEM ? b : MultiCfg<11>::SMEM;
+}
+
+template <bool T1F, bool TAP>
+cudaError_t launch_multi_tt(const MultiArgs& m, unsigned grid, cudaStream_t s) {
+  static bool attr_set[128] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+  if (!attr_set[dev]) {
+    e = cudaFuncSetAttribute(batch_multi_kernel<T1F, TAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)multi_smem());
+    if (e != cudaSuccess) return e;
+    attr_set[dev] = true;
+  }
+  e = cudaMemsetAsync(m.counters, 0, kMultiTiers * sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  batch_multi_kernel<T1F, TAP><<<grid, kMultiThreads, multi_smem(), s>>>(m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_multi(const MultiArgs& m, bool t1f, bool tap, unsigned grid, cudaStream_t s) {
+  if (tap) return t1f ? launch_multi_tt<true, true>(m, grid, s) : launch_multi_tt<false, true>(m, grid, s);
+  return t1f ? launch_multi_tt<true, false>(m, grid, s) : launch_multi_tt<false, false>(m, grid, s);
 }
 
 // T1[kt][idx]: Eq. 3 phase in turns at DM = 1 for channel chan0 + kt and the
@@ -442,7 +555,7 @@ cudaError_t launch_batch_tt(const BatchArgs& a, cudaStream_t s) {
   const long long work = (long long)a.n_tchan * a.q;
   // N = 8192 only: the N = 4096 tier runs faster as three non-persistent
   // 256-thread CTAs per SM (142.3 against 146.4 ms per batched block)
-  if constexpr (LOGN == 13) {
+  if constexpr (LOGN == 13) if (a.persistent) {
     using BP = BatchPersist<LOGN>;
     static bool pset[128] = {};
     if (!pset[dev]) {
@@ -569,6 +682,14 @@ struct cdd_batch_s {
   int* d_shift = nullptr;
   float2* d_dms = nullptr;
   float2* d_xs = nullptr;
+  // execution form (CDD_ATTR_BATCH_FORM): requested (-1: tune at the first
+  // execute) and in use; the one-launch form's counters and scratch slots
+  int form_req = -1, form = -1;
+  bool multi_ok = false;
+  unsigned multi_grid = 0;
+  int* d_counters = nullptr;
+  float2* d_slots = nullptr;
+  int64_t tune_ns[3] = {0, 0, 0};
   size_t bytes_device = 0;
   int parity = 0;
   int64_t blocks = 0;
@@ -622,6 +743,8 @@ void bfree(cdd_batch b) {
   cudaFree(b->d_shift);
   cudaFree(b->d_dms);
   cudaFree(b->d_xs);
+  cudaFree(b->d_counters);
+  cudaFree(b->d_slots);
 }
 
 int bzero_state(cdd_batch b, cudaStream_t s) {
@@ -677,6 +800,16 @@ int bcommit_once(cdd_batch b) {
     }
   }
   if ((rc = balloc(b, &b->d_xs, xs * sizeof(float2)))) return rc;
+  // the one-launch form: tiers of 2048 to 16384 points, at most four
+  b->multi_ok = b->tiers.size() <= (size_t)cdd::kMultiTiers;
+  for (auto& t : b->tiers) b->multi_ok = b->multi_ok && cdd::multi_logn_ok(t.logn);
+  if (b->multi_ok) {
+    int sms = 0;
+    BTRY(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    b->multi_grid = (unsigned)sms;
+    if ((rc = balloc(b, &b->d_counters, cdd::kMultiTiers * sizeof(int)))) return rc;
+    if ((rc = balloc(b, &b->d_slots, (size_t)sms * 16384 * sizeof(float2)))) return rc;
+  }
 
   std::vector<int> sh(b->shift.begin(), b->shift.end());
   BTRY(b, cudaMemcpy(b->d_shift, sh.data(), sh.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -704,6 +837,39 @@ int bcommit_once(cdd_batch b) {
   if (e != cudaSuccess) return bfail(b, e);
   b->committed = true;
   return CDD_OK;
+}
+
+// Execution forms of a batch (CDD_ATTR_BATCH_FORM).
+constexpr int kFormTiers = 0;     // one launch per tier; N = 8192 as a persistent kernel
+constexpr int kFormTiersNP = 1;   // one launch per tier; every tier one CTA per work item
+constexpr int kFormMulti = 2;     // every tier in one persistent launch
+constexpr int kForms = 3;
+
+int launches_of(const cdd_batch b, int form) {
+  return form == kFormMulti ? 2 : (int)b->tiers.size();     // the one-launch form also clears its counters
+}
+
+// Forms chosen by tuning, per device and batch shape, for the process's lifetime.
+std::mutex g_form_mu;
+std::map<std::vector<int64_t>, int> g_forms;
+
+std::vector<int64_t> form_key(const cdd_batch b) {
+  std::vector<int64_t> k = {b->device, b->n_dm, b->n_avg, b->t1_single ? 1 : 0, b->taper, b->q};
+  for (auto& t : b->tiers) {
+    k.push_back(t.logn);
+    k.push_back(t.n_tchan);
+    k.push_back(t.hop);
+  }
+  return k;
+}
+int cached_form(const cdd_batch b) {
+  std::lock_guard<std::mutex> lock(g_form_mu);
+  auto it = g_forms.find(form_key(b));
+  return it == g_forms.end() ? -1 : it->second;
+}
+void remember_form(const cdd_batch b, int form) {
+  std::lock_guard<std::mutex> lock(g_form_mu);
+  g_forms[form_key(b)] = form;
 }
 
 int bprepare(cdd_batch b) {
@@ -826,6 +992,11 @@ int cdd_batch_set(cdd_batch b, int attr, int64_t value) {
     b->taper = (int)value;
     return CDD_OK;
   }
+  if (attr == CDD_ATTR_BATCH_FORM) {
+    if (value < -1 || value >= kForms) return CDD_EINVAL;
+    b->form_req = (int)value;
+    return CDD_OK;
+  }
   if (attr != CDD_ATTR_SEGMENTS_PER_BLOCK) return CDD_EINVAL;
   if (value < 1 || value * b->hop_max * b->n_chan > ((int64_t)1 << 40)) return CDD_EINVAL;
   if (value * b->hop_max / b->n_avg < b->r_max) return CDD_EINVAL;
@@ -850,6 +1021,10 @@ int cdd_batch_get(cdd_batch b, int attr, int64_t* v) {
     case CDD_ATTR_N_AVG: *v = b->n_avg; break;
     case CDD_ATTR_HOP: *v = b->hop_max; break;
     case CDD_ATTR_TAPER: *v = b->taper; break;
+    case CDD_ATTR_BATCH_FORM: *v = b->form >= 0 ? b->form : b->form_req; break;
+    case CDD_ATTR_TUNE_NS_TIERS: *v = b->tune_ns[kFormTiers]; break;
+    case CDD_ATTR_TUNE_NS_TIERS_NP: *v = b->tune_ns[kFormTiersNP]; break;
+    case CDD_ATTR_TUNE_NS_MULTI: *v = b->tune_ns[kFormMulti]; break;
     default: return CDD_EINVAL;
   }
   return CDD_OK;
@@ -879,6 +1054,7 @@ int cdd_batch_execute(cdd_batch b, const int8_t* d_in, float* d_out, cudaStream_
   const int64_t rows = block_samples(b);
   BTRY(b, cdd::launch_corner_turn(reinterpret_cast<const char2*>(d_in), b->d_in_cm, 0, rows, rows,
                                   b->n_chan, stream));
+  std::vector<cdd::BatchArgs> args;
   for (auto& t : b->tiers) {
     cdd::BatchArgs a;
     a.in_cm = b->d_in_cm;
@@ -906,11 +1082,79 @@ int cdd_batch_execute(cdd_batch b, const int8_t* d_in, float* d_out, cudaStream_
     a.n_dm = b->n_dm;
     a.r_max = (int)(b->r_max > 0 ? b->r_max : 1);
     a.tail_stride = b->n_ov_max > 0 ? b->n_ov_max : 1;
-    BTRY(b, cdd::launch_batch(t.logn, a, stream));
+    a.persistent = 1;
+    args.push_back(a);
   }
+  // TIERS and MULTI compute each (channel, segment, DM) with the same
+  // arithmetic and write the same outputs, tails and carried outputs; only
+  // the launch shape differs.  The first execute of an untuned batch runs
+  // each once on this block, times it with CUDA events and keeps the fastest
+  // (the last run's writes are the block's result).
+  auto run = [&](int form) -> int {
+    if (form == kFormMulti) {
+      cdd::MultiArgs m = {};
+      std::vector<int> order(args.size());
+      for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+      std::stable_sort(order.begin(), order.end(),
+                       [&](int x, int y) { return b->tiers[x].logn > b->tiers[y].logn; });   // longest first
+      for (size_t i = 0; i < order.size(); ++i) {
+        m.tier[i] = args[order[i]];
+        m.logn[i] = b->tiers[order[i]].logn;
+      }
+      m.n_tiers = (int)order.size();
+      m.counters = b->d_counters;
+      m.slots = b->d_slots;
+      BTRY(b, cdd::launch_multi(m, b->t1_single, b->taper != CDD_TAPER_NONE, b->multi_grid, stream));
+      return CDD_OK;
+    }
+    for (size_t i = 0; i < args.size(); ++i) {
+      args[i].persistent = form == kFormTiers ? 1 : 0;
+      BTRY(b, cdd::launch_batch(b->tiers[i].logn, args[i], stream));
+    }
+    return CDD_OK;
+  };
+  if (b->form_req == kFormMulti && !b->multi_ok) return CDD_EUNSUPPORTED;
+  if (b->form < 0) {
+    const int key_form = b->form_req >= 0 ? b->form_req : cached_form(b);
+    if (key_form >= 0) {
+      b->form = key_form;
+    } else {
+      cudaEvent_t ev[2];
+      BTRY(b, cudaEventCreate(&ev[0]));
+      BTRY(b, cudaEventCreate(&ev[1]));
+      int best = -1;
+      float best_ms = 0;
+      // TIERS and MULTI give the same bits, so a stream's output does not
+      // depend on which one the timing picked; TIERS_NP rounds the N = 8192
+      // tier's first-pass twiddles differently and is only run on request
+      for (int f = 0; f < kForms; ++f) {
+        if (f == kFormTiersNP || (f == kFormMulti && !b->multi_ok)) continue;
+        BTRY(b, cudaEventRecord(ev[0], stream));
+        if ((rc = run(f))) return rc;
+        BTRY(b, cudaEventRecord(ev[1], stream));
+        BTRY(b, cudaEventSynchronize(ev[1]));
+        float ms = 0;
+        BTRY(b, cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        b->tune_ns[f] = llround((double)ms * 1e6);
+        if (best < 0 || ms < best_ms) {
+          best = f;
+          best_ms = ms;
+        }
+      }
+      cudaEventDestroy(ev[0]);
+      cudaEventDestroy(ev[1]);
+      b->form = best;
+      remember_form(b, best);
+      b->parity ^= 1;
+      b->blocks += 1;
+      b->last_launches = 1 + launches_of(b, best);
+      return CDD_OK;
+    }
+  }
+  if ((rc = run(b->form))) return rc;
   b->parity ^= 1;
   b->blocks += 1;
-  b->last_launches = 1 + (int)b->tiers.size();
+  b->last_launches = 1 + launches_of(b, b->form);
   return CDD_OK;
 }
 

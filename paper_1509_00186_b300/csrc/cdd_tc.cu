@@ -15,10 +15,11 @@
 //
 // One CTA per SM runs two independent pipelines of 256 threads.  Per segment
 // and pipeline, six passes: the threads write a pass's operands into shared
-// memory, one thread issues the products and commits them to the pipeline's
-// mbarrier, every thread waits on it (bounded: after one second the kernel
-// records an error and stops), reads its rows of the result from tensor
-// memory and writes the next pass's operands.  The two pipelines interleave,
+// memory, one thread issues the products in two halves of the tiles, each
+// committed to one of the pipeline's two mbarriers; every thread waits on the
+// one that covers its rows (bounded: after one second the kernel records an
+// error and stops), reads them from tensor memory and writes the next pass's
+// operands, so the first half's rows are read while the second half runs.  The two pipelines interleave,
 // so one computes on the CUDA cores while the other's products run.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -253,17 +254,18 @@ __device__ __forceinline__ void row16(uint32_t trow, int e0, float2 (&v)[16]) {
   }
 }
 
-// The products of one pass: for each tile of 128 rows and each k-step of 16
-// values, A_hi * [B_hi | B_lo] (N = 4R; N = 2R without the split) and, with
-// `lo`, A_lo * B_hi into the first 2R columns.  The first half of the tiles
-// is committed to mbarrier bar0, the second half to bar1, so the rows of the
-// first half can be read while the second half's products run.
+// The products of half h of one pass: for each of its tiles of 128 rows and
+// each k-step of 16 values, A_hi * [B_hi | B_lo] (N = 4R; N = 2R without
+// the split) and, with `lo`, A_lo * B_hi into the first 2R columns; then a
+// commit to the half's mbarrier, so the rows of the first half can be read
+// while the second half runs.
 template <int R, bool BF, bool SPLIT>
-__device__ __forceinline__ void issue_pass(uint32_t tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b, Lay L,
-                                           int tiles, bool lo, uint32_t bar0, uint32_t bar1) {
+__device__ __forceinline__ void issue_half(uint32_t tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b, Lay L,
+                                           int tiles, bool lo, int h, uint32_t bar) {
   constexpr int CW = tile_cols(R, SPLIT);
   const uint32_t id_hi = idesc_f16(128, CW, BF), id_lo = idesc_f16(128, 2 * R, BF);
-  for (int tt = 0; tt < tiles; ++tt) {
+  const int half = tiles / 2;
+  for (int tt = h * half; tt < (h + 1) * half; ++tt) {
 #pragma unroll
     for (int s = 0; s < 2 * R / 16; ++s) {
       const uint64_t bd = smem_desc(b + s * b_ks(R), kLboB, kSboB);
@@ -271,9 +273,8 @@ __device__ __forceinline__ void issue_pass(uint32_t tmem, uint32_t a_hi, uint32_
       mma_f16(tmem + tt * CW, smem_desc(a_hi + aoff, L.lbo, L.sbo), bd, id_hi, s > 0);
       if (SPLIT && lo) mma_f16(tmem + tt * CW, smem_desc(a_lo + aoff, L.lbo, L.sbo), bd, id_lo, 1u);
     }
-    if (tt == tiles / 2 - 1) mma_commit(bar0);
   }
-  mma_commit(bar1);
+  mma_commit(bar);
 }
 
 __device__ __forceinline__ int tc_work_chan(const OlsArgs& a, int w) { return w / a.s_count; }
@@ -347,9 +348,10 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
     fence_async_shared();
     tc_fence_before();
     if (bar_or(barid, kT, abort)) return false;
-    if (lt == 0) {
-      tc_fence_after();
-      issue();
+    if (lt == 0) {                       // one thread issues both halves, each with its commit
+      tc_fence_after();                  // (a second issuing warp measured slower: it stalls its
+      issue(0);                          // own share of the CUDA-core work)
+      issue(1);
     }
     return true;
   };
@@ -409,7 +411,7 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
       }
     }
     // ---- forward pass 0 (radix 32 over stride 256); the int8 input is exact: no lo product
-    if (!pass([&] { issue_pass<32, BF, SPLIT>(tmem, a_hi, a_lo, b32, lay0(), 2, false, bar0, bar1); })) break;
+    if (!pass([&](int h) { issue_half<32, BF, SPLIT>(tmem, a_hi, a_lo, b32, lay0(), 2, false, h, h ? bar1 : bar0); })) break;
     wait_half(lt >> 7);
     {
       const uint32_t trow = tlane + (uint32_t)((lt >> 7) * CW32);
@@ -430,7 +432,7 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
       }
     }
     // ---- forward pass 1 (radix 16 over stride 16)
-    if (!pass([&] { issue_pass<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true, bar0, bar1); })) break;
+    if (!pass([&](int h) { issue_half<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true, h, h ? bar1 : bar0); })) break;
 #pragma unroll
     for (int gi = 0; gi < 2; ++gi) {
       const int g = lt + kT * gi;
@@ -450,7 +452,7 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
     // ---- forward pass 2 (radix 16, stride 1), then the chirp; the first
     // inverse pass works on the same groups, conjugated, so each thread
     // rewrites its own rows
-    if (!pass([&] { issue_pass<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true, bar0, bar1); })) break;
+    if (!pass([&](int h) { issue_half<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true, h, h ? bar1 : bar0); })) break;
     {
       const float4* ch4 = reinterpret_cast<const float4*>(a.chirp + (size_t)k * kN);
 #pragma unroll
@@ -478,7 +480,7 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
       }
     }
     // ---- inverse pass 2 (conjugated data)
-    if (!pass([&] { issue_pass<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true, bar0, bar1); })) break;
+    if (!pass([&](int h) { issue_half<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true, h, h ? bar1 : bar0); })) break;
 #pragma unroll
     for (int gi = 0; gi < 2; ++gi) {
       const int q = lt + kT * gi;
@@ -496,7 +498,7 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
       }
     }
     // ---- inverse pass 1
-    if (!pass([&] { issue_pass<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true, bar0, bar1); })) break;
+    if (!pass([&](int h) { issue_half<16, BF, SPLIT>(tmem, a_hi, a_lo, b16, lay12(), 4, true, h, h ? bar1 : bar0); })) break;
 #pragma unroll
     for (int gi = 0; gi < 2; ++gi) {
       const int g = lt + kT * gi;
@@ -514,7 +516,7 @@ __global__ void __launch_bounds__(TcCfg<PREC>::THREADS, 1) ols_tc_kernel(const O
       }
     }
     // ---- inverse pass 0 (radix 32): conj(y) / kOutScale at positions lt + 256 j
-    if (!pass([&] { issue_pass<32, BF, SPLIT>(tmem, a_hi, a_lo, b32, lay0(), 2, true, bar0, bar1); })) break;
+    if (!pass([&](int h) { issue_half<32, BF, SPLIT>(tmem, a_hi, a_lo, b32, lay0(), 2, true, h, h ? bar1 : bar0); })) break;
     float2 u[kR0];
     wait_half(lt >> 7);
     {

@@ -334,3 +334,21 @@ def test_batch_phase_table_form(cdd):
             assert cdd.cdd_batch_get(b, "phase_floats") == want
         finally:
             cdd.cdd_batch_destroy(b)
+
+
+def test_batch_form_attribute(cdd):
+    """CDD_ATTR_BATCH_FORM: -1 (tune at the first execute) by default; 0..2
+    settable before the first execute; anything else refused."""
+    b = cdd.cdd_batch_create(650.0, 0.78125, 8, [20.0, 30.0], [16384, 8192, 4096, 2048], 16)
+    try:
+        assert cdd.cdd_batch_get(b, "batch_form") == -1
+        for f in (0, 1, 2, -1):
+            cdd.cdd_batch_set(b, "batch_form", f)
+            assert cdd.cdd_batch_get(b, "batch_form") == f
+        for bad in (3, -2):
+            with pytest.raises(cdd.CddError) as ei:
+                cdd.cdd_batch_set(b, "batch_form", bad)
+            assert ei.value.code == cdd.CDD_EINVAL
+        assert cdd.cdd_batch_get(b, "tune_ns_multi") == 0
+    finally:
+        cdd.cdd_batch_destroy(b)

@@ -181,3 +181,60 @@ def test_batch_one_float_phase_table(small):
     from paper_1509_00186_b300.cdd import Batch
     with Batch(*SMALL, segments_per_block=1) as b:
         assert b.get("phase_floats") == 1
+
+
+# tiers of 16384 .. 2048 points (the upgraded-GMRT tiering) on a narrow band:
+# every launch form applies, the one-launch form included
+FORMS = (650.0, 0.78125, 8, [20.0, 30.0, 35.0, 40.0], (16384, 8192, 4096, 2048), 16)
+
+
+def run_form(vin, form, q, n_blocks):
+    import torch
+    from paper_1509_00186_b300.cdd import Batch
+    with Batch(*FORMS, segments_per_block=q, form=form) as b:
+        bs = b.block_samples
+        x = torch.from_numpy(np.ascontiguousarray(vin[: bs * n_blocks])).cuda()
+        outs = [b.execute(x[i * bs:(i + 1) * bs]) for i in range(n_blocks)]
+        torch.cuda.synchronize()
+        info = {k: b.get(k) for k in ("batch_form", "tune_ns_tiers", "tune_ns_tiers_np", "tune_ns_multi",
+                                      "kernel_launches")}
+        return torch.cat(outs, 2).cpu().numpy(), info
+
+
+def test_batch_launch_forms_are_bit_identical_and_match_the_oracle(cuda_device):
+    """Per-tier launches and the one-launch persistent form give the same
+    bits over two blocks; the per-tier form without the persistent N = 8192
+    kernel (first-pass twiddles formed as products) agrees within the
+    tolerance; all against the oracle."""
+    g = O.batch_geometry(*FORMS)
+    q = 2
+    vin = complex_int8_voltages(51, 2 * q * g.hop(0), 8, 20.0)
+    outs = {}
+    for form in ("tiers", "tiers_np", "multi"):
+        outs[form], info = run_form(vin, form, q, 2)
+        assert info["batch_form"] == {"tiers": 0, "tiers_np": 1, "multi": 2}[form]
+    assert np.array_equal(outs["tiers"], outs["multi"])
+    want = O.dedisperse_batch(vin[: 2 * q * g.hop(0)], g)
+    for d in range(4):
+        assert O.rel_rms(outs["multi"][d], want[d]) <= TOL, d
+        assert O.rel_rms(outs["tiers_np"][d], want[d]) <= TOL, d
+
+
+def test_batch_tuning_picks_a_form_and_remembers_it(cuda_device):
+    """With the form left to tuning, the first execute times the per-tier and
+    the one-launch forms (each time reported), keeps the faster, and gives the
+    same bits as a forced form; a second batch of the same shape reuses the
+    choice without timing."""
+    g = O.batch_geometry(*FORMS)
+    vin = complex_int8_voltages(52, 2 * g.hop(0), 8, 20.0)
+    forced, _ = run_form(vin, "tiers", 2, 1)
+    tuned, info = run_form(vin, "tune", 2, 1)
+    assert np.array_equal(tuned, forced)
+    assert info["batch_form"] in (0, 2)
+    times = {0: info["tune_ns_tiers"], 2: info["tune_ns_multi"]}
+    assert all(t > 0 for t in times.values()) and info["tune_ns_tiers_np"] == 0
+    assert times[info["batch_form"]] == min(times.values())
+    again, info2 = run_form(vin, "tune", 2, 1)
+    assert np.array_equal(again, forced)
+    assert info2["batch_form"] == info["batch_form"]
+    assert info2["tune_ns_tiers"] == info2["tune_ns_tiers_np"] == info2["tune_ns_multi"] == 0
