@@ -621,6 +621,12 @@ def row_plan_variant(args, dev, peaks, path, device_input=False):
     from synth import WORKLOADS, complex_int8_voltages
     from paper_1509_00186_b300.cdd import Plan
     w = WORKLOADS["precision" if path == "precision" else "gsb"]
+    if args.channels is not None and args.channels != w.n_chan:
+        # the lowest channels only (same channel width, so the same N, overlap and hop)
+        import dataclasses
+        f_lo0 = w.f_center_mhz - w.bandwidth_mhz / 2
+        cut = w.chan_bw_mhz * args.channels
+        w = dataclasses.replace(w, n_chan=args.channels, bandwidth_mhz=cut, f_center_mhz=f_lo0 + cut / 2)
     bw = -w.bandwidth_mhz if path == "lsb_hann" else w.bandwidth_mhz
     taper = "hann" if path == "lsb_hann" else "none"
     geo = O.plan_geometry(w.f_center_mhz, bw, w.n_chan, w.dm, w.n_fft, w.n_avg)
