@@ -289,6 +289,242 @@ outer_inv_kernel(float2* __restrict__ w, float* __restrict__ pw, long long n, in
   }
 }
 
+// ---- outer radix-64 passes, as 8 x 8 through shared memory ----------------
+// The same DIF (forward) and DIT (inverse) radix-64 butterflies as the
+// register passes above, one HBM round trip for six bits of the outer index
+// instead of four.  A CTA takes kTileCols neighbouring butterflies of one
+// stride-S block: rows base + S*j (j < 64) by columns t0 .. t0 + kTileCols - 1,
+// a lane two neighbouring columns, so every warp access is a 512-byte row
+// piece of 16-byte words.  With j = 8*j1 + j2 and k = k1 + 8*k2,
+//   X[k1 + 8 k2] = sum_j2 w_8^{j2 k2} w_64^{j2 k1} sum_j1 w_8^{j1 k1} v[8 j1 + j2]:
+// warp j2 does the inner radix-8 over j1 straight from global memory and
+// parks Y_j2[k1] (times w_64^{j2 k1}) in row 8*k1 + j2 of the tile; after the
+// barrier warp k1 reads rows 8*k1 .. 8*k1 + 7 and does the radix-8 over j2.
+// w_64^m = w_N^{m N/64} is one entry of the high table (N/64 is a multiple
+// of its 8192-entry step).
+constexpr int kTileCols = 64;
+constexpr int kTileThreads = 256;              // 8 warps: j2 (stage 1) or k1 (stage 2)
+
+__device__ __forceinline__ float2 w64(const float2* __restrict__ thi, long long n, int m) {
+  return __ldg(&thi[(long long)(m & 63) * (n >> 19)]);
+}
+__device__ __forceinline__ float4 pack2(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
+// The outer twiddles of a lane's two columns t and t + 1 for its rows
+// k = k1 + 8*k2 (k2 < 8), w_N^{e1 k} with e1 = t*step: w_N^{e1 k1} times the
+// powers of w_N^{8 e1}, and those of column t + 1 the same times w_N^{step k}
+// (entries that are the same across the warp).  A lane's column is
+// t = t0 + 2*lane (t0 the tile's first column), so w_N^{m t step} is the
+// warp's w_N^{m t0 step} times the lane-table entry w_N^{2 m lane step}
+// (kLaneRows rows of 32 lanes per pass, m = 1..7, 8, 16, 32; then the 64
+// factors w_N^{step k}): every table access is either one entry for the whole
+// warp or 32 neighbouring entries.
+constexpr int kLaneRows = 10;
+constexpr int kLaneTable = kLaneRows * 32 + 64;
+__host__ __device__ constexpr int lane_row_m(int r) { return r < 7 ? r + 1 : 8 << (r - 7); }
+
+struct Tw8x2 {
+  float2 u[8], v[8];
+  __device__ __forceinline__ Tw8x2(const float2* __restrict__ thi, const float2* __restrict__ tlo,
+                                   const float2* __restrict__ lanes, long long t0, long long step, int k1,
+                                   int lane) {
+    // w_N^{m t step} for the lane's t, from row r of the lane table
+    auto wt = [&](int r) {
+      return cmul(twiddle(thi, tlo, (long long)lane_row_m(r) * t0 * step), __ldg(&lanes[r * 32 + lane]));
+    };
+    float2 q[8];                                   // q[k2] = w_N^{8 e1 k2}
+    q[1] = wt(7);
+    q[2] = wt(8);
+    q[4] = wt(9);
+    q[3] = cmul(q[2], q[1]);
+    q[5] = cmul(q[4], q[1]);
+    q[6] = cmul(q[4], q[2]);
+    q[7] = cmul(q[4], q[3]);
+    const float2 a = k1 == 0 ? make_float2(1.f, 0.f) : wt(k1 - 1);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+      u[k2] = k2 == 0 ? a : cmul(a, q[k2]);
+      v[k2] = cmul(u[k2], __ldg(&lanes[kLaneRows * 32 + k1 + 8 * k2]));
+    }
+  }
+};
+
+// lanes[r * 32 + l] = w_N^{2 m_r l step}, lanes[kLaneRows * 32 + k] =
+// w_N^{step k} (FP64, rounded once)
+__global__ void fb_lane_table_kernel(float2* lanes, long long n, long long step) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kLaneTable) return;
+  const long long m = e < kLaneRows * 32 ? (long long)lane_row_m(e / 32) * 2 * (e % 32) * step
+                                         : (long long)(e - kLaneRows * 32) * step;
+  double sn, cs;
+  sincospi(2.0 * (double)(m % n) / (double)n, &sn, &cs);
+  lanes[e] = make_float2((float)cs, (float)(-sn));
+}
+
+template <bool FIRST>
+__global__ void __launch_bounds__(kTileThreads, 3)
+outer64_fwd_kernel(float2* __restrict__ w, const float* __restrict__ ts, long long n, int ls,
+                   const float2* __restrict__ thi, const float2* __restrict__ tlo,
+                   const float2* __restrict__ lanes) {
+  __shared__ float4 tile[64][kTileCols / 2];
+  const long long s = 1LL << ls;
+  const int c = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const long long b = (long long)blockIdx.x * kTileCols + 2 * c;    // butterflies b, b + 1
+  const long long t = b & (s - 1);
+  const long long base = ((b >> ls) << (ls + 6)) + t;
+  const int k1 = wp;
+  float2 twu[8], twv[8];
+  {
+    const int j2 = wp;
+    float2 u[8], v[8];
+#pragma unroll
+    for (int j1 = 0; j1 < 8; ++j1) {
+      const long long at = base + s * (8 * j1 + j2);
+      if constexpr (FIRST) {
+        const float2 r = __ldg(reinterpret_cast<const float2*>(ts + at));
+        u[j1] = make_float2(r.x, 0.f);
+        v[j1] = make_float2(r.y, 0.f);
+      } else {
+        const float4 r = *reinterpret_cast<const float4*>(w + at);
+        u[j1] = make_float2(r.x, r.y);
+        v[j1] = make_float2(r.z, r.w);
+      }
+    }
+    {
+      // the second stage's outer twiddles while the loads are in flight
+      // (w_M^{t k} = w_N^{t k N/M}; the tile's first column t0 = t - 2*lane)
+      const Tw8x2 tw(thi, tlo, lanes, t - 2 * c, n >> (ls + 6), k1, c);
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) {
+        twu[k2] = tw.u[k2];
+        twv[k2] = tw.v[k2];
+      }
+    }
+    dft<8, -1>(u);
+    dft<8, -1>(v);
+    tile[j2][c] = pack2(u[0], v[0]);
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) {
+      const float2 wk = w64(thi, n, j2 * k1);
+      tile[8 * k1 + j2][c] = pack2(cmul(u[k1], wk), cmul(v[k1], wk));
+    }
+  }
+  __syncthreads();
+  float2 u[8], v[8];
+#pragma unroll
+  for (int j2 = 0; j2 < 8; ++j2) {
+    const float4 r = tile[8 * k1 + j2][c];
+    u[j2] = make_float2(r.x, r.y);
+    v[j2] = make_float2(r.z, r.w);
+  }
+  dft<8, -1>(u);                               // u[k2] = X[k1 + 8 k2] of butterfly b
+  dft<8, -1>(v);                               // ... of butterfly b + 1
+#pragma unroll
+  for (int k2 = 0; k2 < 8; ++k2) {
+    u[k2] = cmul(u[k2], twu[k2]);
+    v[k2] = cmul(v[k2], twv[k2]);
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < 8; ++k2) *reinterpret_cast<float4*>(w + base + s * (k1 + 8 * k2)) = pack2(u[k2], v[k2]);
+}
+
+// Inverse: y[8 j1 + j2] = sum_k1 w_8^{-j1 k1} w_64^{-j2 k1} sum_k2 w_8^{-j2 k2} V[k1 + 8 k2],
+// V[k] = W[k] conj(w_N^{e1 k}).  LAST (stride N/64, consecutive butterflies
+// are consecutive samples): NA = 0 writes Re(y)^2 to pw; NA > 0 sums windows
+// of NA neighbouring columns of Re(y)^2 across lanes and writes those of the
+// kept part (window m starts at n_ov + m*NA) to out.
+template <bool LAST, int NA>
+__global__ void __launch_bounds__(kTileThreads, 3)
+outer64_inv_kernel(float2* __restrict__ w, float* __restrict__ pw, long long n, int ls,
+                   const float2* __restrict__ thi, const float2* __restrict__ tlo,
+                   const float2* __restrict__ lanes, float* __restrict__ out, long long n_ov) {
+  static_assert(NA == 0 || (LAST && NA <= 32 && (NA & (NA - 1)) == 0), "column windows");
+  __shared__ float4 tile[64][kTileCols / 2];
+  const long long s = 1LL << ls;
+  const int c = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const long long b = (long long)blockIdx.x * kTileCols + 2 * c;
+  const long long t = b & (s - 1);
+  const long long base = ((b >> ls) << (ls + 6)) + t;
+  {
+    const int k1 = wp;
+    float2 u[8], v[8];
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+      const float4 r = *reinterpret_cast<const float4*>(w + base + s * (k1 + 8 * k2));
+      u[k2] = make_float2(r.x, r.y);
+      v[k2] = make_float2(r.z, r.w);
+    }
+    {
+      const Tw8x2 tw(thi, tlo, lanes, t - 2 * c, n >> (ls + 6), k1, c);
+#pragma unroll
+      for (int k2 = 0; k2 < 8; ++k2) {
+        u[k2] = cmulc(u[k2], tw.u[k2]);
+        v[k2] = cmulc(v[k2], tw.v[k2]);
+      }
+    }
+    dft<8, 1>(u);                              // u[j2] = Z_k1[j2]
+    dft<8, 1>(v);
+    tile[k1][c] = pack2(u[0], v[0]);
+#pragma unroll
+    for (int j2 = 1; j2 < 8; ++j2) {
+      const float2 wk = w64(thi, n, j2 * k1);
+      tile[8 * j2 + k1][c] = pack2(cmulc(u[j2], wk), cmulc(v[j2], wk));
+    }
+  }
+  __syncthreads();
+  const int j2 = wp;
+  float2 u[8], v[8];
+#pragma unroll
+  for (int k1 = 0; k1 < 8; ++k1) {
+    const float4 r = tile[8 * j2 + k1][c];
+    u[k1] = make_float2(r.x, r.y);
+    v[k1] = make_float2(r.z, r.w);
+  }
+  dft<8, 1>(u);                                // u[j1] = y[8 j1 + j2] of butterfly b
+  dft<8, 1>(v);                                // ... of butterfly b + 1
+  if constexpr (!LAST) {
+#pragma unroll
+    for (int j1 = 0; j1 < 8; ++j1) *reinterpret_cast<float4*>(w + base + s * (8 * j1 + j2)) = pack2(u[j1], v[j1]);
+  } else if constexpr (NA == 0) {
+#pragma unroll
+    for (int j1 = 0; j1 < 8; ++j1)
+      *reinterpret_cast<float2*>(pw + base + s * (8 * j1 + j2)) = make_float2(u[j1].x * u[j1].x, v[j1].x * v[j1].x);
+  } else if constexpr (NA == 1) {
+#pragma unroll
+    for (int j1 = 0; j1 < 8; ++j1) {
+      const long long n0 = base + s * (8 * j1 + j2);
+      if (n0 >= n_ov) out[n0 - n_ov] = u[j1].x * u[j1].x;
+      if (n0 + 1 >= n_ov) out[n0 + 1 - n_ov] = v[j1].x * v[j1].x;
+    }
+  } else {
+    // a lane holds samples (2c, 2c + 1) of each row: windows of NA samples
+    // are NA/2 neighbouring lanes of pair sums
+    constexpr int NH = NA / 2;
+    float p[8];
+#pragma unroll
+    for (int j1 = 0; j1 < 8; ++j1) p[j1] = u[j1].x * u[j1].x + v[j1].x * v[j1].x;
+    const long long t0 = (long long)blockIdx.x * kTileCols;    // sample of column 0 in row 0
+    if constexpr (NH <= 8) {
+      lane_window_sums<8, NH>(p, c);
+      constexpr int V = 8 / NH;
+      const int lo = c & (NH - 1);
+#pragma unroll
+      for (int i = 0; i < V; ++i) {
+        const long long n0 = t0 + 2 * (c - lo) + s * (8 * (V * lo + i) + j2);
+        if (n0 >= n_ov) out[(n0 - n_ov) / NA] = p[i];
+      }
+    } else {
+      lane_window_sums<8, 8>(p, c);            // p[0]: 8 lanes of row 8*(c & 7) + j2
+#pragma unroll
+      for (int o = 8; o < NH; o <<= 1) p[0] += __shfl_xor_sync(0xffffffffu, p[0], o);
+      if ((c & (NH - 1)) < 8) {
+        const long long n0 = t0 + 2 * (c & ~(NH - 1)) + s * (8 * (c & 7) + j2);
+        if (n0 >= n_ov) out[(n0 - n_ov) / NA] = p[0];
+      }
+    }
+  }
+}
+
 // ---- middle: contiguous sub-transforms of 2^LOGS points in shared memory --
 // Sub-transform qq holds bins bin_out(qq) + L_out * (its own bins); chirp is the
 // per-bin table in the chirp pass's order.  ts != nullptr: the series is real
@@ -504,10 +740,32 @@ cudaError_t launch_middle(int logs, float2* w, const float* ts, float* pw, const
 
 cudaError_t launch_outer(bool forward, bool edge, int radix, float2* w, const float* ts, float* pw,
                          long long n, long long stride, const float2* thi, const float2* tlo,
-                         cudaStream_t s, float* out = nullptr, long long n_ov = 0, int na = 0) {
+                         const float2* lanes, cudaStream_t s, float* out = nullptr, long long n_ov = 0,
+                         int na = 0) {
   if (stride <= 0 || (stride & (stride - 1)) || n % (stride * radix)) return cudaErrorInvalidValue;
   int ls = 0;
   while ((1LL << ls) < stride) ++ls;
+  if (radix == 64) {                          // tiles of kTileCols butterflies
+    if (stride % kTileCols || n < (1LL << 19) || lanes == nullptr) return cudaErrorInvalidValue;
+    const long long tiles = n / 64 / kTileCols;
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const unsigned g = (unsigned)tiles;
+    if (forward && edge) outer64_fwd_kernel<true><<<g, kTileThreads, 0, s>>>(w, ts, n, ls, thi, tlo, lanes);
+    else if (forward) outer64_fwd_kernel<false><<<g, kTileThreads, 0, s>>>(w, ts, n, ls, thi, tlo, lanes);
+    else if (!edge)
+      outer64_inv_kernel<false, 0><<<g, kTileThreads, 0, s>>>(w, pw, n, ls, thi, tlo, lanes, nullptr, 0);
+    else {
+      switch (na) {
+#define CDD_OUTER64_NA(A) \
+        case A: outer64_inv_kernel<true, A><<<g, kTileThreads, 0, s>>>(w, pw, n, ls, thi, tlo, lanes, out, n_ov); break;
+        CDD_OUTER64_NA(0) CDD_OUTER64_NA(1) CDD_OUTER64_NA(2) CDD_OUTER64_NA(4) CDD_OUTER64_NA(8)
+        CDD_OUTER64_NA(16) CDD_OUTER64_NA(32)
+#undef CDD_OUTER64_NA
+        default: return cudaErrorInvalidValue;
+      }
+    }
+    return cudaGetLastError();
+  }
   const unsigned grid = grid_for(n / radix);
   if (!forward && edge && na > 0) {           // last pass with the integration fused
     if (radix != 16 || (n / radix) % 32) return cudaErrorInvalidValue;
@@ -577,6 +835,7 @@ struct cdd_fullband_s {
   int* d_radix = nullptr;
   long long* d_stride = nullptr;
   long long* d_rprod = nullptr;
+  float2* d_lanes = nullptr;                 // [outer passes][kLaneTable] lane tables of radix-64 passes
   int cur = 0;
   int64_t blocks = 0;
   size_t bytes_device = 0;
@@ -634,6 +893,7 @@ int fcommit_once(cdd_fullband f) {
   if ((rc = falloc(f, &f->d_radix, no * sizeof(int)))) return rc;
   if ((rc = falloc(f, &f->d_stride, no * sizeof(long long)))) return rc;
   if ((rc = falloc(f, &f->d_rprod, no * sizeof(long long)))) return rc;
+  if ((rc = falloc(f, &f->d_lanes, no * cdd::kLaneTable * sizeof(float2)))) return rc;
   if (!f->radix_out.empty()) {
     FTRY(f, cudaMemcpy(f->d_radix, f->radix_out.data(), no * sizeof(int), cudaMemcpyHostToDevice));
     FTRY(f, cudaMemcpy(f->d_stride, f->stride_out.data(), no * sizeof(long long), cudaMemcpyHostToDevice));
@@ -651,6 +911,14 @@ int fcommit_once(cdd_fullband f) {
     cdd::fb_twiddle_kernel<<<cdd::grid_for(n_hi + (1 << cdd::kTwLoBits)), 256, 0, s>>>(f->d_thi, f->d_tlo, n);
     e = cudaGetLastError();
   }
+  for (size_t p = 0; p < f->radix_out.size() && e == cudaSuccess; ++p)
+    if (f->radix_out[p] == 64) {
+      // the pass of stride S works on sub-problems of M = 64 S: step = N / M
+      const long long step = n / (64 * f->stride_out[p]);
+      cdd::fb_lane_table_kernel<<<(cdd::kLaneTable + 127) / 128, 128, 0, s>>>(
+          f->d_lanes + p * cdd::kLaneTable, n, step);
+      e = cudaGetLastError();
+    }
   if (e == cudaSuccess)
     e = cdd::launch_fb_chirp(f->logs, f->d_chirp, n, (int)f->radix_out.size(), f->d_radix, f->d_stride,
                              f->d_rprod, f->f_lo, f->fs, f->dm, f->sideband, s);
@@ -692,6 +960,7 @@ void ffree(cdd_fullband f) {
   cudaFree(f->d_radix);
   cudaFree(f->d_stride);
   cudaFree(f->d_rprod);
+  cudaFree(f->d_lanes);
 }
 
 long long next_pow2_above_ll(double x) {
@@ -754,10 +1023,10 @@ int cdd_fullband_create(cdd_fullband* out, double f_center_mhz, double bandwidth
     int logn = 0;
     while ((1LL << logn) < n_fft) ++logn;
     f->logs = logn < cdd::kMidLog ? logn : cdd::kMidLog;
-    int rest = logn - f->logs;               // outer passes: radix 16, then what remains
+    int rest = logn - f->logs;               // outer passes: radix 64, then 16, 8, 4 or 2
     long long stride = n_fft, rprod = 1;
     while (rest > 0) {
-      const int lr = rest >= 4 ? 4 : rest;
+      const int lr = rest >= 6 ? 6 : rest >= 4 ? 4 : rest;
       stride >>= lr;
       f->radix_out.push_back(1 << lr);
       f->stride_out.push_back(stride);
@@ -829,14 +1098,15 @@ int cdd_fullband_execute(cdd_fullband f, const int8_t* d_in, float* d_out, cudaS
     } else {
       for (int p = 0; p < no; ++p)
         FTRY(f, cdd::launch_outer(true, p == 0, f->radix_out[p], f->d_w, seg, nullptr, n,
-                                  f->stride_out[p], f->d_thi, f->d_tlo, s));
+                                  f->stride_out[p], f->d_thi, f->d_tlo, f->d_lanes + p * cdd::kLaneTable, s));
       FTRY(f, cdd::launch_middle(f->logs, f->d_w, nullptr, nullptr, f->d_chirp, f->d_tw, n_sub, s));
       // the last pass also integrates across lanes when its radix is 16 and
-      // n_avg <= 16; otherwise it writes Re(y)^2 for the integration kernel
-      const bool fused = f->radix_out[0] == 16 && f->n_avg <= 16;
+      // n_avg <= 16, or 64 and n_avg <= 32; otherwise it writes Re(y)^2 for
+      // the integration kernel
+      const bool fused = (f->radix_out[0] == 16 && f->n_avg <= 16) || (f->radix_out[0] == 64 && f->n_avg <= 32);
       for (int p = no - 1; p >= 0; --p)
         FTRY(f, cdd::launch_outer(false, p == 0, f->radix_out[p], f->d_w, nullptr, f->d_pw, n,
-                                  f->stride_out[p], f->d_thi, f->d_tlo, s,
+                                  f->stride_out[p], f->d_thi, f->d_tlo, f->d_lanes + p * cdd::kLaneTable, s,
                                   d_out + (long long)sg * (h / f->n_avg), nov, fused ? f->n_avg : 0));
       launches += 2 * no + 1;
       if (fused) continue;
