@@ -804,13 +804,27 @@ def row_fullband(args, dev, peaks):
     f.close()
     ms = total / args.steps
     logn = int(math.log2(n))
-    outer = max(0, -(-(logn - 14) // 4))
+    # the library's outer radices: 64 while six or more bits remain, then 16, 8, 4 or 2
+    radices, rest = [], max(0, logn - 14)
+    while rest > 0:
+        lr = 6 if rest >= 6 else 4 if rest >= 4 else rest
+        radices.append(1 << lr)
+        rest -= lr
+    outer = len(radices)
+    # per pass: the edge passes 12 bytes per point (real series in, or Re(y)^2 out),
+    # the inner ones 16, the middle 24 (the transform both ways and the chirp)
     pass_bytes = (24 * n + 2 * (12 * n + 16 * n * (outer - 1))) if outer else 16 * n
-    nbytes = pass_bytes + 9.25 * h + 8 * nov
+    extra = 9.25 * h + 8 * nov                     # inverse channelisation and the carried overlap
+    nbytes = pass_bytes + extra
+    # the method's minimum: one outer pass each way around the middle (three round trips)
+    min_bytes = (24 * n + 2 * 12 * n if outer else 16 * n) + extra
     value = h / (ms * 1e-3) / 1e6
-    roof = _hbm_roofline(f"whole step ({outer} radix-16 HBM passes each way around 16384-point "
-                         "shared-memory sub-transforms)", nbytes, ms, peaks)
+    roof = _hbm_roofline(f"whole step ({outer} outer HBM passes each way, radix "
+                         f"{'x'.join(map(str, radices)) or '-'}, around 16384-point shared-memory "
+                         "sub-transforms)", nbytes, ms, peaks)
     roof["flops_per_launch"] = 10.0 * n * logn + 9.0 * n
+    roof["min_bytes_per_launch"] = min_bytes
+    roof["frac_of_min_bytes"] = min_bytes / (ms * 1e-3) / 1e9 / roof["peak"]
     cpu = None
     if not args.no_cpu_baseline:
         geo = O.fullband_geometry(*a)
