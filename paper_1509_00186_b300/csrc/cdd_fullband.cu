@@ -362,7 +362,7 @@ __global__ void fb_lane_table_kernel(float2* lanes, long long n, long long step)
 }
 
 template <bool FIRST>
-__global__ void __launch_bounds__(kTileThreads, 3)
+__global__ void __launch_bounds__(kTileThreads, 4)
 outer64_fwd_kernel(float2* __restrict__ w, const float* __restrict__ ts, long long n, int ls,
                    const float2* __restrict__ thi, const float2* __restrict__ tlo,
                    const float2* __restrict__ lanes) {
@@ -434,7 +434,7 @@ outer64_fwd_kernel(float2* __restrict__ w, const float* __restrict__ ts, long lo
 // of NA neighbouring columns of Re(y)^2 across lanes and writes those of the
 // kept part (window m starts at n_ov + m*NA) to out.
 template <bool LAST, int NA>
-__global__ void __launch_bounds__(kTileThreads, 3)
+__global__ void __launch_bounds__(kTileThreads, 4)
 outer64_inv_kernel(float2* __restrict__ w, float* __restrict__ pw, long long n, int ls,
                    const float2* __restrict__ thi, const float2* __restrict__ tlo,
                    const float2* __restrict__ lanes, float* __restrict__ out, long long n_ov) {
