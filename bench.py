@@ -804,12 +804,14 @@ def row_fullband(args, dev, peaks):
     f.close()
     ms = total / args.steps
     logn = int(math.log2(n))
-    # the library's outer radices: 64 while six or more bits remain, then 16, 8, 4 or 2
-    radices, rest = [], max(0, logn - 14)
-    while rest > 0:
-        lr = 6 if rest >= 6 else 4 if rest >= 4 else rest
-        radices.append(1 << lr)
-        rest -= lr
+    # the library's pass plan: 16384-point middle transforms up to N = 2^19 with
+    # one register pass for the rest; from 2^20 on 8192-point ones, the outer
+    # bits as radix-64/128 tiles (and a register pass for what is left)
+    logs = min(logn, 14) if logn < 20 else 13
+    rest = logn - logs
+    plan = {7: [7], 8: [6, 2], 9: [6, 3], 10: [6, 4], 11: [7, 4], 12: [6, 6], 13: [6, 7], 14: [7, 7]}
+    lrs = plan.get(rest, [4, rest - 4] if rest == 5 else [rest] if rest > 0 else [])
+    radices = [1 << lr for lr in lrs]
     outer = len(radices)
     # per pass: the edge passes 12 bytes per point (real series in, or Re(y)^2 out),
     # the inner ones 16, the middle 24 (the transform both ways and the chirp)
@@ -820,7 +822,7 @@ def row_fullband(args, dev, peaks):
     min_bytes = (24 * n + 2 * 12 * n if outer else 16 * n) + extra
     value = h / (ms * 1e-3) / 1e6
     roof = _hbm_roofline(f"whole step ({outer} outer HBM passes each way, radix "
-                         f"{'x'.join(map(str, radices)) or '-'}, around 16384-point shared-memory "
+                         f"{'x'.join(map(str, radices)) or '-'}, around {1 << logs}-point shared-memory "
                          "sub-transforms)", nbytes, ms, peaks)
     roof["flops_per_launch"] = 10.0 * n * logn + 9.0 * n
     roof["min_bytes_per_launch"] = min_bytes

@@ -30,7 +30,8 @@ namespace {
 
 using namespace passes;
 
-constexpr int kMidLog = 14;                 // L_mid for N > 16384
+constexpr int kMidLog = 14;                 // L_mid for 16384 < N < 2^kTileMinLog
+constexpr int kTileMinLog = 20;             // from here on L_mid = 8192 with tile passes around it
 constexpr int kTwLoBits = 13;               // two-level twiddle table split
 
 // w_N^e = hi[e >> 13] * lo[e & 8191]
@@ -320,8 +321,12 @@ __device__ __forceinline__ float4 pack2(float2 a, float2 b) { return make_float4
 // factors w_N^{step k}): every table access is either one entry for the whole
 // warp or 32 neighbouring entries.
 constexpr int kLaneRows = 10;
-constexpr int kLaneTable = kLaneRows * 32 + 64;
 __host__ __device__ constexpr int lane_row_m(int r) { return r < 7 ? r + 1 : 8 << (r - 7); }
+// The radix-128 passes (one column per lane, t = t0 + lane) use rows
+// w_N^{m lane step} for m = 1..15, 16, 32, 64.
+constexpr int kLaneRows128 = 18;
+__host__ __device__ constexpr int lane_row_m128(int r) { return r < 15 ? r + 1 : 16 << (r - 15); }
+constexpr int kLaneTable = kLaneRows * 32 + 64 > kLaneRows128 * 32 ? kLaneRows * 32 + 64 : kLaneRows128 * 32;
 
 struct Tw8x2 {
   float2 u[8], v[8];
@@ -349,13 +354,20 @@ struct Tw8x2 {
   }
 };
 
-// lanes[r * 32 + l] = w_N^{2 m_r l step}, lanes[kLaneRows * 32 + k] =
-// w_N^{step k} (FP64, rounded once)
-__global__ void fb_lane_table_kernel(float2* lanes, long long n, long long step) {
+// Radix 64: lanes[r * 32 + l] = w_N^{2 m_r l step}, lanes[kLaneRows * 32 + k]
+// = w_N^{step k}.  Radix 128: lanes[r * 32 + l] = w_N^{m_r l step}.  FP64,
+// rounded once.
+__global__ void fb_lane_table_kernel(float2* lanes, long long n, long long step, int radix) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= kLaneTable) return;
-  const long long m = e < kLaneRows * 32 ? (long long)lane_row_m(e / 32) * 2 * (e % 32) * step
-                                         : (long long)(e - kLaneRows * 32) * step;
+  long long m;
+  if (radix == 128) {
+    if (e >= kLaneRows128 * 32) return;
+    m = (long long)lane_row_m128(e / 32) * (e % 32) * step;
+  } else {
+    if (e >= kLaneRows * 32 + 64) return;
+    m = e < kLaneRows * 32 ? (long long)lane_row_m(e / 32) * 2 * (e % 32) * step
+                           : (long long)(e - kLaneRows * 32) * step;
+  }
   double sn, cs;
   sincospi(2.0 * (double)(m % n) / (double)n, &sn, &cs);
   lanes[e] = make_float2((float)cs, (float)(-sn));
@@ -520,6 +532,150 @@ outer64_inv_kernel(float2* __restrict__ w, float* __restrict__ pw, long long n, 
       if ((c & (NH - 1)) < 8) {
         const long long n0 = t0 + 2 * (c & ~(NH - 1)) + s * (8 * (c & 7) + j2);
         if (n0 >= n_ov) out[(n0 - n_ov) / NA] = p[0];
+      }
+    }
+  }
+}
+
+// ---- outer radix-128 passes, as 16 x 8 through shared memory --------------
+// As the radix-64 tiles, with j = 8*j1 + j2 (j1 < 16) and k = k1 + 16*k2:
+//   X[k1 + 16 k2] = sum_j2 w_8^{j2 k2} w_128^{j2 k1} sum_j1 w_16^{j1 k1} v[8 j1 + j2].
+// A CTA takes 32 neighbouring butterflies, one column per lane (256-byte row
+// pieces): warp j2 does the radix-16 over j1, and each warp then does the
+// radix-8 over j2 for k1 = warp and warp + 8.  The tile is 128 rows of 32.
+// w_128^m = w_N^{m N/128} is one entry of the high table (N >= 2^20).
+constexpr int kTile128Cols = 32;
+
+__device__ __forceinline__ float2 w128(const float2* __restrict__ thi, long long n, int m) {
+  return __ldg(&thi[(long long)(m & 127) * (n >> 20)]);
+}
+
+// w_N^{e1 k} for a lane's column t = t0 + lane (e1 = t*step) and rows
+// k = k1 + 16*k2, k2 < 8: w_N^{e1 k1} times the powers of w_N^{16 e1}, each
+// w_N^{m t step} being the warp's w_N^{m t0 step} times the lane-table entry
+struct Tw16x8 {
+  float2 u[8];
+  __device__ __forceinline__ Tw16x8(const float2* __restrict__ thi, const float2* __restrict__ tlo,
+                                    const float2* __restrict__ lanes, long long t0, long long step, int k1,
+                                    int lane) {
+    auto wt = [&](int r) {
+      return cmul(twiddle(thi, tlo, (long long)lane_row_m128(r) * t0 * step), __ldg(&lanes[r * 32 + lane]));
+    };
+    float2 q[8];                                   // q[k2] = w_N^{16 e1 k2}
+    q[1] = wt(15);
+    q[2] = wt(16);
+    q[4] = wt(17);
+    q[3] = cmul(q[2], q[1]);
+    q[5] = cmul(q[4], q[1]);
+    q[6] = cmul(q[4], q[2]);
+    q[7] = cmul(q[4], q[3]);
+    const float2 a = k1 == 0 ? make_float2(1.f, 0.f) : wt(k1 - 1);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) u[k2] = k2 == 0 ? a : cmul(a, q[k2]);
+  }
+};
+
+template <bool FIRST>
+__global__ void __launch_bounds__(kTileThreads, 3)
+outer128_fwd_kernel(float2* __restrict__ w, const float* __restrict__ ts, long long n, int ls,
+                    const float2* __restrict__ thi, const float2* __restrict__ tlo,
+                    const float2* __restrict__ lanes) {
+  __shared__ float2 tile[128][kTile128Cols];
+  const long long s = 1LL << ls;
+  const int c = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const long long b = (long long)blockIdx.x * kTile128Cols + c;
+  const long long t = b & (s - 1);
+  const long long base = ((b >> ls) << (ls + 7)) + t;
+  {
+    const int j2 = wp;
+    float2 v[16];
+#pragma unroll
+    for (int j1 = 0; j1 < 16; ++j1) {
+      const long long at = base + s * (8 * j1 + j2);
+      v[j1] = FIRST ? make_float2(__ldg(&ts[at]), 0.f) : w[at];
+    }
+    dft<16, -1>(v);
+    tile[j2][c] = v[0];
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) tile[8 * k1 + j2][c] = cmul(v[k1], w128(thi, n, j2 * k1));
+  }
+  __syncthreads();
+  const long long step = n >> (ls + 7);        // w_M^{t k} = w_N^{t k N/M}
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    const int k1 = wp + 8 * h;
+    float2 v[8];
+#pragma unroll
+    for (int j2 = 0; j2 < 8; ++j2) v[j2] = tile[8 * k1 + j2][c];
+    dft<8, -1>(v);                             // v[k2] = X[k1 + 16 k2]
+    const Tw16x8 tw(thi, tlo, lanes, t - c, step, k1, c);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) w[base + s * (k1 + 16 * k2)] = cmul(v[k2], tw.u[k2]);
+  }
+}
+
+// Inverse: y[8 j1 + j2] = sum_k1 w_16^{-j1 k1} w_128^{-j2 k1} sum_k2 w_8^{-j2 k2} V[k1 + 16 k2],
+// V[k] = W[k] conj(w_N^{e1 k}); LAST and NA as for the radix-64 tiles.
+template <bool LAST, int NA>
+__global__ void __launch_bounds__(kTileThreads, 3)
+outer128_inv_kernel(float2* __restrict__ w, float* __restrict__ pw, long long n, int ls,
+                    const float2* __restrict__ thi, const float2* __restrict__ tlo,
+                    const float2* __restrict__ lanes, float* __restrict__ out, long long n_ov) {
+  static_assert(NA == 0 || (LAST && NA <= 32 && (NA & (NA - 1)) == 0), "column windows");
+  __shared__ float2 tile[128][kTile128Cols];
+  const long long s = 1LL << ls;
+  const int c = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const long long b = (long long)blockIdx.x * kTile128Cols + c;
+  const long long t = b & (s - 1);
+  const long long base = ((b >> ls) << (ls + 7)) + t;
+  const long long step = n >> (ls + 7);
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) {
+    const int k1 = wp + 8 * h;
+    float2 v[8];
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) v[k2] = w[base + s * (k1 + 16 * k2)];
+    const Tw16x8 tw(thi, tlo, lanes, t - c, step, k1, c);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) v[k2] = cmulc(v[k2], tw.u[k2]);
+    dft<8, 1>(v);                              // v[j2] = Z_k1[j2]
+    tile[8 * k1][c] = v[0];
+#pragma unroll
+    for (int j2 = 1; j2 < 8; ++j2) tile[8 * k1 + j2][c] = cmulc(v[j2], w128(thi, n, j2 * k1));
+  }
+  __syncthreads();
+  const int j2 = wp;
+  float2 v[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) v[k1] = tile[8 * k1 + j2][c];
+  dft<16, 1>(v);                               // v[j1] = y[8 j1 + j2]
+  if constexpr (!LAST) {
+#pragma unroll
+    for (int j1 = 0; j1 < 16; ++j1) w[base + s * (8 * j1 + j2)] = v[j1];
+  } else if constexpr (NA == 0) {
+#pragma unroll
+    for (int j1 = 0; j1 < 16; ++j1) pw[base + s * (8 * j1 + j2)] = v[j1].x * v[j1].x;
+  } else {
+    // windows of NA neighbouring columns are NA neighbouring lanes
+    float u[16];
+#pragma unroll
+    for (int j1 = 0; j1 < 16; ++j1) u[j1] = v[j1].x * v[j1].x;
+    const long long t0 = (long long)blockIdx.x * kTile128Cols;   // sample of column 0 in row 0
+    if constexpr (NA <= 16) {
+      lane_window_sums<16, NA>(u, c);
+      constexpr int V = 16 / NA;
+      const int lo = c & (NA - 1);
+#pragma unroll
+      for (int i = 0; i < V; ++i) {
+        const long long n0 = t0 + (c - lo) + s * (8 * (V * lo + i) + j2);
+        if (n0 >= n_ov) out[(n0 - n_ov) / NA] = u[i];
+      }
+    } else {
+      lane_window_sums<16, 16>(u, c);          // u[0]: 16 lanes of row 8*(c & 15) + j2
+      u[0] += __shfl_xor_sync(0xffffffffu, u[0], 16);
+      if (c < 16) {
+        const long long n0 = t0 + s * (8 * c + j2);
+        if (n0 >= n_ov) out[(n0 - n_ov) / NA] = u[0];
       }
     }
   }
@@ -745,6 +901,27 @@ cudaError_t launch_outer(bool forward, bool edge, int radix, float2* w, const fl
   if (stride <= 0 || (stride & (stride - 1)) || n % (stride * radix)) return cudaErrorInvalidValue;
   int ls = 0;
   while ((1LL << ls) < stride) ++ls;
+  if (radix == 128) {                         // tiles of kTile128Cols butterflies
+    if (stride % kTile128Cols || n < (1LL << 20) || lanes == nullptr) return cudaErrorInvalidValue;
+    const long long tiles = n / 128 / kTile128Cols;
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const unsigned g = (unsigned)tiles;
+    if (forward && edge) outer128_fwd_kernel<true><<<g, kTileThreads, 0, s>>>(w, ts, n, ls, thi, tlo, lanes);
+    else if (forward) outer128_fwd_kernel<false><<<g, kTileThreads, 0, s>>>(w, ts, n, ls, thi, tlo, lanes);
+    else if (!edge)
+      outer128_inv_kernel<false, 0><<<g, kTileThreads, 0, s>>>(w, pw, n, ls, thi, tlo, lanes, nullptr, 0);
+    else {
+      switch (na) {
+#define CDD_OUTER128_NA(A) \
+        case A: outer128_inv_kernel<true, A><<<g, kTileThreads, 0, s>>>(w, pw, n, ls, thi, tlo, lanes, out, n_ov); break;
+        CDD_OUTER128_NA(0) CDD_OUTER128_NA(1) CDD_OUTER128_NA(2) CDD_OUTER128_NA(4) CDD_OUTER128_NA(8)
+        CDD_OUTER128_NA(16) CDD_OUTER128_NA(32)
+#undef CDD_OUTER128_NA
+        default: return cudaErrorInvalidValue;
+      }
+    }
+    return cudaGetLastError();
+  }
   if (radix == 64) {                          // tiles of kTileCols butterflies
     if (stride % kTileCols || n < (1LL << 19) || lanes == nullptr) return cudaErrorInvalidValue;
     const long long tiles = n / 64 / kTileCols;
@@ -835,7 +1012,7 @@ struct cdd_fullband_s {
   int* d_radix = nullptr;
   long long* d_stride = nullptr;
   long long* d_rprod = nullptr;
-  float2* d_lanes = nullptr;                 // [outer passes][kLaneTable] lane tables of radix-64 passes
+  float2* d_lanes = nullptr;                 // [outer passes][kLaneTable] lane tables of the tile passes
   int cur = 0;
   int64_t blocks = 0;
   size_t bytes_device = 0;
@@ -912,11 +1089,11 @@ int fcommit_once(cdd_fullband f) {
     e = cudaGetLastError();
   }
   for (size_t p = 0; p < f->radix_out.size() && e == cudaSuccess; ++p)
-    if (f->radix_out[p] == 64) {
-      // the pass of stride S works on sub-problems of M = 64 S: step = N / M
-      const long long step = n / (64 * f->stride_out[p]);
+    if (f->radix_out[p] >= 64) {
+      // the pass of stride S works on sub-problems of M = R S: step = N / M
+      const long long step = n / (f->radix_out[p] * f->stride_out[p]);
       cdd::fb_lane_table_kernel<<<(cdd::kLaneTable + 127) / 128, 128, 0, s>>>(
-          f->d_lanes + p * cdd::kLaneTable, n, step);
+          f->d_lanes + p * cdd::kLaneTable, n, step, f->radix_out[p]);
       e = cudaGetLastError();
     }
   if (e == cudaSuccess)
@@ -1022,11 +1199,18 @@ int cdd_fullband_create(cdd_fullband* out, double f_center_mhz, double bandwidth
     f->hop = n_fft - f->n_ov;
     int logn = 0;
     while ((1LL << logn) < n_fft) ++logn;
-    f->logs = logn < cdd::kMidLog ? logn : cdd::kMidLog;
-    int rest = logn - f->logs;               // outer passes: radix 64, then 16, 8, 4 or 2
+    // L_mid = 2^14 up to N = 2^19 (at most one outer pass); from N = 2^20 on,
+    // 8192-point middle transforms (several CTAs per SM) and the outer bits
+    // as radix-64 and -128 tile passes where they fit, pass 0 first:
+    // 7: 128; 8: 64 4; 9: 64 8; 10: 64 16; 11: 128 16; 12: 64 64; 13: 64 128; 14: 128 128
+    f->logs = logn < cdd::kMidLog ? logn : logn < cdd::kTileMinLog ? cdd::kMidLog : cdd::kMidLog - 1;
+    int rest = logn - f->logs;
+    static const int kPlan[8][2] = {{7, 0}, {6, 2}, {6, 3}, {6, 4}, {7, 4}, {6, 6}, {6, 7}, {7, 7}};
+    const int* plan = rest >= 7 && rest <= 14 ? kPlan[rest - 7] : nullptr;
+    int ip = 0;
     long long stride = n_fft, rprod = 1;
     while (rest > 0) {
-      const int lr = rest >= 6 ? 6 : rest >= 4 ? 4 : rest;
+      const int lr = plan ? plan[ip++] : rest >= 6 ? 6 : rest >= 4 ? 4 : rest;
       stride >>= lr;
       f->radix_out.push_back(1 << lr);
       f->stride_out.push_back(stride);
@@ -1101,9 +1285,9 @@ int cdd_fullband_execute(cdd_fullband f, const int8_t* d_in, float* d_out, cudaS
                                   f->stride_out[p], f->d_thi, f->d_tlo, f->d_lanes + p * cdd::kLaneTable, s));
       FTRY(f, cdd::launch_middle(f->logs, f->d_w, nullptr, nullptr, f->d_chirp, f->d_tw, n_sub, s));
       // the last pass also integrates across lanes when its radix is 16 and
-      // n_avg <= 16, or 64 and n_avg <= 32; otherwise it writes Re(y)^2 for
+      // n_avg <= 16, or 64 or 128 and n_avg <= 32; otherwise it writes Re(y)^2 for
       // the integration kernel
-      const bool fused = (f->radix_out[0] == 16 && f->n_avg <= 16) || (f->radix_out[0] == 64 && f->n_avg <= 32);
+      const bool fused = (f->radix_out[0] == 16 && f->n_avg <= 16) || (f->radix_out[0] >= 64 && f->n_avg <= 32);
       for (int p = no - 1; p >= 0; --p)
         FTRY(f, cdd::launch_outer(false, p == 0, f->radix_out[p], f->d_w, nullptr, f->d_pw, n,
                                   f->stride_out[p], f->d_thi, f->d_tlo, f->d_lanes + p * cdd::kLaneTable, s,

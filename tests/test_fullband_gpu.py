@@ -24,17 +24,20 @@ def run_fullband(vin, args, q, n_blocks):
 
 @pytest.mark.parametrize("args", [
     (610.0, 1.0, 32, 20.0, 0, 4),            # N = 2^14: the shared-memory transform only
-    (325.0, 2.0, 64, 5.0, 1 << 20, 8),       # N = 2^20: one radix-64 tile pass, lanes sum 8 samples
-    (325.0, 2.0, 64, 5.0, 1 << 20, 1),       # N = 2^20: radix 64, n_avg 1
+    (325.0, 2.0, 64, 5.0, 1 << 20, 8),       # N = 2^20: 8192-point middle, one radix-128 tile pass, lanes sum 8
+    (325.0, 2.0, 64, 5.0, 1 << 20, 1),       # N = 2^20: radix 128, n_avg 1
+    (325.0, 2.0, 64, 5.0, 1 << 20, 32),      # N = 2^20: radix 128, 32-sample windows over two lane groups
+    (325.0, 2.0, 64, 5.0, 1 << 20, 64),      # N = 2^20: radix 128, n_avg 64 > 32 keeps the integration kernel
     (325.0, 2.0, 64, 5.0, 1 << 15, 8),       # N = 2^15: one radix-2 outer pass, integration kernel
     (325.0, 2.0, 64, 5.0, 1 << 18, 1),       # N = 2^18: one radix-16 pass, integrated across lanes (n_avg 1)
-    (325.0, 4.0, 128, 40.0, 0, 16),          # N = 2^20: radix 64, 16-sample windows over two lane groups
-    (325.0, 8.0, 256, 30.0, 0, 32),          # N = 2^21: radix 64 then 2, 32-sample windows across lanes
-    (325.0, 2.0, 64, 5.0, 1 << 21, 64),      # N = 2^21: n_avg 64 > 32 keeps the integration kernel
-    (325.0, 2.0, 64, 5.0, 1 << 24, 4),       # N = 2^24: radix 64 then 16
+    (325.0, 4.0, 128, 40.0, 0, 16),          # N = 2^20: radix 128, 16-sample windows across lanes
+    (325.0, 8.0, 256, 30.0, 0, 32),          # N = 2^21: radix 64 then 4, 32-sample windows across lanes
+    (325.0, 2.0, 64, 5.0, 1 << 21, 64),      # N = 2^21: radix 64, n_avg 64 > 32 keeps the integration kernel
+    (325.0, 2.0, 64, 5.0, 1 << 24, 4),       # N = 2^24: radix 128 then 16
+    pytest.param((325.0, 2.0, 64, 5.0, 1 << 25, 16), marks=pytest.mark.slow),   # N = 2^25: radix 64 then 64
     (610.0, -1.0, 32, 20.0, 0, 4),           # lower sideband, the shared-memory transform only
     (325.0, -2.0, 64, 5.0, 1 << 18, 1),      # lower sideband through the outer passes
-    (325.0, -2.0, 64, 5.0, 1 << 20, 2),      # lower sideband through a radix-64 pass
+    (325.0, -2.0, 64, 5.0, 1 << 20, 2),      # lower sideband through a radix-128 pass
     (610.0, 1.0, 32, 0.0, 1 << 14, 4),       # DM 0: no overlap, the correction is 1
     (325.0, 2.0, 64, 0.0, 1 << 18, 1),       # DM 0 through the outer passes
 ])
@@ -61,8 +64,8 @@ def test_fullband_block_split_is_bit_identical(cuda_device):
 @pytest.mark.slow
 def test_fullband_gsb_32mhz_mode(cuda_device):
     """The paper's 32 MHz mode at 325 MHz with DM 50: N = 2^26 over the whole
-    band (two radix-64 passes through HBM around 16384-point sub-transforms);
-    two segments against the oracle."""
+    band (a radix-64 and a radix-128 pass through HBM each way around
+    8192-point sub-transforms); two segments against the oracle."""
     args = (325.0, 32.0, 512, 50.0, 0, 16)
     g = O.fullband_geometry(*args)
     assert g.n_fft == 2 ** 26
