@@ -73,3 +73,18 @@ def test_fullband_gsb_32mhz_mode(cuda_device):
     want = O.dedisperse_fullband(vin, g)
     got = run_fullband(vin, args, 1, 2)
     assert O.rel_rms(got, want) <= TOL
+
+
+@pytest.mark.slow
+def test_fullband_largest_transform(cuda_device):
+    """N = 2^27, the largest transform the full-band mode takes: two radix-128
+    tile passes each way around 8192-point sub-transforms; one segment against
+    the oracle."""
+    args = (325.0, 2.0, 64, 5.0, 1 << 27, 16)
+    g = O.fullband_geometry(*args)
+    assert g.n_fft == 2 ** 27
+    vin = complex_int8_voltages(14, g.hop // g.frame, 64, 20.0)
+    want = O.dedisperse_fullband(vin, g)
+    got = run_fullband(vin, args, 1, 1)
+    assert got.shape == want.shape
+    assert O.rel_rms(got, want) <= TOL
