@@ -105,11 +105,12 @@ enum cdd_attr {
                                       table is single floats (no chirp phase
                                       above 16 turns), else 2 (two floats)     */
   CDD_ATTR_PRECISION = 23,         /* enum cdd_precision, settable (see below) */
-  CDD_ATTR_DEVICE_ERRORS = 24,     /* tensor-core forms: nonzero once a kernel
-                                      gave up waiting for its tensor-core
-                                      products (it then stopped early and its
-                                      outputs are invalid); reading waits for
-                                      the device                               */
+  CDD_ATTR_DEVICE_ERRORS = 24,     /* nonzero once a kernel gave up a bounded
+                                      wait (it then stopped early and the
+                                      block's outputs are invalid): bit 1 a
+                                      tensor-core form's products, bit 2 the
+                                      corner turn's tile copies; reading waits
+                                      for the device                           */
   CDD_ATTR_HOST_STAGING_BYTES = 25,/* device bytes the host-buffer path adds
                                       (two chunks in, two out)                 */
   CDD_ATTR_BATCH_FORM = 26,        /* batch only, settable: the launch form
@@ -119,7 +120,14 @@ enum cdd_attr {
                                       the first execute's tuning, ns (0: not
                                       run)                                     */
   CDD_ATTR_TUNE_NS_TIERS_NP = 28,
-  CDD_ATTR_TUNE_NS_MULTI = 29
+  CDD_ATTR_TUNE_NS_MULTI = 29,
+  CDD_ATTR_TURN_TMA = 30           /* plan only, settable 0 (default) or 1: the
+                                      corner turn as tensor-memory-accelerator
+                                      tile copies (2-D tensor loads and stores,
+                                      transposed in shared memory) where the
+                                      layout allows it (n_chan a multiple of 8,
+                                      16-byte aligned input); the same bits as
+                                      the default turn                         */
 };
 
 /* Launch forms of a batch; they differ in how the (tier, channel, segment)

@@ -14,7 +14,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libcdd.so")
-SOURCES = ["cdd_api.cu", "cdd_kernels.cu", "cdd_tc.cu", "cdd_static.cu", "cdd_batch.cu", "cdd_pool.cu",
+SOURCES = ["cdd_api.cu", "cdd_kernels.cu", "cdd_tc.cu", "cdd_tma.cu", "cdd_static.cu", "cdd_batch.cu", "cdd_pool.cu",
            "cdd_fullband.cu"]
 HEADERS = ["cdd_fft.cuh", "cdd_passes.cuh", "cdd_internal.h", "cdd_tc_layout.h", os.path.join("..", "..", "include", "cdd.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

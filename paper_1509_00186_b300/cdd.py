@@ -32,7 +32,7 @@ ATTR = {
     "seq_gaps": 15, "polarisations": 16, "stage_timing": 17, "timed_blocks": 18,
     "corner_turn_ns": 19, "ols_ns": 20, "phase_floats": 22, "precision": 23,
     "device_errors": 24, "host_staging_bytes": 25, "batch_form": 26, "tune_ns_tiers": 27,
-    "tune_ns_tiers_np": 28, "tune_ns_multi": 29,
+    "tune_ns_tiers_np": 28, "tune_ns_multi": 29, "turn_tma": 30,
 }
 BATCH_FORM = {"tune": -1, "tiers": 0, "tiers_np": 1, "multi": 2}
 POOL_ATTR = {"budget": 100, "used_bytes": 101, "streams": 102, "queued": 103}
@@ -540,10 +540,12 @@ class Plan:
 
     def __init__(self, f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft=0, n_avg=1,
                  segments_per_block=1, taper="none", pipeline_chunks=None, polarisations=1,
-                 stage_timing=False, precision="fp32"):
+                 stage_timing=False, precision="fp32", turn_tma=False):
         self.handle = cdd_plan_create(f_center_mhz, bandwidth_mhz, n_chan, dm, n_fft, n_avg)
         try:
             cdd_plan_set(self.handle, "segments_per_block", segments_per_block)
+            if turn_tma:
+                cdd_plan_set(self.handle, "turn_tma", 1)
             cdd_plan_set(self.handle, "taper", TAPER[taper])
             if precision != "fp32":
                 cdd_plan_set(self.handle, "precision", PRECISION[precision])

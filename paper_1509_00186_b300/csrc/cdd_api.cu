@@ -44,7 +44,8 @@ struct cdd_plan_s {
   char2* d_tail[2] = {nullptr, nullptr};
   float* d_ring = nullptr;
   int* d_shift = nullptr;
-  int* d_err = nullptr;      // tensor-core forms: the kernels' wait-timeout flag
+  int* d_err = nullptr;      // the kernels' wait-timeout flags (1 tensor-core products, 2 tile copies)
+  bool turn_tma = false;     // corner turn by tensor tile copies (CDD_ATTR_TURN_TMA)
   void* d_dft = nullptr;     // tensor-core forms: the DFT matrices
   char2* d_in_cm = nullptr;  // channel-major copy of the block (corner-turn path)
   long long ring_len = 0;
@@ -183,7 +184,8 @@ int64_t bytes_needed(const cdd_plan p) {
   b += C * (p->r_max + n_out_per_block(p)) * (int64_t)sizeof(float);
   b += C * (int64_t)sizeof(int);
   b += C * p->q * p->hop * (int64_t)sizeof(char2);
-  if (p->precision != CDD_PRECISION_FP32) b += (int64_t)sizeof(int) + (int64_t)cdd::tc_dft_bytes();
+  b += (int64_t)sizeof(int);
+  if (p->precision != CDD_PRECISION_FP32) b += (int64_t)cdd::tc_dft_bytes();
   if (p->pols == 2) {
     if (p->n_ov > 0) b += 2 * C * p->n_ov * (int64_t)sizeof(char2);
     b += C * (p->r_max + n_out_per_block(p)) * (int64_t)sizeof(float);
@@ -293,10 +295,10 @@ int commit_once(cdd_plan p) {
   if ((rc = dalloc(p, &p->d_shift, (size_t)p->n_chan * sizeof(int)))) return rc;
   // channel-major copy of a block: the fused kernel then reads each segment contiguously
   if ((rc = dalloc(p, &p->d_in_cm, (size_t)p->n_chan * p->q * p->hop * sizeof(char2)))) return rc;
+  if ((rc = dalloc(p, &p->d_err, sizeof(int)))) return rc;
+  CDD_TRY(p, cudaMemset(p->d_err, 0, sizeof(int)));
   const bool tc = p->precision != CDD_PRECISION_FP32;
   if (tc) {
-    if ((rc = dalloc(p, &p->d_err, sizeof(int)))) return rc;
-    CDD_TRY(p, cudaMemset(p->d_err, 0, sizeof(int)));
     if ((rc = dalloc(p, &p->d_dft, cdd::tc_dft_bytes()))) return rc;
   }
   if (p->pols == 2) {
@@ -406,7 +408,8 @@ int run_block(cdd_plan p, const int8_t* d_in, float* d_out, float* d_volt, int q
     p->t_pending[slot] = 1;
     CDD_TRY(p, cudaEventRecord(te[0], s));
   }
-  CDD_TRY(p, cdd::launch_corner_turn(a.in, p->d_in_cm, 0, a.rows, a.rows, p->n_chan, s));
+  CDD_TRY(p, cdd::launch_corner_turn(a.in, p->d_in_cm, 0, a.rows, a.rows, p->n_chan, s,
+                                     p->turn_tma ? p->d_err : nullptr));
   if (te) CDD_TRY(p, cudaEventRecord(te[1], s));
   a.s_begin = 0;
   a.s_count = q;
@@ -525,6 +528,10 @@ int cdd_plan_set(cdd_plan p, int attr, int64_t value) {
       if (value != 0 && value != 1) return CDD_EINVAL;
       p->timing = value == 1;
       return CDD_OK;
+    case CDD_ATTR_TURN_TMA:
+      if (value != 0 && value != 1) return CDD_EINVAL;
+      p->turn_tma = value == 1;
+      return CDD_OK;
     case CDD_ATTR_PRECISION:
       if (value < CDD_PRECISION_FP32 || value > CDD_PRECISION_BF16) return CDD_EINVAL;
       if (value != CDD_PRECISION_FP32 && !cdd::tc_supported(p->logn, (int)value)) return CDD_EUNSUPPORTED;
@@ -557,6 +564,7 @@ int cdd_plan_get(cdd_plan p, int attr, int64_t* v) {
     case CDD_ATTR_POLARISATIONS: *v = p->pols; break;
     case CDD_ATTR_STAGE_TIMING: *v = p->timing ? 1 : 0; break;
     case CDD_ATTR_PRECISION: *v = p->precision; break;
+    case CDD_ATTR_TURN_TMA: *v = p->turn_tma ? 1 : 0; break;
     case CDD_ATTR_DEVICE_ERRORS: {
       int e = 0;
       if (p->d_err) {

@@ -51,9 +51,16 @@ int64_t shift_of(const Geometry& g, int k);
 cudaError_t launch_ols(int logn, const OlsArgs& a, cudaStream_t s);
 
 // out[k*stride + row] = in[row][k] for rows [r_begin, r_end): channel-major copy
-// of (part of) a block of int8 pairs.
+// of (part of) a block of int8 pairs.  With err (a device int) the turn goes
+// through tensor-memory-accelerator tile copies where the layout allows them
+// (corner_turn_tma_ok); a copy wait that runs out sets bit 2 of *err.
 cudaError_t launch_corner_turn(const char2* in, char2* out, long long r_begin, long long r_end,
-                               long long stride, int n_chan, cudaStream_t s);
+                               long long stride, int n_chan, cudaStream_t s, int* err = nullptr);
+bool corner_turn_tma_ok(const char2* in, const char2* out, long long r_begin, long long r_end, long long stride,
+                        int n_chan);
+// cudaErrorNotSupported (and nothing launched) where corner_turn_tma_ok fails.
+cudaError_t launch_corner_turn_tma(const char2* in, char2* out, long long r_begin, long long r_end, long long stride,
+                                   int n_chan, int* err, cudaStream_t s);
 
 // Build the chirp table (FP64 phase, reduced mod 1 turn, then rounded to
 // float): chirp[k][idx] = exp(-i Phi_k(f_l)) * w(f_l) * scale in the layout

@@ -837,9 +837,16 @@ cudaError_t launch_shift_table(int* shift, int n_chan, double f_base_mhz, double
   return cudaGetLastError();
 }
 
+#ifndef CDD_TMA_TURN
+#define CDD_TMA_TURN 1
+#endif
 cudaError_t launch_corner_turn(const char2* in, char2* out, long long r_begin, long long r_end,
-                               long long stride, int n_chan, cudaStream_t s) {
+                               long long stride, int n_chan, cudaStream_t s, int* err) {
   if (r_end <= r_begin) return cudaSuccess;
+  if (CDD_TMA_TURN && err) {
+    const cudaError_t e = launch_corner_turn_tma(in, out, r_begin, r_end, stride, n_chan, err, s);
+    if (e != cudaErrorNotSupported) return e;
+  }
   const dim3 grid((unsigned)((r_end - r_begin + kTT - 1) / kTT), (unsigned)((n_chan + kTT - 1) / kTT));
   corner_turn_kernel<<<grid, 256, 0, s>>>(in, out, r_begin, r_end, stride, n_chan);
   return cudaGetLastError();

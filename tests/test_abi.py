@@ -134,6 +134,14 @@ def test_setters(cdd):
             cdd.cdd_plan_set(p, "precision", 9)
         assert ei.value.code == cdd.CDD_EINVAL
         assert cdd.cdd_plan_get(p, "precision") == cdd.PRECISION["fp32"]
+        # the corner turn's form: 0 (default) or 1 (tensor tile copies)
+        assert cdd.cdd_plan_get(p, "turn_tma") == 0
+        cdd.cdd_plan_set(p, "turn_tma", 1)
+        assert cdd.cdd_plan_get(p, "turn_tma") == 1
+        with pytest.raises(cdd.CddError) as ei:
+            cdd.cdd_plan_set(p, "turn_tma", 2)
+        assert ei.value.code == cdd.CDD_EINVAL
+        cdd.cdd_plan_set(p, "turn_tma", 0)
         # nothing allocated yet: no error flag to read
         assert cdd.cdd_plan_get(p, "device_errors") == 0
     finally:

@@ -426,3 +426,32 @@ def test_integration_lengths_n8192(cuda_device, n_avg):
     split, _ = gpu_run(vin, args, 3, 2, volt=False)
     assert np.array_equal(split, whole)
     assert np.all(rel_rms_rows(whole, out_o) <= TOL)
+
+
+@pytest.mark.parametrize("args, q", [
+    ((325.0, 4.0, 64, 10.0, 1024, 8), 5),       # 64 channels: whole tiles across, rows ragged
+    ((325.0, 4.5, 72, 10.0, 1024, 8), 3),       # 72 channels: a ragged last channel tile
+    ((325.0, 32.0, 512, 50.0, 8192, 16), 2),    # the 512-channel block shape
+    ((325.0, 2.3125, 37, 10.0, 512, 4), 4),     # 37 channels: not a multiple of 8, the default turn
+    ((150.0, 4.0, 64, 100.0, 65536, 16), 1),    # the channel-major copy of a cluster shape
+])
+def test_tma_corner_turn_same_bits(cuda_device, args, q):
+    """The corner turn as tensor tile copies (CDD_ATTR_TURN_TMA) gives the
+    same outputs, bit for bit, as the default turn, and within the bound of
+    the oracle; it reports no device error."""
+    import torch
+    from paper_1509_00186_b300.cdd import Plan
+    outs = []
+    for tma in (False, True):
+        with Plan(*args, segments_per_block=q, turn_tma=tma) as plan:
+            bs, n_out, C = plan.block_samples, plan.n_out, plan.n_chan
+            vin = complex_int8_voltages(31, bs * 2, C, 20.0)
+            x = torch.from_numpy(np.ascontiguousarray(vin)).cuda()
+            o = [plan.execute(x[b * bs:(b + 1) * bs]) for b in range(2)]
+            torch.cuda.synchronize()
+            assert plan.get("device_errors") == 0
+            assert plan.get("turn_tma") == int(tma)
+            outs.append(torch.cat(o, 1).cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+    want, _ = oracle_run(vin, args, bs * 2, channels=range(min(8, C)))
+    assert rel_rms_rows(outs[1][:min(8, C)], want[:min(8, C)]).max() <= TOL
