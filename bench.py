@@ -581,7 +581,7 @@ def _compact(line):
     r = line.get("roofline")
     if r:
         out["roofline"] = {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel", "kernel_ms",
-                                              "fp32_equivalent") if k in r}
+                                              "fp32_equivalent", "frac_of_min_bytes") if k in r}
     return out
 
 
