@@ -576,7 +576,7 @@ struct Tw16x8 {
 };
 
 template <bool FIRST>
-__global__ void __launch_bounds__(kTileThreads, 3)
+__global__ void __launch_bounds__(kTileThreads, 4)
 outer128_fwd_kernel(float2* __restrict__ w, const float* __restrict__ ts, long long n, int ls,
                     const float2* __restrict__ thi, const float2* __restrict__ tlo,
                     const float2* __restrict__ lanes) {
@@ -617,7 +617,7 @@ outer128_fwd_kernel(float2* __restrict__ w, const float* __restrict__ ts, long l
 // Inverse: y[8 j1 + j2] = sum_k1 w_16^{-j1 k1} w_128^{-j2 k1} sum_k2 w_8^{-j2 k2} V[k1 + 16 k2],
 // V[k] = W[k] conj(w_N^{e1 k}); LAST and NA as for the radix-64 tiles.
 template <bool LAST, int NA>
-__global__ void __launch_bounds__(kTileThreads, 3)
+__global__ void __launch_bounds__(kTileThreads, 4)
 outer128_inv_kernel(float2* __restrict__ w, float* __restrict__ pw, long long n, int ls,
                     const float2* __restrict__ thi, const float2* __restrict__ tlo,
                     const float2* __restrict__ lanes, float* __restrict__ out, long long n_ov) {
