@@ -530,6 +530,16 @@ const char* cdd_strerror(int code);
 /* Library version as major*10000 + minor*100 + patch. */
 int cdd_version(void);
 
+/* Self-test of the kernels' bounded waits on the current device.  It runs
+ * the tensor-copy corner turn on one 64 x 64 tile whose mbarrier expects more
+ * bytes than the copy brings, so the wait can never be met.  The kernel must
+ * give up after its limit (20 ms here, 1 s in normal launches), set its error
+ * flag and return.  *status receives that flag (2 when the wait ran out as it
+ * should).  Returns CDD_OK when the kernel returned and the device still
+ * answered afterwards; CDD_EUNSUPPORTED without tensor maps; CDD_ENOMEM or
+ * CDD_ECUDA otherwise.  Allocates and frees 16 KB; synchronises the device. */
+int cdd_selftest_wait_limit(int* status);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,7 +55,7 @@ EXPORTS = ("cdd_plan_create", "cdd_plan_set", "cdd_plan_get", "cdd_plan_shifts",
            "cdd_batch_state_bytes", "cdd_batch_export_state", "cdd_batch_import_state",
            "cdd_execute_host_async", "cdd_plan_prepare_host", "cdd_pool_clock_ms", "cdd_pool_admit_ex",
            "cdd_pool_request", "cdd_pool_request_status", "cdd_pool_submit_at", "cdd_pool_submit_host",
-           "cdd_pool_submit_many", "cdd_pool_stream_resync")
+           "cdd_pool_submit_many", "cdd_pool_stream_resync", "cdd_selftest_wait_limit")
 
 
 class CddError(RuntimeError):
@@ -142,6 +142,7 @@ def _load() -> ctypes.CDLL:
     lib.cdd_strerror.argtypes = [ctypes.c_int]
     lib.cdd_strerror.restype = ctypes.c_char_p
     lib.cdd_version.argtypes = []
+    lib.cdd_selftest_wait_limit.argtypes = [ctypes.POINTER(ctypes.c_int)]
     for name in EXPORTS:
         if name not in ("cdd_strerror", "cdd_pool_clock_ms"):
             getattr(lib, name).restype = ctypes.c_int
@@ -165,6 +166,13 @@ def strerror(code: int) -> str:
 
 def cdd_version() -> int:
     return int(_lib.cdd_version())
+
+
+def cdd_selftest_wait_limit() -> int:
+    """Run the bounded-wait self-test; returns the kernel's error flag (2 expected)."""
+    st = ctypes.c_int(0)
+    _check(_lib.cdd_selftest_wait_limit(ctypes.byref(st)), "cdd_selftest_wait_limit")
+    return int(st.value)
 
 
 def cdd_plan_create(f_center_mhz: float, bandwidth_mhz: float, n_chan: int, dm: float,

@@ -21,6 +21,7 @@
 
 #include <mutex>
 
+#include "../../include/cdd.h"
 #include "cdd_internal.h"
 
 namespace cdd {
@@ -60,8 +61,8 @@ __device__ __forceinline__ void mbar_expect(uint32_t bar, uint32_t bytes) {
                : "memory");
 }
 
-// Wait for phase `parity` of an mbarrier for at most kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait for phase `parity` of an mbarrier for at most limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
   const uint64_t t0 = global_ns();
   for (;;) {
     uint32_t ok;
@@ -73,7 +74,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (global_ns() - t0 > kWaitLimitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 
@@ -99,7 +100,8 @@ __device__ __forceinline__ uint32_t swz(int r, int e) {
 
 __global__ void __launch_bounds__(kThreads)
 corner_turn_tma_kernel(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout,
-                       int r_begin, int tiles_r, int tiles_c, int* err) {
+                       int r_begin, int tiles_r, int tiles_c, int* err, uint32_t expect_extra,
+                       uint64_t limit_ns) {
   __shared__ TurnSmem sm;
   const int tid = threadIdx.x;
   const long long n_tiles = (long long)tiles_r * tiles_c;
@@ -117,7 +119,7 @@ corner_turn_tma_kernel(const __grid_constant__ CUtensorMap tin, const __grid_con
     for (int s = 0; s < kStages; ++s) {
       const long long i = blockIdx.x + s * step;
       if (i < n_tiles) {
-        mbar_expect(smem_u32(&sm.bar[s]), kTileBytes);
+        mbar_expect(smem_u32(&sm.bar[s]), kTileBytes + expect_extra);
         tma_load(&tin, smem_u32(sm.in[s]), smem_u32(&sm.bar[s]), tile_x(i), tile_y(i));
         issued[s] += 1;
       }
@@ -129,7 +131,7 @@ corner_turn_tma_kernel(const __grid_constant__ CUtensorMap tin, const __grid_con
   for (; blockIdx.x + j * step < n_tiles; ++j) {
     const long long i = blockIdx.x + j * step;
     const int s = (int)(j % kStages);
-    const bool ok = mbar_wait(smem_u32(&sm.bar[s]), (uint32_t)((j / kStages) & 1));
+    const bool ok = mbar_wait(smem_u32(&sm.bar[s]), (uint32_t)((j / kStages) & 1), limit_ns);
     // every thread knows the load landed, and thread 0's wait on the store
     // that last read out[j & 1] is done
     if (__syncthreads_or(!ok)) {
@@ -165,7 +167,7 @@ corner_turn_tma_kernel(const __grid_constant__ CUtensorMap tin, const __grid_con
       asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
       const long long i2 = i + kStages * step;
       if (i2 < n_tiles) {
-        mbar_expect(smem_u32(&sm.bar[s]), kTileBytes);
+        mbar_expect(smem_u32(&sm.bar[s]), kTileBytes + expect_extra);
         tma_load(&tin, smem_u32(sm.in[s]), smem_u32(&sm.bar[s]), tile_x(i2), tile_y(i2));
         issued[s] += 1;
       }
@@ -178,7 +180,7 @@ corner_turn_tma_kernel(const __grid_constant__ CUtensorMap tin, const __grid_con
       // slot s among tiles < j) completions waited; wait (bounded) for the rest
       for (int s = 0; s < kStages; ++s) {
         const int done = (int)((j + kStages - 1 - s) / kStages);   // tiles j' < j with j' mod kStages == s
-        for (int p = done; p < issued[s]; ++p) mbar_wait(smem_u32(&sm.bar[s]), (uint32_t)(p & 1));
+        for (int p = done; p < issued[s]; ++p) mbar_wait(smem_u32(&sm.bar[s]), (uint32_t)(p & 1), limit_ns);
       }
     }
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
@@ -243,8 +245,46 @@ cudaError_t launch_corner_turn_tma(const char2* in, char2* out, long long r_begi
   if (e != cudaSuccess) return e;
   const long long cap = (long long)CDD_TMA_CTAS_PER_SM * sms;
   const unsigned grid = (unsigned)(n_tiles < cap ? n_tiles : cap);
-  corner_turn_tma_kernel<<<grid, kThreads, 0, s>>>(tin, tout, (int)r_begin, (int)tiles_r, (int)tiles_c, err);
+  corner_turn_tma_kernel<<<grid, kThreads, 0, s>>>(tin, tout, (int)r_begin, (int)tiles_r, (int)tiles_c, err, 0u,
+                                                    kWaitLimitNs);
   return cudaGetLastError();
 }
 
 }  // namespace cdd
+
+// Self-test of the bounded waits: one tile whose mbarrier expects 16 bytes
+// more than the copy delivers, so its phase never completes and the wait
+// runs out after 20 ms.  The kernel must set bit 2 of its flag, give up its
+// bounded cleanup wait, and return with the device still usable.
+extern "C" int cdd_selftest_wait_limit(int* status) {
+  if (!status) return CDD_EINVAL;
+  *status = 0;
+  using namespace cdd;
+  char2* d_in = nullptr;
+  char2* d_out = nullptr;
+  int* d_err = nullptr;
+  int rc = CDD_OK;
+  cudaError_t e = cudaMalloc((void**)&d_in, kTileBytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d_out, kTileBytes);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(d_in, 0, kTileBytes);
+  if (e == cudaSuccess) e = cudaMemset(d_err, 0, sizeof(int));
+  CUtensorMap tin, tout;
+  if (e == cudaSuccess && (!encode_2d(&tin, d_in, kTT, kTT, kTT) || !encode_2d(&tout, d_out, kTT, kTT, kTT)))
+    rc = CDD_EUNSUPPORTED;
+  if (e == cudaSuccess && rc == CDD_OK) {
+    corner_turn_tma_kernel<<<1, kThreads>>>(tin, tout, 0, 1, 1, d_err, 16u, 20000000ull);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(status, d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    // the context still answers
+    if (e == cudaSuccess) e = cudaMemset(d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  if (e == cudaErrorMemoryAllocation) rc = CDD_ENOMEM;
+  else if (e != cudaSuccess) rc = CDD_ECUDA;
+  cudaFree(d_in);
+  cudaFree(d_out);
+  cudaFree(d_err);
+  return rc;
+}
