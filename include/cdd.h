@@ -54,7 +54,7 @@ extern "C" {
 #define CDD_EINVAL       -1   /* bad argument or geometry                     */
 #define CDD_ENOMEM       -2   /* device or pinned-host allocation failed      */
 #define CDD_ECUDA        -3   /* a CUDA call failed (sticky)                  */
-#define CDD_EUNSUPPORTED -4   /* valid request this build does not run       */
+#define CDD_EUNSUPPORTED -4   /* valid request this library does not run     */
 #define CDD_ESTATE       -5   /* call not allowed in the plan's current state */
 #define CDD_ETOOBIG      -6   /* request needs more than the fixed scratch of
                                  cdd_execute_static                          */
@@ -183,14 +183,14 @@ typedef struct cdd_plan_s* cdd_plan;
  *     chirp is conjugated on mirrored bins, and shifts are taken against the
  *     band's lowest channel.
  *   n_chan > 0: channels.  dm >= 0: dispersion measure in pc cm^-3 (Eq. 3).
- *   n_fft: FFT length N (power of two, 64..65536 in this build; above 16384
+ *   n_fft: FFT length N (power of two, 64..65536 in this library; above 16384
  *     a segment runs on a cluster of N/8192 CTAs and n_avg must be at most
  *     8192*8192/N), or 0 for the
  *     Sec. 2.3 rule: the smallest power of two > 2*n_d (raised so that
  *     N > n_ov, N >= 2*n_avg and N >= 64).
  *   n_avg > 0: detected samples summed per output; h must be a multiple of it.
  * Touches no GPU.  Returns CDD_EINVAL for an impossible geometry,
- * CDD_EUNSUPPORTED for an N this build does not run. */
+ * CDD_EUNSUPPORTED for an N this library does not run. */
 int cdd_plan_create(cdd_plan* plan, double f_center_mhz, double bandwidth_mhz,
                     int n_chan, double dm, int n_fft, int n_avg);
 

@@ -472,7 +472,7 @@ const char* cdd_strerror(int code) {
     case CDD_EINVAL: return "invalid argument or geometry";
     case CDD_ENOMEM: return "out of device or host memory";
     case CDD_ECUDA: return "CUDA error (sticky for this plan)";
-    case CDD_EUNSUPPORTED: return "not supported by this build";
+    case CDD_EUNSUPPORTED: return "not supported by this library";
     case CDD_ESTATE: return "not allowed in the plan's current state";
     case CDD_ETOOBIG: return "request exceeds the fixed scratch of cdd_execute_static";
     case CDD_EBUSY: return "admission refused: HBM budget or stream slots exhausted";

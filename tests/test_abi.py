@@ -103,7 +103,7 @@ def test_invalid_geometry_is_rejected(cdd):
             cdd.cdd_plan_create(*args)
         assert ei.value.code == cdd.CDD_EINVAL, args
     with pytest.raises(cdd.CddError) as ei:
-        cdd.cdd_plan_create(150.0, 32.0, 512, 100.0, 131072, 16)    # valid, not in this build
+        cdd.cdd_plan_create(150.0, 32.0, 512, 100.0, 131072, 16)    # valid, not in this library
     assert ei.value.code == cdd.CDD_EUNSUPPORTED
     with pytest.raises(cdd.CddError) as ei:                         # window spans two CTAs
         cdd.cdd_plan_create(150.0, 32.0, 512, 100.0, 65536, 2048)
@@ -276,7 +276,7 @@ def test_fullband_rejects_bad_requests(cdd):
                  (325.0, 0.0, 512, 50.0, 0, 16)]:          # no bandwidth
         with pytest.raises(cdd.CddError):
             cdd.cdd_fullband_create(*args)
-    with pytest.raises(cdd.CddError) as ei:                 # N = 2^28: beyond this build
+    with pytest.raises(cdd.CddError) as ei:                 # N = 2^28: beyond this library
         cdd.cdd_fullband_create(325.0, 32.0, 512, 200.0, 0, 16)
     assert ei.value.code == cdd.CDD_EUNSUPPORTED
 
