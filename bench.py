@@ -801,17 +801,16 @@ def row_fullband(args, dev, peaks):
     out = torch.empty((f.n_out,), dtype=torch.float32, device=dev)
     total, steps_ms, clocks = _timed(lambda: f.execute(x, out), args.steps, args.warmup, dev)
     launches = f.get("kernel_launches")
+    pp = f.get("pass_plan")
     f.close()
     ms = total / args.steps
     logn = int(math.log2(n))
-    # the library's pass plan: 16384-point middle transforms up to N = 2^19 with
-    # one register pass for the rest; from 2^20 on 8192-point ones, the outer
-    # bits as radix-64/128 tiles (and a register pass for what is left)
-    logs = min(logn, 14) if logn < 20 else 13
-    rest = logn - logs
-    plan = {7: [7], 8: [6, 2], 9: [6, 3], 10: [6, 4], 11: [7, 4], 12: [6, 6], 13: [6, 7], 14: [7, 7]}
-    lrs = plan.get(rest, [4, rest - 4] if rest == 5 else [rest] if rest > 0 else [])
-    radices = [1 << lr for lr in lrs]
+    # the library's pass plan: the shared-memory transform and the outer radices
+    logs = pp & 0xFF
+    radices, sh = [], 8
+    while (pp >> sh) & 0xF:
+        radices.append(1 << ((pp >> sh) & 0xF))
+        sh += 4
     outer = len(radices)
     # per pass: the edge passes 12 bytes per point (real series in, or Re(y)^2 out),
     # the inner ones 16, the middle 24 (the transform both ways and the chirp)

@@ -121,13 +121,18 @@ enum cdd_attr {
                                       run)                                     */
   CDD_ATTR_TUNE_NS_TIERS_NP = 28,
   CDD_ATTR_TUNE_NS_MULTI = 29,
-  CDD_ATTR_TURN_TMA = 30           /* plan only, settable 0 (default) or 1: the
+  CDD_ATTR_TURN_TMA = 30,          /* plan only, settable 0 (default) or 1: the
                                       corner turn as tensor-memory-accelerator
                                       tile copies (2-D tensor loads and stores,
                                       transposed in shared memory) where the
                                       layout allows it (n_chan a multiple of 8,
                                       16-byte aligned input); the same bits as
                                       the default turn                         */
+  CDD_ATTR_PASS_PLAN = 31          /* full band only: the transform's pass plan,
+                                      log2 of the shared-memory transform in
+                                      bits 0-7, then log2 of each outer HBM
+                                      pass's radix, 4 bits each from bit 8,
+                                      pass 0 (largest stride) first            */
 };
 
 /* Launch forms of a batch; they differ in how the (tier, channel, segment)

@@ -32,7 +32,7 @@ ATTR = {
     "seq_gaps": 15, "polarisations": 16, "stage_timing": 17, "timed_blocks": 18,
     "corner_turn_ns": 19, "ols_ns": 20, "phase_floats": 22, "precision": 23,
     "device_errors": 24, "host_staging_bytes": 25, "batch_form": 26, "tune_ns_tiers": 27,
-    "tune_ns_tiers_np": 28, "tune_ns_multi": 29, "turn_tma": 30,
+    "tune_ns_tiers_np": 28, "tune_ns_multi": 29, "turn_tma": 30, "pass_plan": 31,
 }
 BATCH_FORM = {"tune": -1, "tiers": 0, "tiers_np": 1, "multi": 2}
 POOL_ATTR = {"budget": 100, "used_bytes": 101, "streams": 102, "queued": 103}

@@ -1250,6 +1250,16 @@ int cdd_fullband_get(cdd_fullband f, int attr, int64_t* v) {
     case CDD_ATTR_BYTES_DEVICE: *v = (int64_t)f->bytes_device; break;
     case CDD_ATTR_BLOCKS_DONE: *v = f->blocks; break;
     case CDD_ATTR_KERNEL_LAUNCHES: *v = f->last_launches; break;
+    case CDD_ATTR_PASS_PLAN: {
+      int64_t plan = f->logs;
+      for (size_t p = 0; p < f->radix_out.size(); ++p) {
+        int lr = 0;
+        while ((1 << lr) < f->radix_out[p]) ++lr;
+        plan |= (int64_t)lr << (8 + 4 * p);
+      }
+      *v = plan;
+      break;
+    }
     default: return CDD_EINVAL;
   }
   return CDD_OK;

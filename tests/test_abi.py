@@ -270,6 +270,34 @@ def test_fullband_geometry_matches_oracle(cdd, geo):
         assert g.n_fft == 2 ** 26
 
 
+@pytest.mark.parametrize("logn, want", [
+    (14, (14, [])),                 # one shared-memory transform
+    (15, (14, [1])),                # one radix-2 register pass
+    (18, (14, [4])),                # one radix-16 pass
+    (19, (14, [4, 1])),             # radix 16 then 2
+    (20, (13, [7])),                # 8192-point transforms and one radix-128 tile pass
+    (21, (13, [6, 2])),
+    (24, (13, [7, 4])),
+    (25, (13, [6, 6])),
+    (26, (13, [6, 7])),             # the 32 MHz mode: radix 64 then 128
+    (27, (13, [7, 7])),
+])
+def test_fullband_pass_plan(cdd, logn, want):
+    """Every outer pass plan covers log2 N exactly, and the plans are those the
+    full-band parity tests run (CDD_ATTR_PASS_PLAN)."""
+    f = cdd.cdd_fullband_create(325.0, 2.0, 64, 5.0, 1 << logn, 4)
+    try:
+        pp = cdd.cdd_fullband_get(f, "pass_plan")
+    finally:
+        cdd.cdd_fullband_destroy(f)
+    logs, lrs, sh = pp & 0xFF, [], 8
+    while (pp >> sh) & 0xF:
+        lrs.append((pp >> sh) & 0xF)
+        sh += 4
+    assert (logs, lrs) == want
+    assert logs + sum(lrs) == logn
+
+
 def test_fullband_rejects_bad_requests(cdd):
     for args in [(325.0, 32.0, 500, 50.0, 0, 16),          # frame not a power of two
                  (325.0, 32.0, 512, 50.0, 1 << 20, 16),    # N below the smear
