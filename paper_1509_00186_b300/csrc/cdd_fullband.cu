@@ -5,13 +5,18 @@
 //
 // The real series is transformed as a complex one (zero imaginary part) with a
 // Hermitian chirp, so the inverse is real up to rounding and its real part is
-// kept.  N = L_out * L_mid, L_mid = min(N, 16384):
-//   outer DIF passes   radix <= 16 per pass through HBM, one thread per
-//                      butterfly, twiddles from two small tables
+// kept.  N = L_out * L_mid, L_mid = min(N, 16384) below N = 2^20 and 8192
+// from there on:
+//   outer DIF passes   through HBM: radix-64 and radix-128 tiles of
+//                      neighbouring butterflies, their DFT done in two radix
+//                      stages through shared memory, and radix <= 16 register
+//                      passes (one thread per butterfly) for the bits left
 //   middle kernel      each contiguous L_mid sub-transform in shared memory:
 //                      forward passes, chirp, inverse passes
-//   outer DIT passes   back through HBM; the last writes Re(y)^2
-//   integrate          sums n_avg samples of the kept part of the segment
+//   outer DIT passes   back through HBM; the last writes Re(y)^2, or sums the
+//                      windows of the kept part across lanes and writes them
+//   integrate          sums n_avg samples of the kept part of the segment,
+//                      where the last pass does not
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
